@@ -1,0 +1,488 @@
+/*
+ * oracle.c -- exact decimal text -> nearest IEEE-754 binary64 (ties to even).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the parity oracle for the GPU path:
+ * only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant with
+ * the CUDA library, and the CUDA library never calls it.
+ *
+ * What it computes is the plain definition of the problem (Section 1 and
+ * Section 2 of the paper): the binary64 value nearest to the exact rational
+ * value of the decimal string, with ties broken toward the even significand,
+ * signed zero and signed infinity kept (the sign is applied last, Algorithm 1
+ * handles negatives by flipping the sign bit).  No table, no truncated
+ * product, no fast path: the decimal value is held as an exact ratio of two
+ * arbitrary-precision naturals and rounded by integer division.
+ *
+ * Grammar of one field (Section 4 lists the choices; this is the reading
+ * taken here):
+ *     [ \t\r]*  [+-]?  ( d+ ( '.' d* )? | '.' d+ )  ( [eE] [+-]? d+ )?  [ \t\r]*
+ * A field that does not match as a whole is INVALID (value = quiet NaN).
+ * An explicit exponent whose magnitude exceeds 10^15 saturates at 10^15
+ * (Section 4 allows stopping the update above a threshold); this is exact
+ * for every field shorter than about 10^15 bytes.
+ *
+ * Status byte: 0 OK, 1 INVALID, 2 OVERFLOW (finite text, |value| rounds to
+ * infinity), 3 UNDERFLOW (nonzero text, value rounds to zero).
+ *
+ * Buffers: fields are the byte runs between separators {delim, '\n'}.  A
+ * buffer that ends in a separator has no trailing empty field; an empty
+ * field elsewhere is INVALID.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+enum { OR_OK = 0, OR_INVALID = 1, OR_OVERFLOW = 2, OR_UNDERFLOW = 3 };
+
+#define OR_EXP_SAT 1000000000000000LL /* 10^15 */
+#define OR_QNAN_BITS 0x7FF8000000000000ULL
+#define OR_INF_BITS 0x7FF0000000000000ULL
+
+/* ------------------------------------------------------------------------ */
+/* Arbitrary-precision naturals: little-endian base-2^32 limbs, normalised   */
+/* so that the top limb is nonzero (n == 0 means the value 0).               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint32_t *d;
+    size_t n;
+    size_t cap;
+} big;
+
+static int big_reserve(big *a, size_t cap) {
+    if (cap <= a->cap) return 0;
+    size_t nc = a->cap ? a->cap : 8;
+    while (nc < cap) nc *= 2;
+    uint32_t *p = (uint32_t *)realloc(a->d, nc * sizeof(uint32_t));
+    if (!p) return -1;
+    a->d = p;
+    a->cap = nc;
+    return 0;
+}
+
+static void big_free(big *a) {
+    free(a->d);
+    a->d = NULL;
+    a->n = a->cap = 0;
+}
+
+static void big_trim(big *a) {
+    while (a->n && a->d[a->n - 1] == 0) a->n--;
+}
+
+static int big_set_u64(big *a, uint64_t v) {
+    if (big_reserve(a, 2)) return -1;
+    a->d[0] = (uint32_t)v;
+    a->d[1] = (uint32_t)(v >> 32);
+    a->n = 2;
+    big_trim(a);
+    return 0;
+}
+
+static int big_copy(big *dst, const big *src) {
+    if (big_reserve(dst, src->n + 1)) return -1;
+    if (src->n) memcpy(dst->d, src->d, src->n * sizeof(uint32_t));
+    dst->n = src->n;
+    return 0;
+}
+
+/* a = a * m + c */
+static int big_mul_add_small(big *a, uint32_t m, uint32_t c) {
+    uint64_t carry = c;
+    for (size_t i = 0; i < a->n; i++) {
+        uint64_t t = (uint64_t)a->d[i] * m + carry;
+        a->d[i] = (uint32_t)t;
+        carry = t >> 32;
+    }
+    if (carry) {
+        if (big_reserve(a, a->n + 1)) return -1;
+        a->d[a->n++] = (uint32_t)carry;
+    }
+    big_trim(a);
+    return 0;
+}
+
+/* a = a * 10^k */
+static int big_mul_pow10(big *a, int64_t k) {
+    while (k >= 9) {
+        if (big_mul_add_small(a, 1000000000u, 0)) return -1;
+        k -= 9;
+    }
+    uint32_t p = 1;
+    while (k-- > 0) p *= 10;
+    if (p != 1 && big_mul_add_small(a, p, 0)) return -1;
+    return 0;
+}
+
+/* a = a * 2^s */
+static int big_shl(big *a, uint64_t s) {
+    if (a->n == 0 || s == 0) return 0;
+    size_t w = (size_t)(s / 32);
+    unsigned b = (unsigned)(s % 32);
+    if (big_reserve(a, a->n + w + 1)) return -1;
+    size_t n = a->n;
+    a->d[n + w] = 0;
+    for (size_t i = n; i-- > 0;) {
+        uint32_t v = a->d[i];
+        if (b) {
+            a->d[i + w + 1] |= v >> (32 - b);
+            a->d[i + w] = v << b;
+        } else {
+            a->d[i + w] = v;
+        }
+    }
+    for (size_t i = 0; i < w; i++) a->d[i] = 0;
+    a->n = n + w + 1;
+    big_trim(a);
+    return 0;
+}
+
+/* a = floor(a / 2) */
+static void big_shr1(big *a) {
+    for (size_t i = 0; i < a->n; i++) {
+        uint32_t hi = (i + 1 < a->n) ? a->d[i + 1] : 0;
+        a->d[i] = (a->d[i] >> 1) | (hi << 31);
+    }
+    big_trim(a);
+}
+
+static int big_cmp(const big *a, const big *b) {
+    if (a->n != b->n) return a->n < b->n ? -1 : 1;
+    for (size_t i = a->n; i-- > 0;) {
+        if (a->d[i] != b->d[i]) return a->d[i] < b->d[i] ? -1 : 1;
+    }
+    return 0;
+}
+
+/* a = a - b, requires a >= b */
+static void big_sub(big *a, const big *b) {
+    int64_t borrow = 0;
+    for (size_t i = 0; i < a->n; i++) {
+        int64_t t = (int64_t)a->d[i] - (i < b->n ? (int64_t)b->d[i] : 0) - borrow;
+        borrow = t < 0;
+        a->d[i] = (uint32_t)(t + (borrow ? ((int64_t)1 << 32) : 0));
+    }
+    big_trim(a);
+}
+
+static uint64_t big_bitlen(const big *a) {
+    if (a->n == 0) return 0;
+    uint32_t top = a->d[a->n - 1];
+    unsigned bits = 0;
+    while (top) {
+        bits++;
+        top >>= 1;
+    }
+    return (uint64_t)(a->n - 1) * 32 + bits;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tokenizer                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int negative;
+    /* the digit characters of the significand, possibly split by one '.' */
+    const char *int_digits;
+    size_t n_int;
+    const char *frac_digits;
+    size_t n_frac;
+    int64_t exp10; /* explicit exponent, saturated */
+} token;
+
+static int is_ws(char c) { return c == ' ' || c == '\t' || c == '\r'; }
+static int is_digit(char c) { return c >= '0' && c <= '9'; }
+
+/* returns 0 on a whole-field match, -1 otherwise */
+static int tokenize(const char *s, size_t n, token *t) {
+    size_t i = 0;
+    memset(t, 0, sizeof(*t));
+    while (i < n && is_ws(s[i])) i++;
+    if (i < n && (s[i] == '+' || s[i] == '-')) {
+        t->negative = (s[i] == '-');
+        i++;
+    }
+    t->int_digits = s + i;
+    while (i < n && is_digit(s[i])) {
+        i++;
+        t->n_int++;
+    }
+    if (i < n && s[i] == '.') {
+        i++;
+        t->frac_digits = s + i;
+        while (i < n && is_digit(s[i])) {
+            i++;
+            t->n_frac++;
+        }
+    }
+    if (t->n_int + t->n_frac == 0) return -1; /* needs at least one digit */
+    if (i < n && (s[i] == 'e' || s[i] == 'E')) {
+        i++;
+        int eneg = 0;
+        if (i < n && (s[i] == '+' || s[i] == '-')) {
+            eneg = (s[i] == '-');
+            i++;
+        }
+        size_t nd = 0;
+        int64_t e = 0;
+        while (i < n && is_digit(s[i])) {
+            if (e < OR_EXP_SAT) e = e * 10 + (s[i] - '0');
+            if (e > OR_EXP_SAT) e = OR_EXP_SAT;
+            i++;
+            nd++;
+        }
+        if (nd == 0) return -1; /* 'e' must be followed by digits */
+        t->exp10 = eneg ? -e : e;
+    }
+    while (i < n && is_ws(s[i])) i++;
+    return i == n ? 0 : -1;
+}
+
+/* digit k (0-based) of the concatenated significand digit string */
+static int digit_at(const token *t, size_t k) {
+    if (k < t->n_int) return t->int_digits[k] - '0';
+    return t->frac_digits[k - t->n_int] - '0';
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact conversion                                                         */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Nearest binary64 to D * 10^E for a natural D given by its significant
+ * digits [first, last] of the token (first digit nonzero, last digit
+ * nonzero).  Returns the unsigned bit pattern; writes the status.
+ */
+static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t E,
+                              uint8_t *status, int *err) {
+    size_t nd = last - first + 1;
+    /* Cheap range exits, each by a wide margin:
+     *   10^(nd-1+E) <= V < 10^(nd+E).
+     *   nd-1+E >= 309  =>  V >= 1e309 > 2^1024: rounds to infinity.
+     *   nd+E <= -324   =>  V < 1e-324 < 2^-1075: rounds to zero.            */
+    if ((int64_t)nd - 1 + E >= 309) {
+        *status = OR_OVERFLOW;
+        return OR_INF_BITS;
+    }
+    if ((int64_t)nd + E <= -324) {
+        *status = OR_UNDERFLOW;
+        return 0;
+    }
+
+    big N = {0}, D = {0}, num = {0}, den = {0}, tmp = {0};
+    uint64_t bits = 0;
+    *err = 0;
+
+    /* N = digits * 10^max(E,0),  D = 10^max(-E,0)  so that V = N / D. */
+    if (big_set_u64(&N, 0)) goto oom;
+    {
+        size_t k = first;
+        while (k <= last) {
+            uint32_t chunk = 0, mul = 1;
+            for (int j = 0; j < 9 && k <= last; j++, k++) {
+                chunk = chunk * 10 + (uint32_t)digit_at(t, k);
+                mul *= 10;
+            }
+            if (big_mul_add_small(&N, mul, chunk)) goto oom;
+        }
+    }
+    if (big_set_u64(&D, 1)) goto oom;
+    if (E >= 0) {
+        if (big_mul_pow10(&N, E)) goto oom;
+    } else {
+        if (big_mul_pow10(&D, -E)) goto oom;
+    }
+
+    /* k = floor(log2 V).  With bn, bd the bit lengths,
+     * V lies in (2^(bn-1-bd), 2^(bn-bd+1)), so k is bn-bd or bn-bd-1:
+     * it is bn-bd exactly when N >= D * 2^(bn-bd).                          */
+    int64_t k = (int64_t)big_bitlen(&N) - (int64_t)big_bitlen(&D);
+    if (big_copy(&num, &N) || big_copy(&den, &D)) goto oom;
+    if (k >= 0) {
+        if (big_shl(&den, (uint64_t)k)) goto oom;
+    } else {
+        if (big_shl(&num, (uint64_t)(-k))) goto oom;
+    }
+    if (big_cmp(&num, &den) < 0) k -= 1;
+
+    /* Unit in the last place of the result: 2^e with e = max(k,-1022) - 52.
+     * Q = floor(V / 2^e) < 2^53 and R is the remainder of that division.    */
+    int64_t e = (k > -1022 ? k : -1022) - 52;
+    if (big_copy(&num, &N) || big_copy(&den, &D)) goto oom;
+    if (e >= 0) {
+        if (big_shl(&den, (uint64_t)e)) goto oom;
+    } else {
+        if (big_shl(&num, (uint64_t)(-e))) goto oom;
+    }
+    /* Binary long division, 53 quotient bits (Q < 2^53). */
+    uint64_t Q = 0;
+    if (big_copy(&tmp, &den) || big_shl(&tmp, 52)) goto oom;
+    for (int i = 52; i >= 0; i--) {
+        if (big_cmp(&num, &tmp) >= 0) {
+            big_sub(&num, &tmp);
+            Q |= (uint64_t)1 << i;
+        }
+        big_shr1(&tmp);
+    }
+    /* num now holds R.  Round half to even: compare 2R with den. */
+    if (big_shl(&num, 1)) goto oom;
+    int c = big_cmp(&num, &den);
+    if (c > 0 || (c == 0 && (Q & 1))) Q += 1;
+    if (Q == ((uint64_t)1 << 53)) {
+        Q >>= 1;
+        e += 1;
+    }
+    if (e > 1023 - 52) {
+        *status = OR_OVERFLOW;
+        bits = OR_INF_BITS;
+    } else if (Q == 0) {
+        *status = OR_UNDERFLOW;
+        bits = 0;
+    } else if (Q < ((uint64_t)1 << 52)) {
+        /* subnormal: exponent field 0, e == -1074 */
+        *status = OR_OK;
+        bits = Q;
+    } else {
+        *status = OR_OK;
+        bits = ((uint64_t)(e + 1075) << 52) | (Q - ((uint64_t)1 << 52));
+    }
+    big_free(&N);
+    big_free(&D);
+    big_free(&num);
+    big_free(&den);
+    big_free(&tmp);
+    return bits;
+oom:
+    big_free(&N);
+    big_free(&D);
+    big_free(&num);
+    big_free(&den);
+    big_free(&tmp);
+    *err = 1;
+    *status = OR_INVALID;
+    return OR_QNAN_BITS;
+}
+
+/* One field.  Returns 0, or -1 if memory ran out. */
+int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *status) {
+    token t;
+    if (tokenize(s, n, &t) != 0) {
+        *out_bits = OR_QNAN_BITS;
+        *status = OR_INVALID;
+        return 0;
+    }
+    size_t total = t.n_int + t.n_frac;
+    /* strip leading zeros */
+    size_t first = 0;
+    while (first < total && digit_at(&t, first) == 0) first++;
+    uint64_t sign = t.negative ? 0x8000000000000000ULL : 0;
+    if (first == total) { /* the value is zero */
+        *out_bits = sign;
+        *status = OR_OK;
+        return 0;
+    }
+    /* strip trailing zeros; each one folds into the exponent */
+    size_t last = total - 1;
+    while (digit_at(&t, last) == 0) last--;
+    /* V = (digits first..last) * 10^E,
+     * E = explicit exponent - fraction digits + stripped trailing zeros.   */
+    int64_t E = t.exp10 - (int64_t)t.n_frac + (int64_t)(total - 1 - last);
+    int err = 0;
+    uint64_t bits = convert_exact(&t, first, last, E, status, &err);
+    *out_bits = bits | sign;
+    if (bits == OR_QNAN_BITS) *out_bits = bits;
+    return err ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Buffers                                                                  */
+/* ------------------------------------------------------------------------ */
+static int is_sep(char c, char delim) { return c == '\n' || c == delim; }
+
+/* Number of fields in text[0, len) under the buffer rule above. */
+uint64_t oracle_count_fields(const char *text, size_t len, char delim) {
+    if (len == 0) return 0;
+    uint64_t n = 1;
+    for (size_t i = 0; i + 1 < len; i++) n += is_sep(text[i], delim);
+    return n;
+}
+
+typedef struct {
+    const char *text;
+    size_t len;
+    char delim;
+    size_t lo, hi; /* this worker parses fields whose first byte is in [lo,hi) */
+    uint64_t first_index;
+    uint64_t *out_bits;
+    uint8_t *status;
+    int err;
+} work;
+
+/* is position p the first byte of a field? */
+static int starts_field(const char *text, size_t len, char delim, size_t p) {
+    return p < len && (p == 0 || is_sep(text[p - 1], delim));
+}
+
+static uint64_t count_starts(const char *text, size_t len, char delim, size_t lo, size_t hi) {
+    uint64_t n = 0;
+    for (size_t p = lo; p < hi; p++) n += starts_field(text, len, delim, p);
+    return n;
+}
+
+static void *worker(void *arg) {
+    work *w = (work *)arg;
+    uint64_t idx = w->first_index;
+    for (size_t p = w->lo; p < w->hi; p++) {
+        if (!starts_field(w->text, w->len, w->delim, p)) continue;
+        size_t q = p;
+        while (q < w->len && !is_sep(w->text[q], w->delim)) q++;
+        if (oracle_parse_field(w->text + p, q - p, &w->out_bits[idx], &w->status[idx])) w->err = 1;
+        idx++;
+        p = q; /* the loop increment steps over the separator */
+    }
+    return NULL;
+}
+
+/*
+ * Parse every field of text[0,len).  out_bits/status must hold `cap`
+ * entries; the number of fields is written to *count.  Returns 0, -1 on a
+ * capacity or memory error.  nthreads <= 1 runs on the calling thread.
+ */
+int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
+                        uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
+    uint64_t total = oracle_count_fields(text, len, delim);
+    *count = total;
+    if (total > cap) return -1;
+    if (nthreads < 1) nthreads = 1;
+    if ((size_t)nthreads > len / 4096 + 1) nthreads = (int)(len / 4096 + 1);
+    work *ws = (work *)calloc((size_t)nthreads, sizeof(work));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!ws || !th) {
+        free(ws);
+        free(th);
+        return -1;
+    }
+    uint64_t before = 0;
+    for (int i = 0; i < nthreads; i++) {
+        ws[i].text = text;
+        ws[i].len = len;
+        ws[i].delim = delim;
+        ws[i].lo = (size_t)((unsigned __int128)len * (unsigned)i / (unsigned)nthreads);
+        ws[i].hi = (size_t)((unsigned __int128)len * (unsigned)(i + 1) / (unsigned)nthreads);
+        ws[i].out_bits = out_bits;
+        ws[i].status = status;
+        ws[i].first_index = before;
+        before += count_starts(text, len, delim, ws[i].lo, ws[i].hi);
+    }
+    int rc = 0;
+    if (nthreads == 1) {
+        worker(&ws[0]);
+    } else {
+        for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, worker, &ws[i]);
+        for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    }
+    for (int i = 0; i < nthreads; i++) rc |= ws[i].err;
+    free(ws);
+    free(th);
+    return rc ? -1 : 0;
+}
