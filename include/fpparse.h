@@ -1,0 +1,205 @@
+/*
+ * fpparse.h -- C ABI of the GB300 bulk decimal-text -> binary64 parser.
+ *
+ * The library converts delimited ASCII decimal numbers to the nearest
+ * IEEE-754 binary64, rounding ties to even, bit for bit (the problem of
+ * Section 1 of Lemire, "Number Parsing at a Gigabyte per Second").  Every
+ * step runs in CUDA kernels on the device: field indexing, significand and
+ * exponent parsing (Section 4), the truncated power-of-five product of
+ * Algorithm 1 (Sections 6-9), the 19-digit truncation check for long
+ * significands (Section 10) and an exact big-number fallback for the rare
+ * cases those cannot settle.  There is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Pointers.  Unless stated otherwise, text, output and count pointers are
+ * DEVICE memory owned by the caller.  The library never frees them and
+ * never keeps them after the work queued by the call has finished.
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = the legacy default stream).
+ * Calls are asynchronous: they return once the work is queued on `stream`;
+ * outputs, counts and device-side errors are valid after the stream has
+ * reached that point.  Calls on the same stream are ordered.  Calls on
+ * different streams may run concurrently; each stream gets its own scratch.
+ *
+ * Fields.  A field is a maximal run of bytes between separators, the
+ * separators being '\n' and `delim` (pass '\n' for newline-only).  Field i of
+ * the buffer is written to out_f64[i] / out_status[i].  A buffer ending in a
+ * separator has no trailing empty field; an empty field elsewhere is
+ * INVALID.  A buffer of len bytes holds at most fp_max_fields(len) fields;
+ * the output arrays must hold that many entries.
+ *
+ * Grammar of a field (Section 4; the library's reading):
+ *     [ \t\r]*  [+-]?  ( d+ ( '.' d* )? | '.' d+ )  ( [eE] [+-]? d+ )?  [ \t\r]*
+ * Digits may be arbitrarily many (Section 10: up to 768 significant digits
+ * can matter; all of them are honoured).  An explicit exponent of magnitude
+ * above 10^15 saturates, which is exact for fields shorter than ~10^15 bytes.
+ *
+ * Results.  out_f64[i] is the nearest binary64 to the field's exact decimal
+ * value, ties to even; the sign is applied last, so "-0" gives -0.0 and
+ * "-1e999" gives -inf (Algorithm 1 flips the sign bit).  out_status[i] is
+ * one of FP_STATUS_*; an INVALID field gets the quiet NaN 0x7FF8000000000000.
+ * Results do not depend on which internal path produced them.
+ *
+ * Reading of text bytes.  The kernels only use bytes inside [text, text+len).
+ * Staging copies move whole aligned 16-byte granules, so they may read up
+ * to 15 bytes on either side of the range within the same granule (never
+ * another page); those bytes are never used.
+ *
+ * Errors.  Argument errors are returned before anything is queued.  CUDA
+ * launch or allocation failures return FP_ERR_CUDA.  Conditions found on the
+ * device (a bounded wait that ran out, an internal limit) are recorded in
+ * the per-stream error word, read with fp_get_error().
+ */
+#ifndef FPPARSE_H
+#define FPPARSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st; /* cudaStream_t is `struct CUstream_st *` */
+
+#if defined(__GNUC__)
+#define FP_API __attribute__((visibility("default")))
+#else
+#define FP_API
+#endif
+
+typedef enum {
+    FP_OK = 0,
+    FP_ERR_ARG = 1,      /* a bad pointer, size or flag                       */
+    FP_ERR_CAPACITY = 2, /* an output or internal capacity would be exceeded   */
+    FP_ERR_CUDA = 3,     /* a CUDA call failed (launch, copy, allocation)      */
+    FP_ERR_BUDGET = 4,   /* a device-memory budget would be exceeded           */
+    FP_ERR_TIMEOUT = 5,  /* a bounded device-side wait ran out                 */
+    FP_ERR_INTERNAL = 6  /* an internal invariant failed on the device        */
+} fp_err_t;
+
+/* Per-field status byte (device). */
+enum {
+    FP_STATUS_OK = 0,        /* finite, or an exact zero                      */
+    FP_STATUS_INVALID = 1,   /* not a number under the grammar; value is NaN  */
+    FP_STATUS_OVERFLOW = 2,  /* finite text whose value rounds to +-infinity  */
+    FP_STATUS_UNDERFLOW = 3  /* nonzero text whose value rounds to +-0        */
+};
+
+/* Path counters, accumulated over calls on one stream (fp_get_stats).      */
+typedef struct {
+    uint64_t calls;           /* parse calls queued on this stream              */
+    uint64_t fields;          /* fields parsed                                   */
+    uint64_t bytes;           /* text bytes parsed                               */
+    uint64_t one_multiply;    /* Algorithm 1 settled by one 64x64 product        */
+    uint64_t two_multiplies;  /* ... needed the second product (Section 7)       */
+    uint64_t long_fields;     /* more than 19 significant digits (Section 10)    */
+    uint64_t long_settled;    /* ... settled by the w / w+1 check                */
+    uint64_t fallback;        /* fields resolved by the exact fallback kernel    */
+    uint64_t fallback_bignum; /* ... that needed a big-number comparison         */
+    uint64_t queue_overflow;  /* fallback fields found by scanning (queue full)  */
+} fp_stats_t;
+
+/*
+ * fp_max_fields -- capacity rule for output arrays.
+ *   Returns the largest number of fields a len-byte buffer can hold: len
+ *   (every byte a separator, each closing an empty field), 0 for len == 0.
+ *   Output arrays of this many entries are always sufficient.
+ */
+FP_API size_t fp_max_fields(size_t len);
+
+/*
+ * fp_parse_f64 -- parse every field of one buffer (Sections 4-10).
+ *   text        device pointer to len bytes (any alignment; may be NULL iff len == 0)
+ *   len         bytes in the buffer (< 2^40)
+ *   delim       the second separator besides '\n'
+ *   out_f64     device array, fp_max_fields(len) doubles; field i -> out_f64[i]
+ *   out_status  device array, fp_max_fields(len) bytes; field i -> out_status[i]
+ *   out_count   device pointer to one uint64_t: the number of fields
+ *   stream      CUDA stream the work is queued on
+ * Entries of out_f64/out_status beyond the field count are left unchanged.
+ * The first call on a stream (and a call needing more scratch than any
+ * before it) allocates the stream's scratch with cudaMalloc; make such a
+ * call before capturing the stream into a CUDA graph.
+ * Returns FP_OK once queued; FP_ERR_ARG for NULL pointers with len > 0.
+ */
+FP_API fp_err_t fp_parse_f64(const char *text, size_t len, char delim, double *out_f64,
+                      uint8_t *out_status, uint64_t *out_count, struct CUstream_st *stream);
+
+/*
+ * fp_parse_f64_batch -- parse many independent buffers in one persistent
+ * launch (work is split by chunk across all buffers, not by buffer).
+ *   texts        HOST array of nbuf device pointers (NULL allowed iff lens[b] == 0)
+ *   lens         HOST array of nbuf lengths (each < 2^40)
+ *   nbuf         number of buffers (1 .. 2^24)
+ *   delim        as for fp_parse_f64
+ *   out_f64      device array; buffer b's field i -> out_f64[out_offsets[b] + i]
+ *   out_status   device array, same indexing
+ *   out_offsets  HOST array of nbuf+1 non-decreasing offsets: buffer b owns
+ *                entries [out_offsets[b], out_offsets[b+1]) of both arrays.
+ *                Fields beyond that capacity are counted but not stored, so
+ *                a region of fp_max_fields(lens[b]) entries is always enough.
+ *   out_counts   device array of nbuf uint64_t: fields per buffer (the true
+ *                count, which may exceed the region's capacity)
+ *   stream       CUDA stream
+ * The descriptors are staged and copied to the device inside the call, so
+ * the host arrays may be reused as soon as the call returns.  Scratch is
+ * allocated as for fp_parse_f64.
+ */
+FP_API fp_err_t fp_parse_f64_batch(const char *const *texts, const size_t *lens, uint32_t nbuf,
+                            char delim, double *out_f64, uint8_t *out_status,
+                            const uint64_t *out_offsets, uint64_t *out_counts,
+                            struct CUstream_st *stream);
+
+/*
+ * fp_get_stats -- copy the path counters of `stream` into *host_out
+ * (host memory).  Synchronises `stream`.  If reset != 0 the counters are
+ * zeroed afterwards.
+ */
+FP_API fp_err_t fp_get_stats(fp_stats_t *host_out, int reset, struct CUstream_st *stream);
+
+/*
+ * fp_get_error -- synchronise `stream` and return the first device-side
+ * error recorded by calls on it since the last fp_get_error (FP_OK if none);
+ * clears it.
+ */
+FP_API fp_err_t fp_get_error(struct CUstream_st *stream);
+
+/*
+ * fp_set_config / fp_get_config -- launch parameters used by later calls
+ * (all streams).  chunk_bytes: text bytes per work tile (4096, 8192 or
+ * 16384); ctas_per_sm: resident blocks per SM for the persistent grid
+ * (1..8); fallback_queue: entries of the per-stream fallback queue
+ * (>= 1024).  Returns FP_ERR_ARG for values outside those sets.
+ */
+typedef struct {
+    uint32_t chunk_bytes;
+    uint32_t ctas_per_sm;
+    uint32_t fallback_queue;
+} fp_config_t;
+FP_API fp_err_t fp_set_config(const fp_config_t *cfg);
+FP_API fp_err_t fp_get_config(fp_config_t *cfg);
+
+/*
+ * fp_autotune -- time the candidate configurations on a device buffer
+ * supplied by the caller (text/len as for fp_parse_f64; it should be
+ * representative of the workload), pick the fastest, make it current and,
+ * if cache_path is not NULL, write it to that file as one JSON object.  If
+ * cache_path names an existing file written for the same GPU, its entry is
+ * loaded instead and nothing is timed.  Synchronous; allocates temporary
+ * output arrays with cudaMalloc.
+ */
+FP_API fp_err_t fp_autotune(const char *text, size_t len, char delim, const char *cache_path,
+                     fp_config_t *chosen);
+
+/* fp_shutdown -- synchronise and free every stream's scratch. */
+FP_API fp_err_t fp_shutdown(void);
+
+/* fp_strerror -- static text for an fp_err_t. */
+FP_API const char *fp_strerror(fp_err_t err);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPPARSE_H */

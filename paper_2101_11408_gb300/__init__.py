@@ -1,0 +1,194 @@
+"""GB300-native bulk parser: ASCII decimal text -> nearest binary64, bit-exact.
+
+Python front end of libfpparse.so (C ABI in include/fpparse.h).  PyTorch
+supplies device memory and streams; every step of the parse runs in the
+library's sm_103a kernels.  If the library cannot be loaded these functions
+raise: there is no CPU implementation behind them.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (STATUS_INVALID, STATUS_OK, STATUS_OVERFLOW, STATUS_UNDERFLOW, Config,
+                   FpError, Stats)
+
+__all__ = ["parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_batch",
+           "parse_f64_batch_into", "max_fields", "stats", "get_error", "set_config",
+           "get_config", "autotune", "shutdown", "library_path", "FpError", "STATUS_OK",
+           "STATUS_INVALID", "STATUS_OVERFLOW", "STATUS_UNDERFLOW"]
+
+
+def library_path() -> str:
+    return _lib.library_path()
+
+
+def _delim_byte(delim) -> bytes:
+    if isinstance(delim, str):
+        delim = delim.encode()
+    if not isinstance(delim, (bytes, bytearray)) or len(delim) != 1:
+        raise ValueError("delim must be one byte")
+    return bytes(delim)
+
+
+def _stream_handle(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _check_text(text: torch.Tensor) -> None:
+    if not isinstance(text, torch.Tensor) or text.dtype != torch.uint8 or text.dim() != 1:
+        raise TypeError("text must be a 1-D torch.uint8 tensor")
+    if not text.is_cuda:
+        raise TypeError("text must be a CUDA tensor (use parse_f64_host for host data)")
+    if not text.is_contiguous():
+        raise TypeError("text must be contiguous")
+
+
+def max_fields(nbytes: int) -> int:
+    return int(_lib.load().fp_max_fields(nbytes))
+
+
+def parse_f64_into(text: torch.Tensor, out_f64: torch.Tensor, out_status: torch.Tensor,
+                   out_count: torch.Tensor, delim=b"\n", stream=None) -> None:
+    """Queue the parse of `text` on `stream` (asynchronous).
+
+    out_f64 (float64), out_status (uint8) need max_fields(len) entries on the
+    same device; out_count is a one-element int64/uint64 device tensor.
+    """
+    _check_text(text)
+    n = text.numel()
+    if out_f64.dtype != torch.float64 or out_status.dtype != torch.uint8:
+        raise TypeError("out_f64 must be float64 and out_status uint8")
+    if n and (out_f64.numel() < n or out_status.numel() < n):
+        raise ValueError("output arrays need max_fields(len) entries")
+    lib = _lib.load()
+    rc = lib.fp_parse_f64(text.data_ptr() if n else None, n, _delim_byte(delim),
+                          out_f64.data_ptr() if n else None,
+                          out_status.data_ptr() if n else None, out_count.data_ptr(),
+                          _stream_handle(stream))
+    _lib.check(rc, "fp_parse_f64")
+
+
+def parse_f64(text: torch.Tensor, delim=b"\n", stream=None):
+    """Parse every field of a device buffer.  Returns (values float64,
+    status uint8) device tensors of the field count (synchronises)."""
+    _check_text(text)
+    dev = text.device
+    cap = max(text.numel(), 1)
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+    st = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    parse_f64_into(text, out, st, cnt, delim, stream)
+    n = int(cnt.item()) if stream is None else None
+    if n is None:
+        stream.synchronize()
+        n = int(cnt.item())
+    return out[:n], st[:n]
+
+
+def parse_f64_host(data, delim=b"\n", device=None, stream=None):
+    """End-to-end path for host data: pinned host -> device copy, parse,
+    device -> host copy of the results.  Returns numpy (values, status)."""
+    if isinstance(data, (bytes, bytearray, memoryview)):
+        arr = np.frombuffer(bytes(data), dtype=np.uint8)
+    else:
+        arr = np.ascontiguousarray(data, dtype=np.uint8)
+    device = torch.device(device or "cuda")
+    host = torch.from_numpy(arr).pin_memory() if arr.size else torch.empty(0, dtype=torch.uint8)
+    text = torch.empty(arr.size, dtype=torch.uint8, device=device)
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    with torch.cuda.stream(s):
+        if arr.size:
+            text.copy_(host, non_blocking=True)
+        vals, st = parse_f64(text, delim, stream=s)
+        return vals.cpu().numpy(), st.cpu().numpy()
+
+
+def parse_f64_batch_into(texts, out_f64: torch.Tensor, out_status: torch.Tensor,
+                         out_offsets, out_counts: torch.Tensor, delim=b"\n",
+                         stream=None) -> None:
+    """Queue one persistent launch over many device buffers.
+
+    out_offsets: nbuf+1 host integers; buffer b owns output entries
+    [out_offsets[b], out_offsets[b+1]).  out_counts: nbuf-element device
+    tensor receiving the field counts.
+    """
+    nbuf = len(texts)
+    if nbuf == 0:
+        raise ValueError("no buffers")
+    for t in texts:
+        _check_text(t)
+    ptrs = (ctypes.c_void_p * nbuf)(*[t.data_ptr() if t.numel() else None for t in texts])
+    lens = (ctypes.c_size_t * nbuf)(*[t.numel() for t in texts])
+    offs = (ctypes.c_uint64 * (nbuf + 1))(*[int(o) for o in out_offsets])
+    if out_counts.numel() < nbuf:
+        raise ValueError("out_counts needs one entry per buffer")
+    lib = _lib.load()
+    rc = lib.fp_parse_f64_batch(ptrs, lens, nbuf, _delim_byte(delim), out_f64.data_ptr(),
+                                out_status.data_ptr(), offs, out_counts.data_ptr(),
+                                _stream_handle(stream))
+    _lib.check(rc, "fp_parse_f64_batch")
+
+
+def parse_f64_batch(texts, delim=b"\n", stream=None):
+    """Parse many device buffers in one launch.  Returns a list of
+    (values, status) device tensors, one per buffer (synchronises)."""
+    offs = [0]
+    for t in texts:
+        offs.append(offs[-1] + max(t.numel(), 0))
+    dev = texts[0].device
+    cap = max(offs[-1], 1)
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+    st = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(len(texts), dtype=torch.int64, device=dev)
+    parse_f64_batch_into(texts, out, st, offs, cnt, delim, stream)
+    if stream is not None:
+        stream.synchronize()
+    counts = cnt.cpu().tolist()
+    return [(out[offs[b]:offs[b] + counts[b]], st[offs[b]:offs[b] + counts[b]])
+            for b in range(len(texts))]
+
+
+def stats(reset: bool = False, stream=None) -> dict:
+    s = Stats()
+    _lib.check(_lib.load().fp_get_stats(ctypes.byref(s), int(reset), _stream_handle(stream)),
+               "fp_get_stats")
+    return s.as_dict()
+
+
+def get_error(stream=None) -> int:
+    return int(_lib.load().fp_get_error(_stream_handle(stream)))
+
+
+def set_config(chunk_bytes=None, ctas_per_sm=None, fallback_queue=None) -> dict:
+    cur = get_config()
+    c = Config(chunk_bytes if chunk_bytes is not None else cur["chunk_bytes"],
+               ctas_per_sm if ctas_per_sm is not None else cur["ctas_per_sm"],
+               fallback_queue if fallback_queue is not None else cur["fallback_queue"])
+    _lib.check(_lib.load().fp_set_config(ctypes.byref(c)), "fp_set_config")
+    return get_config()
+
+
+def get_config() -> dict:
+    c = Config()
+    _lib.check(_lib.load().fp_get_config(ctypes.byref(c)), "fp_get_config")
+    return {"chunk_bytes": c.chunk_bytes, "ctas_per_sm": c.ctas_per_sm,
+            "fallback_queue": c.fallback_queue}
+
+
+def autotune(text: torch.Tensor, delim=b"\n", cache_path: str | None = None) -> dict:
+    _check_text(text)
+    c = Config()
+    _lib.check(_lib.load().fp_autotune(text.data_ptr(), text.numel(), _delim_byte(delim),
+                                       cache_path.encode() if cache_path else None,
+                                       ctypes.byref(c)), "fp_autotune")
+    return {"chunk_bytes": c.chunk_bytes, "ctas_per_sm": c.ctas_per_sm,
+            "fallback_queue": c.fallback_queue}
+
+
+def shutdown() -> None:
+    _lib.check(_lib.load().fp_shutdown(), "fp_shutdown")

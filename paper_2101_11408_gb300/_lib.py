@@ -1,0 +1,97 @@
+"""ctypes binding of libfpparse.so (include/fpparse.h).  Argument marshalling
+only: every step of the parse runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+FP_OK, FP_ERR_ARG, FP_ERR_CAPACITY, FP_ERR_CUDA, FP_ERR_BUDGET, FP_ERR_TIMEOUT, \
+    FP_ERR_INTERNAL = range(7)
+STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
+
+# every symbol include/fpparse.h declares
+EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f64_batch", "fp_get_stats",
+           "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_shutdown",
+           "fp_strerror"]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "calls", "fields", "bytes", "one_multiply", "two_multiplies", "long_fields",
+        "long_settled", "fallback", "fallback_bignum", "queue_overflow")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("chunk_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("fallback_queue", ctypes.c_uint32)]
+
+
+class FpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (where, strerror(code), code))
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it in-tree if absent).  Raises if it
+    cannot be loaded: there is no fallback implementation."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError("libfpparse.so is not built (%s)" % path)
+            _build.build_library()
+        lib = ctypes.CDLL(path)
+        vp, sz, u8p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p
+        lib.fp_max_fields.argtypes = [sz]
+        lib.fp_max_fields.restype = sz
+        lib.fp_parse_f64.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
+        lib.fp_parse_f64.restype = ctypes.c_int
+        lib.fp_parse_f64_batch.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_char, vp, u8p,
+                                           vp, vp, vp]
+        lib.fp_parse_f64_batch.restype = ctypes.c_int
+        lib.fp_get_stats.argtypes = [ctypes.POINTER(Stats), ctypes.c_int, vp]
+        lib.fp_get_stats.restype = ctypes.c_int
+        lib.fp_get_error.argtypes = [vp]
+        lib.fp_get_error.restype = ctypes.c_int
+        lib.fp_set_config.argtypes = [ctypes.POINTER(Config)]
+        lib.fp_set_config.restype = ctypes.c_int
+        lib.fp_get_config.argtypes = [ctypes.POINTER(Config)]
+        lib.fp_get_config.restype = ctypes.c_int
+        lib.fp_autotune.argtypes = [vp, sz, ctypes.c_char, ctypes.c_char_p,
+                                    ctypes.POINTER(Config)]
+        lib.fp_autotune.restype = ctypes.c_int
+        lib.fp_shutdown.argtypes = []
+        lib.fp_shutdown.restype = ctypes.c_int
+        lib.fp_strerror.argtypes = [ctypes.c_int]
+        lib.fp_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().fp_strerror(code).decode()
+    except Exception:  # library not loadable: describe the code ourselves
+        return "error %d" % code
+
+
+def check(code: int, where: str) -> None:
+    if code != FP_OK:
+        raise FpError(code, where)

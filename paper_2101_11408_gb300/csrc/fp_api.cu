@@ -1,0 +1,527 @@
+// fp_api.cu -- the C ABI (include/fpparse.h): argument checks, per-stream
+// scratch, launch configuration, counters and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fpparse.h"
+#include "fp_device.cuh"
+#include "fp_launch.h"
+#include "fp_types.cuh"
+
+namespace {
+
+using fp::BufDesc;
+using fp::Ctl;
+using fp::LaunchParams;
+
+constexpr unsigned long long MAX_LEN = 1ull << 40;
+constexpr uint32_t MAX_BUFS = 1u << 24;
+
+struct Config {
+  uint32_t chunk_bytes = 8192;
+  uint32_t ctas_per_sm = 0;  // 0: as many as fit
+  uint32_t fallback_queue = 1u << 20;
+};
+
+std::mutex g_mu;
+Config g_cfg;
+
+struct DeviceInfo {
+  int sms = 0;
+  std::map<int, int> parse_occ;  // chunk bytes -> resident blocks per SM
+  int fb_occ = 0;
+  char name[256] = {0};
+};
+std::map<int, DeviceInfo> g_dev;
+
+struct Scratch {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  Ctl* ctl = nullptr;
+  unsigned long long* chunk_status = nullptr;
+  unsigned long long cap_chunks = 0;
+  unsigned long long* queue = nullptr;
+  unsigned long long qcap = 0;
+  unsigned long long* ovf = nullptr;
+  unsigned long long ovf_cap = 0;
+  BufDesc* d_descs = nullptr;
+  BufDesc* h_descs = nullptr;  // pinned staging for the descriptor upload
+  uint32_t cap_descs = 0;
+  cudaEvent_t desc_copied = nullptr;
+  bool desc_pending = false;
+  unsigned int epoch = 1;
+  unsigned long long calls = 0, bytes = 0;
+};
+std::map<std::pair<int, cudaStream_t>, Scratch*> g_scratch;
+
+#define FP_CUDA(x)                                  \
+  do {                                              \
+    cudaError_t e_ = (x);                           \
+    if (e_ != cudaSuccess) {                        \
+      fprintf(stderr, "fpparse: %s failed: %s\n", #x, cudaGetErrorString(e_)); \
+      return FP_ERR_CUDA;                           \
+    }                                               \
+  } while (0)
+
+fp_err_t device_info(int dev, DeviceInfo** out) {
+  auto it = g_dev.find(dev);
+  if (it == g_dev.end()) {
+    DeviceInfo di;
+    cudaDeviceProp prop;
+    FP_CUDA(cudaGetDeviceProperties(&prop, dev));
+    di.sms = prop.multiProcessorCount;
+    snprintf(di.name, sizeof(di.name), "%s", prop.name);
+    for (int c : {4096, 8192, 16384}) {
+      int occ = 0;
+      FP_CUDA(fp::parse_occupancy(c, &occ));
+      di.parse_occ[c] = std::max(occ, 1);
+    }
+    FP_CUDA(fp::fallback_occupancy(&di.fb_occ));
+    di.fb_occ = std::max(di.fb_occ, 1);
+    it = g_dev.emplace(dev, di).first;
+  }
+  *out = &it->second;
+  return FP_OK;
+}
+
+void free_scratch(Scratch* s) {
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaFree(s->ctl);
+  cudaFree(s->chunk_status);
+  cudaFree(s->queue);
+  cudaFree(s->ovf);
+  cudaFree(s->d_descs);
+  cudaFreeHost(s->h_descs);
+  if (s->desc_copied) cudaEventDestroy(s->desc_copied);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete s;
+}
+
+// Scratch of (current device, stream) with room for `chunks` chunks and
+// `nbuf` descriptors.
+fp_err_t get_scratch(cudaStream_t stream, unsigned long long chunks, uint32_t nbuf,
+                     uint32_t qcap, Scratch** out) {
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  auto key = std::make_pair(dev, stream);
+  Scratch*& s = g_scratch[key];
+  if (!s) {
+    s = new Scratch();
+    s->device = dev;
+    s->stream = stream;
+    if (cudaMalloc(&s->ctl, sizeof(Ctl)) != cudaSuccess) {
+      delete s;
+      s = nullptr;
+      return FP_ERR_CUDA;
+    }
+    FP_CUDA(cudaMemsetAsync(s->ctl, 0, sizeof(Ctl), stream));
+    FP_CUDA(cudaEventCreateWithFlags(&s->desc_copied, cudaEventDisableTiming));
+  }
+  if (chunks > s->cap_chunks) {
+    unsigned long long cap = std::max<unsigned long long>(chunks, 1ull << 15);
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->chunk_status);
+    cudaFree(s->ovf);
+    s->chunk_status = nullptr;
+    s->ovf = nullptr;
+    s->cap_chunks = 0;
+    FP_CUDA(cudaMalloc(&s->chunk_status, cap * sizeof(unsigned long long)));
+    FP_CUDA(cudaMalloc(&s->ovf, 2 * cap * sizeof(unsigned long long)));
+    FP_CUDA(cudaMemsetAsync(s->chunk_status, 0, cap * sizeof(unsigned long long), stream));
+    s->cap_chunks = cap;
+    s->ovf_cap = cap;
+    s->epoch = 1;
+  }
+  if (qcap != s->qcap) {
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->queue);
+    s->queue = nullptr;
+    s->qcap = 0;
+    FP_CUDA(cudaMalloc(&s->queue, (size_t)qcap * sizeof(unsigned long long)));
+    s->qcap = qcap;
+  }
+  if (nbuf > 1 && nbuf > s->cap_descs) {
+    uint32_t cap = std::max<uint32_t>(nbuf, 256);
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->d_descs);
+    cudaFreeHost(s->h_descs);
+    s->d_descs = nullptr;
+    s->h_descs = nullptr;
+    s->cap_descs = 0;
+    FP_CUDA(cudaMalloc(&s->d_descs, (size_t)cap * sizeof(BufDesc)));
+    FP_CUDA(cudaMallocHost(&s->h_descs, (size_t)cap * sizeof(BufDesc)));
+    s->cap_descs = cap;
+    s->desc_pending = false;
+  }
+  *out = s;
+  return FP_OK;
+}
+
+unsigned long long chunks_of(unsigned long long o, unsigned long long len, uint32_t C) {
+  unsigned long long n = (o + len + C - 1) / C;
+  return n ? n : 1;
+}
+
+void fill_desc(BufDesc& d, const char* text, size_t len, unsigned long long chunk0,
+               unsigned long long nchunks, unsigned long long out_base, unsigned long long out_cap,
+               uint64_t* out_count) {
+  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
+  d.base = reinterpret_cast<const uint8_t*>(t & ~(uintptr_t)15);
+  d.o = t & 15;
+  d.len = len;
+  d.chunk0 = chunk0;
+  d.nchunks = nchunks;
+  d.out_base = out_base;
+  d.out_cap = out_cap;
+  d.out_count = reinterpret_cast<unsigned long long*>(out_count);
+}
+
+// Queue the two kernels of one call.
+fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& p,
+             unsigned long long total_chunks, unsigned long long total_bytes, cudaStream_t stream) {
+  if (s->epoch >= fp::LB_EPOCH_MAX) {
+    FP_CUDA(cudaMemsetAsync(s->chunk_status, 0, s->cap_chunks * sizeof(unsigned long long), stream));
+    s->epoch = 1;
+  }
+  p.ctl = s->ctl;
+  p.chunk_status = s->chunk_status;
+  p.epoch = s->epoch++;
+  p.queue = s->queue;
+  p.qcap = s->qcap;
+  p.ovf = s->ovf;
+  p.ovf_cap = s->ovf_cap;
+  p.total_chunks = total_chunks;
+  const int occ = di.parse_occ.at((int)cfg.chunk_bytes);
+  const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
+  unsigned long long grid = (unsigned long long)di.sms * per_sm;
+  if (grid > total_chunks) grid = total_chunks;
+  FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream));
+  FP_CUDA(fp::launch_fallback(p, di.sms * di.fb_occ, stream));
+  s->calls++;
+  s->bytes += total_bytes;
+  return FP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t fp_max_fields(size_t len) { return len; }
+
+fp_err_t fp_parse_f64(const char* text, size_t len, char delim, double* out_f64,
+                      uint8_t* out_status, uint64_t* out_count, struct CUstream_st* stream_) {
+  if (len >= MAX_LEN) return FP_ERR_ARG;
+  if (!out_count) return FP_ERR_ARG;
+  if (len > 0 && (!text || !out_f64 || !out_status)) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Config cfg = g_cfg;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
+  const unsigned long long nch = chunks_of(t & 15, len, cfg.chunk_bytes);
+  Scratch* s = nullptr;
+  e = get_scratch(stream, nch, 1, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  fill_desc(p.one, text, len, 0, nch, 0, len, out_count);
+  p.descs = nullptr;
+  p.nbuf = 1;
+  p.delim = (unsigned char)delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
+  p.out_status = out_status;
+  return run(s, cfg, *di, p, nch, len, stream);
+}
+
+fp_err_t fp_parse_f64_batch(const char* const* texts, const size_t* lens, uint32_t nbuf,
+                            char delim, double* out_f64, uint8_t* out_status,
+                            const uint64_t* out_offsets, uint64_t* out_counts,
+                            struct CUstream_st* stream_) {
+  if (!texts || !lens || !out_offsets || !out_counts) return FP_ERR_ARG;
+  if (nbuf == 0 || nbuf > MAX_BUFS) return FP_ERR_ARG;
+  bool any = false;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    if (lens[b] >= MAX_LEN) return FP_ERR_ARG;
+    if (lens[b] > 0 && !texts[b]) return FP_ERR_ARG;
+    if (out_offsets[b + 1] < out_offsets[b]) return FP_ERR_ARG;
+    any |= out_offsets[b + 1] > out_offsets[b];
+  }
+  if (any && (!out_f64 || !out_status)) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Config cfg = g_cfg;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  unsigned long long total = 0, bytes = 0;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    total += chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
+    bytes += lens[b];
+  }
+  Scratch* s = nullptr;
+  e = get_scratch(stream, total, nbuf, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  p.nbuf = nbuf;
+  p.delim = (unsigned char)delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
+  p.out_status = out_status;
+  if (nbuf == 1) {
+    fill_desc(p.one, texts[0], lens[0], 0, total, out_offsets[0], out_offsets[1] - out_offsets[0],
+              out_counts);
+  } else {
+    // the staging buffer may still feed the previous call's upload
+    if (s->desc_pending) FP_CUDA(cudaEventSynchronize(s->desc_copied));
+    unsigned long long c = 0;
+    for (uint32_t b = 0; b < nbuf; b++) {
+      const unsigned long long nch =
+          chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
+      fill_desc(s->h_descs[b], texts[b], lens[b], c, nch, out_offsets[b],
+                out_offsets[b + 1] - out_offsets[b], out_counts + b);
+      c += nch;
+    }
+    FP_CUDA(cudaMemcpyAsync(s->d_descs, s->h_descs, (size_t)nbuf * sizeof(BufDesc),
+                            cudaMemcpyHostToDevice, stream));
+    FP_CUDA(cudaEventRecord(s->desc_copied, stream));
+    s->desc_pending = true;
+    p.descs = s->d_descs;
+  }
+  return run(s, cfg, *di, p, total, bytes, stream);
+}
+
+fp_err_t fp_get_stats(fp_stats_t* host_out, int reset, struct CUstream_st* stream_) {
+  if (!host_out) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  memset(host_out, 0, sizeof(*host_out));
+  auto it = g_scratch.find(std::make_pair(dev, stream));
+  if (it == g_scratch.end()) return FP_OK;
+  Scratch* s = it->second;
+  unsigned long long st[16];
+  FP_CUDA(cudaMemcpyAsync(st, s->ctl->stats, sizeof(st), cudaMemcpyDeviceToHost, stream));
+  FP_CUDA(cudaStreamSynchronize(stream));
+  host_out->calls = s->calls;
+  host_out->bytes = s->bytes;
+  host_out->fields = st[fp::CNT_FIELDS];
+  host_out->one_multiply = st[fp::CNT_ONE_MUL];
+  host_out->two_multiplies = st[fp::CNT_TWO_MUL];
+  host_out->long_fields = st[fp::CNT_LONG];
+  host_out->long_settled = st[fp::CNT_LONG_SETTLED];
+  host_out->fallback = st[fp::CNT_FALLBACK];
+  host_out->fallback_bignum = st[fp::CNT_FALLBACK_BIGNUM];
+  host_out->queue_overflow = st[fp::CNT_QUEUE_OVERFLOW];
+  if (reset) {
+    FP_CUDA(cudaMemsetAsync(s->ctl->stats, 0, sizeof(st), stream));
+    FP_CUDA(cudaStreamSynchronize(stream));
+    s->calls = s->bytes = 0;
+  }
+  return FP_OK;
+}
+
+fp_err_t fp_get_error(struct CUstream_st* stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  auto it = g_scratch.find(std::make_pair(dev, stream));
+  if (it == g_scratch.end()) return FP_OK;
+  Scratch* s = it->second;
+  unsigned int err = 0;
+  FP_CUDA(cudaMemcpyAsync(&err, &s->ctl->error, sizeof(err), cudaMemcpyDeviceToHost, stream));
+  FP_CUDA(cudaStreamSynchronize(stream));
+  if (err) {
+    FP_CUDA(cudaMemsetAsync(&s->ctl->error, 0, sizeof(err), stream));
+    FP_CUDA(cudaStreamSynchronize(stream));
+  }
+  return (fp_err_t)err;
+}
+
+fp_err_t fp_set_config(const fp_config_t* cfg) {
+  if (!cfg) return FP_ERR_ARG;
+  if (cfg->chunk_bytes != 4096 && cfg->chunk_bytes != 8192 && cfg->chunk_bytes != 16384)
+    return FP_ERR_ARG;
+  if (cfg->ctas_per_sm > 8) return FP_ERR_ARG;
+  if (cfg->fallback_queue < 1024 || cfg->fallback_queue > (1u << 28)) return FP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cfg.chunk_bytes = cfg->chunk_bytes;
+  g_cfg.ctas_per_sm = cfg->ctas_per_sm;
+  g_cfg.fallback_queue = cfg->fallback_queue;
+  return FP_OK;
+}
+
+fp_err_t fp_get_config(fp_config_t* cfg) {
+  if (!cfg) return FP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cfg->chunk_bytes = g_cfg.chunk_bytes;
+  cfg->ctas_per_sm = g_cfg.ctas_per_sm;
+  cfg->fallback_queue = g_cfg.fallback_queue;
+  return FP_OK;
+}
+
+fp_err_t fp_shutdown(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& kv : g_scratch) {
+    if (kv.second) {
+      cudaSetDevice(kv.second->device);
+      cudaStreamSynchronize(kv.second->stream);
+      free_scratch(kv.second);
+    }
+  }
+  g_scratch.clear();
+  return FP_OK;
+}
+
+const char* fp_strerror(fp_err_t err) {
+  switch (err) {
+    case FP_OK: return "ok";
+    case FP_ERR_ARG: return "invalid argument";
+    case FP_ERR_CAPACITY: return "capacity exceeded";
+    case FP_ERR_CUDA: return "CUDA call failed";
+    case FP_ERR_BUDGET: return "device memory budget exceeded";
+    case FP_ERR_TIMEOUT: return "bounded device wait ran out";
+    case FP_ERR_INTERNAL: return "internal device error";
+  }
+  return "unknown error";
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+bool read_cache(const char* path, const char* gpu, fp_config_t* cfg) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char buf[4096];
+  size_t n = fread(buf, 1, sizeof(buf) - 1, f);
+  fclose(f);
+  buf[n] = 0;
+  std::string s(buf);
+  std::string key = std::string("\"gpu\": \"") + gpu + "\"";
+  if (s.find(key) == std::string::npos) return false;
+  auto num = [&](const char* k, uint32_t* v) -> bool {
+    std::string kk = std::string("\"") + k + "\": ";
+    size_t p = s.find(kk);
+    if (p == std::string::npos) return false;
+    *v = (uint32_t)strtoul(s.c_str() + p + kk.size(), nullptr, 10);
+    return true;
+  };
+  return num("chunk_bytes", &cfg->chunk_bytes) && num("ctas_per_sm", &cfg->ctas_per_sm) &&
+         num("fallback_queue", &cfg->fallback_queue);
+}
+
+}  // namespace
+
+extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const char* cache_path,
+                                fp_config_t* chosen) {
+  if (!text || len == 0 || len >= MAX_LEN) return FP_ERR_ARG;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  char gpu[256];
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceInfo* di = nullptr;
+    fp_err_t e = device_info(dev, &di);
+    if (e != FP_OK) return e;
+    snprintf(gpu, sizeof(gpu), "%s", di->name);
+  }
+  fp_config_t cur;
+  fp_get_config(&cur);
+  if (cache_path) {
+    fp_config_t c = cur;
+    if (read_cache(cache_path, gpu, &c) && fp_set_config(&c) == FP_OK) {
+      if (chosen) *chosen = c;
+      return FP_OK;
+    }
+  }
+  double* out = nullptr;
+  uint8_t* st = nullptr;
+  uint64_t* cnt = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  FP_CUDA(cudaMalloc(&out, len * sizeof(double)));
+  FP_CUDA(cudaMalloc(&st, len));
+  FP_CUDA(cudaMalloc(&cnt, sizeof(uint64_t)));
+  FP_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  FP_CUDA(cudaEventCreate(&e0));
+  FP_CUDA(cudaEventCreate(&e1));
+  fp_config_t best = cur;
+  float best_ms = 1e30f;
+  fp_err_t err = FP_OK;
+  for (uint32_t chunk : {4096u, 8192u, 16384u}) {
+    for (uint32_t per_sm : {1u, 2u, 3u, 4u, 0u}) {
+      fp_config_t c = cur;
+      c.chunk_bytes = chunk;
+      c.ctas_per_sm = per_sm;
+      if (fp_set_config(&c) != FP_OK) continue;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4 && err == FP_OK; rep++) {
+        cudaEventRecord(e0, stream);
+        err = fp_parse_f64(text, len, delim, out, st, cnt, stream);
+        cudaEventRecord(e1, stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) err = FP_ERR_CUDA;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) ms_min = std::min(ms_min, ms);
+      }
+      if (err != FP_OK) break;
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        best = c;
+      }
+    }
+  }
+  {
+    // release this temporary stream's scratch
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_scratch.find(std::make_pair(dev, stream));
+    if (it != g_scratch.end()) {
+      free_scratch(it->second);
+      g_scratch.erase(it);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamDestroy(stream);
+  cudaFree(out);
+  cudaFree(st);
+  cudaFree(cnt);
+  if (err != FP_OK) {
+    fp_set_config(&cur);
+    return err;
+  }
+  fp_set_config(&best);
+  if (chosen) *chosen = best;
+  if (cache_path) {
+    FILE* f = fopen(cache_path, "w");
+    if (f) {
+      fprintf(f,
+              "{\"gpu\": \"%s\", \"chunk_bytes\": %u, \"ctas_per_sm\": %u, \"fallback_queue\": %u, "
+              "\"ms\": %.6f, \"bytes\": %zu}\n",
+              gpu, best.chunk_bytes, best.ctas_per_sm, best.fallback_queue, best_ms, len);
+      fclose(f);
+    }
+  }
+  return FP_OK;
+}

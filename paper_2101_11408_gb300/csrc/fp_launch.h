@@ -1,0 +1,17 @@
+// fp_launch.h -- host-side entry points of the kernel translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "fp_types.cuh"
+
+namespace fp {
+
+cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream);
+int parse_smem_bytes(int chunk_bytes);
+cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm);
+
+cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream);
+int fallback_smem_bytes();
+cudaError_t fallback_occupancy(int* blocks_per_sm);
+
+}  // namespace fp

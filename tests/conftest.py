@@ -21,3 +21,7 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+# Generated workloads are cached for the session (git-ignored build folder).
+os.environ.setdefault("FP_WORKLOAD_CACHE", os.path.join(ROOT, "_build", "workloads"))
