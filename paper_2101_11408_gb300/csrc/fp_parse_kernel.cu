@@ -218,6 +218,9 @@ __global__ void __launch_bounds__(NT) parse_kernel(const LaunchParams p) {
           if (lo_in - 1 >= 0 && lo_in - 1 < 16) m |= 1u << (lo_in - 1);
           if (hi_in >= 0 && hi_in < 16) m |= 1u << hi_in;
         }
+        // the pad granule only contributes the boundary at c0-1: earlier ones
+        // close fields of the previous chunk and must not enter the list
+        if (j == 0) m &= 0x8000u;
         const long long ol = (c0 - 1) - x0, oh = lim - x0;
         uint32_t own;
         if (ol <= 0 && oh >= 16) {
