@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of bulk decimal-text -> binary64 parsing on one GB300 (or N).
+
+One step = one parse of the bulk mixed workload: 10,000,000 newline-separated
+numbers (about 188 MB of text; 40% uniform [0,1) at 17 significant digits,
+30% coordinates with 12-16 fractional digits, 20% integers in [0, 2^63),
+10% d.ddddE+-xxx with exponents in [-340, 320]) through fp_parse_f64, with
+the text already resident in device memory.  The whole-job value is GB/s of
+input text; `e2e` repeats the measurement through fp_parse_f64_host with the
+host<->device copies inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank parses its own independently seeded shard (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GB/s of decimal text parsed to binary64 (bit-exact); p50/p99 request latency"
+UNIT = "GB/s"
+WORKLOAD = ("bulk mixed text, 10M numbers newline-separated: 40% uniform [0,1) at 17 "
+            "significant digits, 30% coordinates (lat/lon, 12-16 fractional digits), 20% "
+            "integers in [0,2^63), 10% d.ddddE+-xxx with exponents in [-340,320]")
+FALLBACK_HBM_GBS = 6800.0
+L2_BYTES = 129 * 1000 * 1000
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_sha() -> str:
+    d = os.path.join(ROOT, "paper_2101_11408_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".inc")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, when that summary
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "%s_bulk_mixed_10m.md" % kernel)
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith("- "):
+                k, v = line.strip()[2:].split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha") != kernel_source_sha():
+        return None
+    try:
+        return int(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cut_at_line(text: bytes, nbytes: int) -> bytes:
+    if nbytes >= len(text):
+        return text
+    k = text.rfind(b"\n", 0, nbytes)
+    return text[:k] if k > 0 else text[:nbytes]
+
+
+def oracle_time(sample: bytes, threads: int) -> float:
+    import oracle
+    t = time.perf_counter()
+    oracle.parse_buffer(sample, b"\n", nthreads=threads)
+    return time.perf_counter() - t
+
+
+def cpu_baseline(text: bytes, target_bytes: int = 64 << 20) -> dict:
+    cores = os.cpu_count() or 1
+    sample = cut_at_line(text, target_bytes)
+    dt = oracle_time(sample, cores)
+    return {"value": len(sample) / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d bytes (%.1f MB, cut at a line break) of the bulk mixed "
+                      "workload, one pass, %d threads, %.2f s" % (len(sample), len(sample) / 1e6,
+                                                                  cores, dt)}
+
+
+def run_reference(args, world, rank) -> None:
+    """The oracle on the host cores, bounded samples of the same workload."""
+    if rank != 0:
+        return
+    from paper_2101_11408_gb300 import workloads
+    cores = os.cpu_count() or 1
+    text = workloads.bulk_mixed_text(args.n, workloads.SEED_BASE + 2)
+    calib = cut_at_line(text, 4 << 20)
+    rate = len(calib) / oracle_time(calib, cores)
+    per_step = int(min(64 << 20, max(1 << 20, rate * args.reference_seconds /
+                                     max(1, args.steps + args.warmup))))
+    sample = cut_at_line(text, per_step)
+    for _ in range(args.warmup):
+        oracle_time(sample, cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_time(sample, cores)
+    dt = time.perf_counter() - t
+    value = len(sample) * args.steps / dt / 1e9
+    desc = ("oracle (exact big-number C parser) on %d host threads; each step parses the "
+            "first %d bytes (cut at a line break) of the bulk mixed workload" % (cores, len(sample)))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "numbers": args.n,
+                                        "text_bytes": len(text)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, world, rank, dist) -> None:
+    import torch
+
+    import paper_2101_11408_gb300 as fp
+    from paper_2101_11408_gb300 import workloads
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fp._lib.load()
+    seed = workloads.SEED_BASE + 2 + 1000 * rank
+    t = time.perf_counter()
+    text = workloads.bulk_mixed_text(args.n, seed)
+    log("rank %d: generated %d bytes in %.1f s" % (rank, len(text), time.perf_counter() - t))
+    B = len(text)
+    host_text = torch.frombuffer(bytearray(text), dtype=torch.uint8)
+    d_text = host_text.to(dev)
+    out = torch.empty(B, dtype=torch.float64, device=dev)
+    st = torch.empty(B, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # one untimed parse, checked against the oracle on a prefix
+    fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+    torch.cuda.synchronize()
+    N = int(cnt.item())
+    check_fields = 0
+    if rank == 0 and not args.skip_check:
+        import oracle
+        prefix = cut_at_line(text, 4 << 20)
+        rb, rs = oracle.parse_buffer(prefix)
+        got = out[:rb.size].cpu().numpy().view(np.uint64)
+        gst = st[:rb.size].cpu().numpy()
+        if not (np.array_equal(got, rb) and np.array_equal(gst, rs)):
+            raise SystemExit("bench: GPU output differs from the oracle")
+        check_fields = int(rb.size)
+    if fp.get_error():
+        raise SystemExit("bench: device error flag set")
+
+    sampler = ClockSampler(local).start() if rank == 0 else None
+    for _ in range(args.warmup):
+        fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+    # keep the GPU busy for a second before timing so the clock samples
+    # describe the same steady state as the timed steps
+    t_end = time.perf_counter() + args.clock_settle
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+        torch.cuda.synchronize()
+
+    fp.timing_enable(True)
+    fp.timing_read(stream)  # reset the sums
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    kt = fp.timing_read(stream)
+    fp.timing_enable(False)
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    value = world * B * args.steps / (elapsed_ms / 1e3) / 1e9
+
+    # end to end: host text -> device, parse, results -> host, every step
+    e2e = None
+    if not args.skip_e2e:
+        h_text = host_text.pin_memory()
+        h_out = torch.empty(B, dtype=torch.float64).pin_memory()
+        h_st = torch.empty(B, dtype=torch.uint8).pin_memory()
+        steps = min(args.steps, args.e2e_steps)
+        for _ in range(min(args.warmup, 3)):
+            fp.parse_f64_host_into(h_text, h_out, h_st, stream=stream)
+        if dist is not None:
+            dist.barrier()
+        t = time.perf_counter()
+        n_host = 0
+        for _ in range(steps):
+            n_host = fp.parse_f64_host_into(h_text, h_out, h_st, stream=stream)
+        dt = time.perf_counter() - t
+        if dist is not None:
+            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        assert n_host == N
+        if rank == 0 and check_fields:
+            assert np.array_equal(h_out[:check_fields].numpy().view(np.uint64),
+                                  out[:check_fields].cpu().numpy().view(np.uint64))
+        e2e = {"value": world * B * steps / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": B, "d2h_bytes_per_step": 9 * N + 8, "steps": steps,
+               "api": "fp_parse_f64_host (pinned host buffers)"}
+
+    if rank != 0:
+        return
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = B + 9 * N
+    parse_ms = kt["parse_ms"] / max(kt["calls"], 1)
+    fb_ms = kt["fallback_ms"] / max(kt["calls"], 1)
+    achieved = alg_bytes / (parse_ms / 1e3) / 1e9
+    traffic = profiled_traffic("parse_kernel")
+    cfg = fp.get_config()
+    s = fp.stats(reset=True, stream=stream)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "numbers": N, "text_bytes": B,
+                   "mfloats_per_s": world * N * args.steps / (elapsed_ms / 1e3) / 1e6,
+                   "l2": "no flush: each step reads %.0f MB of text and writes %.0f MB of "
+                         "results, more than the %.0f MB L2" % (B / 1e6, 9 * N / 1e6, L2_BYTES / 1e6),
+                   "parallelism": "replicas: one independent shard per GPU",
+                   "chunk_bytes": cfg["chunk_bytes"], "ctas_per_sm": cfg["ctas_per_sm"],
+                   "checked_fields": check_fields},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "parse_kernel (fused index+parse+Algorithm 1)",
+                     "kernel_ms": parse_ms, "fallback_kernel_ms": fb_ms,
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "path_counts_per_step": {k: s[k] // max(s["calls"], 1) for k in (
+            "fields", "one_multiply", "two_multiplies", "general_tokenizer", "long_fields",
+            "long_settled", "fallback", "fallback_bignum")},
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.skip_baseline:
+        line["cpu_baseline"] = cpu_baseline(text)
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=10_000_000, help="numbers per shard")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--clock-settle", type=float, default=1.0,
+                    help="seconds of untimed steps before the timed region")
+    ap.add_argument("--reference-seconds", type=float, default=60.0,
+                    help="target duration of the reference arm's timed steps")
+    ap.add_argument("--skip-baseline", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-check", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -92,13 +92,14 @@ typedef struct {
     uint64_t calls;           /* parse calls queued on this stream              */
     uint64_t fields;          /* fields parsed                                   */
     uint64_t bytes;           /* text bytes parsed                               */
-    uint64_t one_multiply;    /* Algorithm 1 settled by one 64x64 product        */
-    uint64_t two_multiplies;  /* ... needed the second product (Section 7)       */
+    uint64_t one_multiply;    /* fast-path Algorithm 1 runs with one 64x64 product */
+    uint64_t two_multiplies;  /* Algorithm 1 runs that needed the second product   */
     uint64_t long_fields;     /* more than 19 significant digits (Section 10)    */
     uint64_t long_settled;    /* ... settled by the w / w+1 check                */
     uint64_t fallback;        /* fields resolved by the exact fallback kernel    */
     uint64_t fallback_bignum; /* ... that needed a big-number comparison         */
     uint64_t queue_overflow;  /* fallback fields found by scanning (queue full)  */
+    uint64_t general_tokenizer; /* fields that needed the general tokenizer       */
 } fp_stats_t;
 
 /*
@@ -192,6 +193,38 @@ FP_API fp_err_t fp_get_config(fp_config_t *cfg);
  */
 FP_API fp_err_t fp_autotune(const char *text, size_t len, char delim, const char *cache_path,
                      fp_config_t *chosen);
+
+/*
+ * fp_timing_enable -- when on != 0, later parse calls record CUDA events on
+ * their stream around each kernel they launch, and the library adds up the
+ * kernels' device time per stream without synchronising (events are
+ * harvested as they complete).  Off by default.
+ */
+FP_API fp_err_t fp_timing_enable(int on);
+
+/*
+ * fp_timing_read -- wait for the timed calls queued on `stream`, return the
+ * summed device time in milliseconds of their parse kernels (*parse_ms) and
+ * fallback kernels (*fallback_ms) and the number of calls (*calls), then
+ * reset the sums.  All three are host pointers.
+ */
+FP_API fp_err_t fp_timing_read(struct CUstream_st *stream, double *parse_ms,
+                               double *fallback_ms, uint64_t *calls);
+
+/*
+ * fp_parse_f64_host -- end-to-end parse of a HOST buffer.
+ *   host_text    host pointer to len bytes (pinned memory copies fastest)
+ *   host_f64     host array of at least fp_max_fields(len) doubles
+ *   host_status  host array of at least fp_max_fields(len) bytes
+ *   host_count   host pointer: the number of fields
+ * Copies the text to a per-stream device staging buffer, parses it there,
+ * reads the field count and copies back exactly that many results.
+ * Synchronous: returns after the results are in host memory.  The staging
+ * buffers are allocated with cudaMalloc on first use and grown as needed.
+ */
+FP_API fp_err_t fp_parse_f64_host(const char *host_text, size_t len, char delim,
+                                  double *host_f64, uint8_t *host_status, uint64_t *host_count,
+                                  struct CUstream_st *stream);
 
 /* fp_shutdown -- synchronise and free every stream's scratch. */
 FP_API fp_err_t fp_shutdown(void);

@@ -16,9 +16,9 @@ from . import _lib
 from ._lib import (STATUS_INVALID, STATUS_OK, STATUS_OVERFLOW, STATUS_UNDERFLOW, Config,
                    FpError, Stats)
 
-__all__ = ["parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_batch",
+__all__ = ["parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
            "parse_f64_batch_into", "max_fields", "stats", "get_error", "set_config",
-           "get_config", "autotune", "shutdown", "library_path", "FpError", "STATUS_OK",
+           "get_config", "autotune", "timing_enable", "timing_read", "shutdown", "library_path", "FpError", "STATUS_OK",
            "STATUS_INVALID", "STATUS_OVERFLOW", "STATUS_UNDERFLOW"]
 
 
@@ -90,22 +90,33 @@ def parse_f64(text: torch.Tensor, delim=b"\n", stream=None):
     return out[:n], st[:n]
 
 
-def parse_f64_host(data, delim=b"\n", device=None, stream=None):
-    """End-to-end path for host data: pinned host -> device copy, parse,
-    device -> host copy of the results.  Returns numpy (values, status)."""
+def parse_f64_host_into(host_text, host_f64, host_status, delim=b"\n", stream=None) -> int:
+    """End-to-end parse of host memory through the C ABI (fp_parse_f64_host):
+    host_text is a uint8 numpy array or CPU tensor (pinned copies fastest),
+    host_f64 / host_status receive the results.  Returns the field count."""
+    def ptr(a):
+        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+    n = host_text.numel() if isinstance(host_text, torch.Tensor) else host_text.size
+    cnt = ctypes.c_uint64()
+    rc = _lib.load().fp_parse_f64_host(ptr(host_text) if n else None, n, _delim_byte(delim),
+                                       ptr(host_f64) if n else None,
+                                       ptr(host_status) if n else None, ctypes.byref(cnt),
+                                       _stream_handle(stream))
+    _lib.check(rc, "fp_parse_f64_host")
+    return int(cnt.value)
+
+
+def parse_f64_host(data, delim=b"\n", stream=None):
+    """Parse host bytes end to end.  Returns numpy (values, status)."""
     if isinstance(data, (bytes, bytearray, memoryview)):
-        arr = np.frombuffer(bytes(data), dtype=np.uint8)
+        arr = np.frombuffer(bytearray(data), dtype=np.uint8)
     else:
         arr = np.ascontiguousarray(data, dtype=np.uint8)
-    device = torch.device(device or "cuda")
-    host = torch.from_numpy(arr).pin_memory() if arr.size else torch.empty(0, dtype=torch.uint8)
-    text = torch.empty(arr.size, dtype=torch.uint8, device=device)
-    s = stream if stream is not None else torch.cuda.current_stream(device)
-    with torch.cuda.stream(s):
-        if arr.size:
-            text.copy_(host, non_blocking=True)
-        vals, st = parse_f64(text, delim, stream=s)
-        return vals.cpu().numpy(), st.cpu().numpy()
+    cap = max(arr.size, 1)
+    vals = np.empty(cap, dtype=np.float64)
+    st = np.empty(cap, dtype=np.uint8)
+    n = parse_f64_host_into(arr, vals, st, delim, stream)
+    return vals[:n], st[:n]
 
 
 def parse_f64_batch_into(texts, out_f64: torch.Tensor, out_status: torch.Tensor,
@@ -188,6 +199,20 @@ def autotune(text: torch.Tensor, delim=b"\n", cache_path: str | None = None) -> 
                                        ctypes.byref(c)), "fp_autotune")
     return {"chunk_bytes": c.chunk_bytes, "ctas_per_sm": c.ctas_per_sm,
             "fallback_queue": c.fallback_queue}
+
+
+def timing_enable(on: bool = True) -> None:
+    """Record CUDA events around each kernel of later calls (see timing_read)."""
+    _lib.check(_lib.load().fp_timing_enable(int(on)), "fp_timing_enable")
+
+
+def timing_read(stream=None) -> dict:
+    """Summed device time of the kernels of the timed calls on `stream` since
+    the last read: {"parse_ms", "fallback_ms", "calls"} (waits for them)."""
+    a, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_uint64()
+    _lib.check(_lib.load().fp_timing_read(_stream_handle(stream), ctypes.byref(a),
+                                          ctypes.byref(b), ctypes.byref(n)), "fp_timing_read")
+    return {"parse_ms": a.value, "fallback_ms": b.value, "calls": int(n.value)}
 
 
 def shutdown() -> None:

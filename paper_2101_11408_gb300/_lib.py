@@ -17,14 +17,14 @@ STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
 
 # every symbol include/fpparse.h declares
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f64_batch", "fp_get_stats",
-           "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_shutdown",
-           "fp_strerror"]
+           "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
+           "fp_timing_read", "fp_parse_f64_host", "fp_shutdown", "fp_strerror"]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "calls", "fields", "bytes", "one_multiply", "two_multiplies", "long_fields",
-        "long_settled", "fallback", "fallback_bignum", "queue_overflow")]
+        "long_settled", "fallback", "fallback_bignum", "queue_overflow", "general_tokenizer")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -77,6 +77,14 @@ def load(build_if_missing: bool = True):
         lib.fp_autotune.argtypes = [vp, sz, ctypes.c_char, ctypes.c_char_p,
                                     ctypes.POINTER(Config)]
         lib.fp_autotune.restype = ctypes.c_int
+        lib.fp_timing_enable.argtypes = [ctypes.c_int]
+        lib.fp_timing_enable.restype = ctypes.c_int
+        lib.fp_timing_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_uint64)]
+        lib.fp_timing_read.restype = ctypes.c_int
+        lib.fp_parse_f64_host.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
+        lib.fp_parse_f64_host.restype = ctypes.c_int
         lib.fp_shutdown.argtypes = []
         lib.fp_shutdown.restype = ctypes.c_int
         lib.fp_strerror.argtypes = [ctypes.c_int]

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -26,13 +27,32 @@ constexpr unsigned long long MAX_LEN = 1ull << 40;
 constexpr uint32_t MAX_BUFS = 1u << 24;
 
 struct Config {
-  uint32_t chunk_bytes = 8192;
+  uint32_t chunk_bytes = 16384;
   uint32_t ctas_per_sm = 0;  // 0: as many as fit
   uint32_t fallback_queue = 1u << 20;
 };
 
+// Launch parameters; FP_CHUNK_BYTES, FP_CTAS_PER_SM and FP_FALLBACK_QUEUE in
+// the environment override the defaults when the library is loaded.
+Config initial_config() {
+  Config c;
+  if (const char* v = getenv("FP_CHUNK_BYTES")) {
+    unsigned long x = strtoul(v, nullptr, 10);
+    if (x == 4096 || x == 8192 || x == 16384) c.chunk_bytes = (uint32_t)x;
+  }
+  if (const char* v = getenv("FP_CTAS_PER_SM")) {
+    unsigned long x = strtoul(v, nullptr, 10);
+    if (x <= 8) c.ctas_per_sm = (uint32_t)x;
+  }
+  if (const char* v = getenv("FP_FALLBACK_QUEUE")) {
+    unsigned long x = strtoul(v, nullptr, 10);
+    if (x >= 1024 && x <= (1u << 28)) c.fallback_queue = (uint32_t)x;
+  }
+  return c;
+}
+
 std::mutex g_mu;
-Config g_cfg;
+Config g_cfg = initial_config();
 
 struct DeviceInfo {
   int sms = 0;
@@ -59,7 +79,22 @@ struct Scratch {
   bool desc_pending = false;
   unsigned int epoch = 1;
   unsigned long long calls = 0, bytes = 0;
+  // kernel timing (optional): a ring of event triples harvested as they complete
+  static constexpr int RING = 256;
+  cudaEvent_t ev[RING][3] = {};
+  bool ev_used[RING] = {};
+  int ev_head = 0;
+  double acc_parse_ms = 0, acc_fb_ms = 0;
+  unsigned long long acc_calls = 0;
+  // staging for fp_parse_f64_host
+  uint8_t* stage_text = nullptr;
+  double* stage_out = nullptr;
+  uint8_t* stage_status = nullptr;
+  unsigned long long* stage_count = nullptr;
+  size_t stage_cap = 0;
 };
+bool g_timing = false;
+
 std::map<std::pair<int, cudaStream_t>, Scratch*> g_scratch;
 
 #define FP_CUDA(x)                                  \
@@ -70,6 +105,23 @@ std::map<std::pair<int, cudaStream_t>, Scratch*> g_scratch;
       return FP_ERR_CUDA;                           \
     }                                               \
   } while (0)
+
+fp_err_t harvest(Scratch* s, int slot, bool wait) {
+  if (!s->ev_used[slot]) return FP_OK;
+  if (wait) {
+    FP_CUDA(cudaEventSynchronize(s->ev[slot][2]));
+  } else if (cudaEventQuery(s->ev[slot][2]) != cudaSuccess) {
+    return FP_OK;
+  }
+  float a = 0, b = 0;
+  FP_CUDA(cudaEventElapsedTime(&a, s->ev[slot][0], s->ev[slot][1]));
+  FP_CUDA(cudaEventElapsedTime(&b, s->ev[slot][1], s->ev[slot][2]));
+  s->acc_parse_ms += a;
+  s->acc_fb_ms += b;
+  s->acc_calls++;
+  s->ev_used[slot] = false;
+  return FP_OK;
+}
 
 fp_err_t device_info(int dev, DeviceInfo** out) {
   auto it = g_dev.find(dev);
@@ -103,6 +155,13 @@ void free_scratch(Scratch* s) {
   cudaFree(s->d_descs);
   cudaFreeHost(s->h_descs);
   if (s->desc_copied) cudaEventDestroy(s->desc_copied);
+  for (auto& tri : s->ev)
+    for (cudaEvent_t e : tri)
+      if (e) cudaEventDestroy(e);
+  cudaFree(s->stage_text);
+  cudaFree(s->stage_out);
+  cudaFree(s->stage_status);
+  cudaFree(s->stage_count);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
 }
@@ -205,8 +264,29 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
   unsigned long long grid = (unsigned long long)di.sms * per_sm;
   if (grid > total_chunks) grid = total_chunks;
+  const bool timing = g_timing;
+  int slot = -1;
+  if (timing) {
+    slot = s->ev_head;
+    s->ev_head = (s->ev_head + 1) % Scratch::RING;
+    fp_err_t e = harvest(s, slot, true);  // only blocks with RING calls in flight
+    if (e != FP_OK) return e;
+    if (!s->ev[slot][0])
+      for (cudaEvent_t& ev : s->ev[slot]) FP_CUDA(cudaEventCreate(&ev));
+    FP_CUDA(cudaEventRecord(s->ev[slot][0], stream));
+  }
   FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream));
+  if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
   FP_CUDA(fp::launch_fallback(p, di.sms * di.fb_occ, stream));
+  if (timing) {
+    FP_CUDA(cudaEventRecord(s->ev[slot][2], stream));
+    s->ev_used[slot] = true;
+    for (int k = 1; k <= 2; k++) {  // harvest a couple of older slots, non-blocking
+      int old = (slot - k + Scratch::RING) % Scratch::RING;
+      fp_err_t e = harvest(s, old, false);
+      if (e != FP_OK) return e;
+    }
+  }
   s->calls++;
   s->bytes += total_bytes;
   return FP_OK;
@@ -322,13 +402,14 @@ fp_err_t fp_get_stats(fp_stats_t* host_out, int reset, struct CUstream_st* strea
   host_out->calls = s->calls;
   host_out->bytes = s->bytes;
   host_out->fields = st[fp::CNT_FIELDS];
-  host_out->one_multiply = st[fp::CNT_ONE_MUL];
+  host_out->one_multiply = st[fp::CNT_EL] - std::min(st[fp::CNT_EL], st[fp::CNT_TWO_MUL]);
   host_out->two_multiplies = st[fp::CNT_TWO_MUL];
   host_out->long_fields = st[fp::CNT_LONG];
   host_out->long_settled = st[fp::CNT_LONG_SETTLED];
   host_out->fallback = st[fp::CNT_FALLBACK];
   host_out->fallback_bignum = st[fp::CNT_FALLBACK_BIGNUM];
   host_out->queue_overflow = st[fp::CNT_QUEUE_OVERFLOW];
+  host_out->general_tokenizer = st[fp::CNT_SLOW];
   if (reset) {
     FP_CUDA(cudaMemsetAsync(s->ctl->stats, 0, sizeof(st), stream));
     FP_CUDA(cudaStreamSynchronize(stream));
@@ -374,6 +455,81 @@ fp_err_t fp_get_config(fp_config_t* cfg) {
   cfg->chunk_bytes = g_cfg.chunk_bytes;
   cfg->ctas_per_sm = g_cfg.ctas_per_sm;
   cfg->fallback_queue = g_cfg.fallback_queue;
+  return FP_OK;
+}
+
+fp_err_t fp_timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_timing = on != 0;
+  return FP_OK;
+}
+
+fp_err_t fp_timing_read(struct CUstream_st* stream_, double* parse_ms, double* fallback_ms,
+                        uint64_t* calls) {
+  if (!parse_ms || !fallback_ms || !calls) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  *parse_ms = *fallback_ms = 0;
+  *calls = 0;
+  auto it = g_scratch.find(std::make_pair(dev, stream));
+  if (it == g_scratch.end()) return FP_OK;
+  Scratch* s = it->second;
+  for (int k = 0; k < Scratch::RING; k++) {
+    fp_err_t e = harvest(s, k, true);
+    if (e != FP_OK) return e;
+  }
+  *parse_ms = s->acc_parse_ms;
+  *fallback_ms = s->acc_fb_ms;
+  *calls = s->acc_calls;
+  s->acc_parse_ms = s->acc_fb_ms = 0;
+  s->acc_calls = 0;
+  return FP_OK;
+}
+
+fp_err_t fp_parse_f64_host(const char* host_text, size_t len, char delim, double* host_f64,
+                           uint8_t* host_status, uint64_t* host_count,
+                           struct CUstream_st* stream_) {
+  if (len >= MAX_LEN || !host_count) return FP_ERR_ARG;
+  if (len > 0 && (!host_text || !host_f64 || !host_status)) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Scratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    fp_err_t e = get_scratch(stream, 1, 1, g_cfg.fallback_queue, &s);
+    if (e != FP_OK) return e;
+    if (!s->stage_count) FP_CUDA(cudaMalloc(&s->stage_count, sizeof(unsigned long long)));
+    if (len > s->stage_cap) {
+      FP_CUDA(cudaStreamSynchronize(stream));
+      cudaFree(s->stage_text);
+      cudaFree(s->stage_out);
+      cudaFree(s->stage_status);
+      s->stage_text = nullptr;
+      s->stage_out = nullptr;
+      s->stage_status = nullptr;
+      s->stage_cap = 0;
+      FP_CUDA(cudaMalloc(&s->stage_text, len));
+      FP_CUDA(cudaMalloc(&s->stage_out, len * sizeof(double)));
+      FP_CUDA(cudaMalloc(&s->stage_status, len));
+      s->stage_cap = len;
+    }
+  }
+  if (len) FP_CUDA(cudaMemcpyAsync(s->stage_text, host_text, len, cudaMemcpyHostToDevice, stream));
+  fp_err_t e = fp_parse_f64(len ? (const char*)s->stage_text : nullptr, len, delim, s->stage_out,
+                            s->stage_status, (uint64_t*)s->stage_count, stream_);
+  if (e != FP_OK) return e;
+  unsigned long long n = 0;
+  FP_CUDA(cudaMemcpyAsync(&n, s->stage_count, sizeof(n), cudaMemcpyDeviceToHost, stream));
+  FP_CUDA(cudaStreamSynchronize(stream));
+  if (n > len) return FP_ERR_INTERNAL;
+  if (n) {
+    FP_CUDA(cudaMemcpyAsync(host_f64, s->stage_out, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream));
+    FP_CUDA(cudaMemcpyAsync(host_status, s->stage_status, n, cudaMemcpyDeviceToHost, stream));
+  }
+  FP_CUDA(cudaStreamSynchronize(stream));
+  *host_count = n;
   return FP_OK;
 }
 

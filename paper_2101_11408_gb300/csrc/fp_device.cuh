@@ -29,6 +29,7 @@ enum : uint8_t {
   ST_PENDING = 0xFF,         // internal result of the short-field parser
   ST_PENDING_QUEUED = 0xFE,  // stored status: pending, listed in the fallback queue
   ST_PENDING_SCAN = 0xFF,    // stored status: pending, found by scanning its chunk
+  ST_GENERAL = 0xFD,         // staged only: the general tokenizer must decide
 };
 
 constexpr uint64_t QNAN_BITS = 0x7FF8000000000000ull;
@@ -46,13 +47,14 @@ constexpr uint32_t DERR_INTERNAL = 6;
 // Counters kept per CTA and added to the stream's totals.
 enum {
   CNT_FIELDS = 0,
-  CNT_ONE_MUL,
+  CNT_EL,       // Algorithm 1 evaluations on the fast tokenizer's output
   CNT_TWO_MUL,
   CNT_LONG,
   CNT_LONG_SETTLED,
   CNT_FALLBACK,
   CNT_FALLBACK_BIGNUM,
   CNT_QUEUE_OVERFLOW,
+  CNT_SLOW,     // fields that needed the general tokenizer
   CNT_NUM
 };
 
@@ -157,20 +159,15 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const uint64_t* tab,
   return r;
 }
 
-// Quick exits of Algorithm 1 plus the product, for w != 0.
-FP_HD ElResult convert_wq(uint64_t w, int64_t q, const uint64_t* tab,
-                                               bool allow_abort) {
-  ElResult r;
-  r.two_mul = 0;
-  if (q < FP_POW5_QMIN) {
-    r.bits = 0;
-    return r;
-  }
-  if (q > FP_POW5_QMAX) {
-    r.bits = INF_BITS;
-    return r;
-  }
-  return eisel_lemire(w, (int)q, tab, allow_abort);
+// Quick exits of Algorithm 1 plus the product, for w != 0.  The product is
+// formed with q clamped to the table's range and the exits applied after,
+// so that the code has no data-dependent branch around the table access.
+FP_HD ElResult convert_wq(uint64_t w, int64_t q, const uint64_t* tab, bool allow_abort) {
+  const int qc = q < FP_POW5_QMIN ? FP_POW5_QMIN : (q > FP_POW5_QMAX ? FP_POW5_QMAX : (int)q);
+  ElResult r = eisel_lemire(w, qc, tab, allow_abort);
+  if (q < FP_POW5_QMIN) r.bits = 0;
+  if (q > FP_POW5_QMAX) r.bits = INF_BITS;
+  return r;
 }
 
 FP_HD uint8_t status_of(uint64_t pos_bits) {
@@ -298,6 +295,194 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n,
   r.bits = a.bits | sign;
   r.status = status_of(a.bits);
   return r;
+}
+
+
+// ---------------------------------------------------------------------------
+// SWAR fast path (Section 4; eight digits at a time as in the appendix's
+// string functions, with GPU byte-dot-product instructions for the values)
+// ---------------------------------------------------------------------------
+
+// (hi:lo) >> sh for sh in [0, 31].
+FP_HD uint32_t fshr(uint32_t lo, uint32_t hi, uint32_t sh) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_r(lo, hi, sh);
+#else
+  return (uint32_t)((((uint64_t)hi << 32) | lo) >> (sh & 31));
+#endif
+}
+
+FP_HD int ctz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __ffs(x) - 1;
+#else
+  return __builtin_ctz(x);
+#endif
+}
+
+FP_HD int ctz64(uint64_t x) {
+#ifdef __CUDA_ARCH__
+  return __ffsll((long long)x) - 1;
+#else
+  return __builtin_ctzll(x);
+#endif
+}
+
+// Value of four ASCII digits, the first byte (lowest address) most
+// significant: 1000 b0 + 100 b1 + 10 b2 + b3 - 1111 * '0'.
+FP_HD uint32_t dig4(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __dp2a_hi(0x0001000Au, x, __dp2a_lo(0x006403E8u, x, 0u - 53328u));
+#else
+  return 1000u * (x & 0xFF) + 100u * ((x >> 8) & 0xFF) + 10u * ((x >> 16) & 0xFF) + (x >> 24) -
+         53328u;
+#endif
+}
+
+FP_HD uint32_t dig8(uint32_t a, uint32_t b) { return dig4(a) * 10000u + dig4(b); }
+
+// 0x80 in the first byte of x that is not an ASCII digit.  Only that first
+// flag is exact (a borrow or carry out of a non-digit byte may mark later
+// bytes), which is all the callers use.
+FP_HD uint32_t nondigit_flags(uint32_t x) {
+  return ((x + 0x46464646u) | (x - 0x30303030u)) & 0x80808080u;
+}
+
+// (hi:lo) << n, upper word, n clamped to [0, 32]: ~0u << n for lo=0, hi=~0.
+FP_HD uint32_t fshl_clamp(uint32_t lo, uint32_t hi, uint32_t n) {
+#ifdef __CUDA_ARCH__
+  return __funnelshift_lc(lo, hi, n);
+#else
+  n = n > 32 ? 32 : n;
+  return (uint32_t)(((((uint64_t)hi << 32) | lo) << n) >> 32);
+#endif
+}
+
+// Byte permute: byte i of the result is byte ((sel >> 4i) & 7) of (y:x).
+FP_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t sel) {
+#ifdef __CUDA_ARCH__
+  return __byte_perm(x, y, sel);
+#else
+  const uint64_t v = ((uint64_t)y << 32) | x;
+  uint32_t r = 0;
+  for (int i = 0; i < 4; i++) r |= (uint32_t)((v >> (8 * ((sel >> (4 * i)) & 7))) & 0xFF) << (8 * i);
+  return r;
+#endif
+}
+
+FP_HD int clz32(uint32_t x) {
+#ifdef __CUDA_ARCH__
+  return __clz(x);
+#else
+  return x ? __builtin_clz(x) : 32;
+#endif
+}
+
+// 0x80 in every byte of t that is zero, exactly.
+FP_HD uint32_t zero_bytes(uint32_t t) {
+  return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+
+struct FastToken {
+  uint64_t w;     // decimal significand (< 10^19)
+  int q;          // decimal exponent
+  uint64_t sign;
+};
+
+// Straight-line tokenizer for the common field shape
+//     [+-] digits-with-at-most-one-'.' [ [eE] [+-] d{1,4} ]
+// with at most 24 significand characters whose value stays below 10^19
+// (Section 4).  s is the field's first byte and e its terminator (both tile
+// offsets; the bytes in [s, e) are text).  The significand is read as one
+// 24-byte window ending where it ends, so every field of this shape runs the
+// same instructions: the point is found with an exact byte test and removed
+// by a byte permute, bytes before the significand become '0', and the 20
+// low digits are converted four at a time.  Returns false for anything
+// else; the general tokenizer then decides (with identical results for the
+// shapes accepted here).  tile is 4-byte aligned; reads may touch up to 8
+// bytes before s and 8 after e.
+FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
+  const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
+  auto load4 = [&](int p) -> uint32_t {
+    const int i = p >> 2;  // floor, also for negative p
+    return fshr(t32[i], t32[i + 1], (uint32_t)(p & 3) * 8);
+  };
+  if (e - s < 1 || e - s > 30) return false;
+  const uint32_t c0 = tile[s];
+  t.sign = (c0 == '-') ? SIGN_BIT : 0;
+  const int s1 = s + ((c0 == '-') | (c0 == '+'));
+  // exponent: the last 'e' or 'E' among bytes e-5 .. e-2
+  int sig_end = e;
+  int ex = 0;
+  {
+    const uint32_t Q = load4(e - 5);
+    const uint32_t ez = zero_bytes((Q | 0x20202020u) ^ 0x65656565u);
+    const int ep = e - 5 + ((31 - clz32(ez)) >> 3);
+    if (ez && ep > s1) {
+      const uint32_t cs = tile[ep + 1];
+      const int sg = (cs == '-') | (cs == '+');
+      const int ne = e - ep - 1 - sg;  // exponent digits, at most 4
+      if (ne < 1) return false;
+      const uint32_t keep = 0xFFFFFFFFu << (8 * (4 - ne));
+      const uint32_t R = (load4(e - 4) & keep) | (0x30303030u & ~keep);
+      if (nondigit_flags(R)) return false;
+      ex = (int)dig4(R);
+      if (cs == '-') ex = -ex;
+      sig_end = ep;
+    }
+  }
+  const int Ls = sig_end - s1;  // significand characters, point included
+  if (Ls < 1 || Ls > 24) return false;
+  // the 24-byte window [sig_end - 24, sig_end)
+  const int w0 = sig_end - 24;
+  const int i0 = w0 >> 2;
+  const uint32_t sh = (uint32_t)(w0 & 3) * 8;
+  uint32_t x[6];
+  {
+    uint32_t W[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) W[j] = t32[i0 + j];
+#pragma unroll
+    for (int j = 0; j < 6; j++) x[j] = fshr(W[j], W[j + 1], sh);
+  }
+  // the last '.' of the window; one before the significand is not ours
+  int dpos = -1;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    const uint32_t dz = zero_bytes(x[j] ^ 0x2E2E2E2Eu);
+    if (dz) dpos = 4 * j + ((31 - clz32(dz)) >> 3);
+  }
+  const int tsig = 24 - Ls;  // window index of the first significand byte
+  if (dpos < tsig) dpos = -1;
+  // bytes before the significand become '0'; then the bytes up to the point
+  // move one place toward the end, over it (a '0' enters at the front)
+  uint32_t prev = 0x30303030u;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    const int fill = 8 * (tsig - 4 * j);
+    const uint32_t m = fshl_clamp(0u, 0xFFFFFFFFu, (uint32_t)(fill > 0 ? fill : 0));
+    const uint32_t xj = (x[j] & m) | (0x30303030u & ~m);
+    int c = dpos + 1 - 4 * j;  // bytes of word j at or before the point
+    c = c < 0 ? 0 : (c > 4 ? 4 : c);
+    const uint32_t M = 0xFFFFu >> (16 - 4 * c);
+    const uint32_t sel = (0x6543u & M) | (0x7654u & ~M);
+    x[j] = byte_perm(prev, xj, sel);
+    prev = xj;
+  }
+  // all 24 bytes must be digits, and the four above the 20-digit frame plus
+  // its first one zero, so that the value is below 10^19
+  uint32_t bad = 0;
+#pragma unroll
+  for (int j = 0; j < 6; j++) bad |= nondigit_flags(x[j]);
+  if (bad || x[0] != 0x30303030u || (x[1] & 0xFFu) != 0x30u) return false;
+  if (Ls - (dpos >= 0) < 1) return false;  // no digit at all
+  uint64_t w = dig4(x[1]) * 10000u + dig4(x[2]);
+  w = w * 10000u + dig4(x[3]);
+  w = w * 10000u + dig4(x[4]);
+  w = w * 10000u + dig4(x[5]);
+  t.w = w;
+  t.q = ex - (dpos >= 0 ? 23 - dpos : 0);
+  return true;
 }
 
 }  // namespace fp

@@ -406,8 +406,14 @@ __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
 int fallback_smem_bytes() { return 3 * LIMBS * FB_NT * 4; }
 
 cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream) {
-  cudaFuncSetAttribute(fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       fallback_smem_bytes());
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(fallback_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         fallback_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   fallback_kernel<<<grid, FB_NT, fallback_smem_bytes(), stream>>>(p);
   return cudaGetLastError();
 }

@@ -7,6 +7,17 @@ namespace fp {
 // ---------------------------------------------------------------------------
 // memory-order helpers for the cross-CTA look-back
 // ---------------------------------------------------------------------------
+// Relaxed (no fence) device-scope store / load: for self-contained values
+// such as the look-back words, whose readers need no other data ordered
+// with them.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
