@@ -226,6 +226,32 @@ FP_API fp_err_t fp_parse_f64_host(const char *host_text, size_t len, char delim,
                                   double *host_f64, uint8_t *host_status, uint64_t *host_count,
                                   struct CUstream_st *stream);
 
+/*
+ * fp_parse_f64_noalloc -- fp_parse_f64 for callers that must not allocate.
+ *   (The paper has no counterpart: this is a deployment variant of the same
+ *   parse.)  Same arguments, results and asynchrony as fp_parse_f64, but no
+ *   call ever allocates memory: the scratch of the two kernels lives in one
+ *   fixed 2 MiB + 256 B device array inside the library, which every GPU that
+ *   loads the library holds until the process exits.  It is for callers that
+ *   may not allocate once running -- fixed-memory or certified processes,
+ *   plugins whose host owns all allocations, services that must not fail on
+ *   an allocation mid-request.
+ *   Limits: at most 65,536 chunks of the current chunk size (len + (text % 16)
+ *   <= 65,536 * chunk_bytes: 1 GiB at the default 16 KiB chunks); beyond that
+ *   it returns FP_ERR_CAPACITY and queues nothing.  The first call on each
+ *   device looks up the array's device address (cudaGetSymbolAddress) and the
+ *   launch shape; make that first call before capturing the stream into a
+ *   CUDA graph.
+ *   Every call on every stream shares the one array and clears its control
+ *   part on `stream` first: calls whose work overlaps on the GPU (different
+ *   streams without ordering) race and give wrong results.  Order them, or
+ *   use fp_parse_f64.  Device-side error conditions of these calls are not
+ *   reported (fp_get_error does not see them); path counters are not kept.
+ */
+FP_API fp_err_t fp_parse_f64_noalloc(const char *text, size_t len, char delim, double *out_f64,
+                                     uint8_t *out_status, uint64_t *out_count,
+                                     struct CUstream_st *stream);
+
 /* fp_shutdown -- synchronise and free every stream's scratch. */
 FP_API fp_err_t fp_shutdown(void);
 

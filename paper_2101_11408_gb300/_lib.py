@@ -18,7 +18,8 @@ STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
 # every symbol include/fpparse.h declares
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
-           "fp_timing_read", "fp_parse_f64_host", "fp_shutdown", "fp_strerror"]
+           "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_shutdown",
+           "fp_strerror"]
 
 
 class Stats(ctypes.Structure):
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = True):
         lib.fp_timing_read.restype = ctypes.c_int
         lib.fp_parse_f64_host.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
         lib.fp_parse_f64_host.restype = ctypes.c_int
+        lib.fp_parse_f64_noalloc.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
+        lib.fp_parse_f64_noalloc.restype = ctypes.c_int
         lib.fp_shutdown.argtypes = []
         lib.fp_shutdown.restype = ctypes.c_int
         lib.fp_strerror.argtypes = [ctypes.c_int]
