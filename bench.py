@@ -54,13 +54,17 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+PARSE_KERNEL_SOURCES = ("fp_parse_kernel.cu", "fp_device.cuh", "fp_sync.cuh", "fp_types.cuh",
+                        "pow5_table.inc")
+
+
 def kernel_source_sha() -> str:
+    """Hash of the sources the parse kernel is compiled from."""
     d = os.path.join(ROOT, "paper_2101_11408_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
-        if name.endswith((".cu", ".cuh", ".h", ".inc")):
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in PARSE_KERNEL_SOURCES:
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
