@@ -38,7 +38,7 @@ Config initial_config() {
   Config c;
   if (const char* v = getenv("FP_CHUNK_BYTES")) {
     unsigned long x = strtoul(v, nullptr, 10);
-    if (x == 4096 || x == 8192 || x == 16384) c.chunk_bytes = (uint32_t)x;
+    if (x == 4096 || x == 8192 || x == 12288 || x == 16384) c.chunk_bytes = (uint32_t)x;
   }
   if (const char* v = getenv("FP_CTAS_PER_SM")) {
     unsigned long x = strtoul(v, nullptr, 10);
@@ -131,7 +131,7 @@ fp_err_t device_info(int dev, DeviceInfo** out) {
     FP_CUDA(cudaGetDeviceProperties(&prop, dev));
     di.sms = prop.multiProcessorCount;
     snprintf(di.name, sizeof(di.name), "%s", prop.name);
-    for (int c : {4096, 8192, 16384}) {
+    for (int c : {4096, 8192, 12288, 16384}) {
       int occ = 0;
       FP_CUDA(fp::parse_occupancy(c, &occ));
       di.parse_occ[c] = std::max(occ, 1);
@@ -438,7 +438,8 @@ fp_err_t fp_get_error(struct CUstream_st* stream_) {
 
 fp_err_t fp_set_config(const fp_config_t* cfg) {
   if (!cfg) return FP_ERR_ARG;
-  if (cfg->chunk_bytes != 4096 && cfg->chunk_bytes != 8192 && cfg->chunk_bytes != 16384)
+  if (cfg->chunk_bytes != 4096 && cfg->chunk_bytes != 8192 && cfg->chunk_bytes != 12288 &&
+      cfg->chunk_bytes != 16384)
     return FP_ERR_ARG;
   if (cfg->ctas_per_sm > 8) return FP_ERR_ARG;
   if (cfg->fallback_queue < 1024 || cfg->fallback_queue > (1u << 28)) return FP_ERR_ARG;
@@ -625,7 +626,7 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
   fp_config_t best = cur;
   float best_ms = 1e30f;
   fp_err_t err = FP_OK;
-  for (uint32_t chunk : {4096u, 8192u, 16384u}) {
+  for (uint32_t chunk : {8192u, 12288u, 16384u}) {
     for (uint32_t per_sm : {1u, 2u, 3u, 4u, 0u}) {
       fp_config_t c = cur;
       c.chunk_bytes = chunk;

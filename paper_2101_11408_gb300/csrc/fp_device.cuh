@@ -82,6 +82,24 @@ FP_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 // ---------------------------------------------------------------------------
 // Algorithm 1
 // ---------------------------------------------------------------------------
+// The power-of-five table as the kernels see it: the high words, possibly a
+// dense copy in shared memory (hi_stride 1) or the interleaved table itself
+// (hi_stride 2), and the low words read from the interleaved table (only
+// needed for the second product, Section 7).
+struct Pow5 {
+  const uint64_t* hi;
+  int hi_stride;
+  const uint64_t* lo;  // &table[1]: the low word of entry i is lo[2 i]
+};
+
+FP_HD uint64_t load_lo(const uint64_t* p) {
+#ifdef __CUDA_ARCH__
+  return __ldg(reinterpret_cast<const unsigned long long*>(p));
+#else
+  return *p;
+#endif
+}
+
 struct ElResult {
   uint64_t bits;  // positive binary64 pattern, or EL_ABORT
   int two_mul;    // 1 if the second 64x64 product was needed
@@ -92,21 +110,20 @@ struct ElResult {
 // product even where Algorithm 1 would give up; that value is then within
 // one unit in the last place of the correct result (the fallback kernel
 // uses it as its first candidate).
-FP_HD ElResult eisel_lemire(uint64_t w, int q, const uint64_t* tab,
-                                                 bool allow_abort) {
+FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort) {
   ElResult r;
   r.two_mul = 0;
   // Normalise the decimal significand into [2^63, 2^64) (Section 7).
   int l = clz64(w);
   w <<= l;
-  const uint64_t thi = tab[2 * (q - FP_POW5_QMIN)];
+  const uint64_t thi = tab.hi[(q - FP_POW5_QMIN) * tab.hi_stride];
   // z = (T[q] * w) / 2^64, truncated: first the product with the high word.
   uint64_t lo = w * thi;
   uint64_t hi = mulhi64(w, thi);
   // Unless the low 9 bits of the high word are all ones, the top 55 bits
   // are exact and one product suffices (Sections 7 and 8).
   if ((hi & 0x1FF) == 0x1FF) {
-    const uint64_t tlo = tab[2 * (q - FP_POW5_QMIN) + 1];
+    const uint64_t tlo = load_lo(tab.lo + 2 * (q - FP_POW5_QMIN));
     uint64_t h2 = mulhi64(w, tlo);
     lo += h2;
     hi += (lo < h2);
@@ -162,7 +179,7 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const uint64_t* tab,
 // Quick exits of Algorithm 1 plus the product, for w != 0.  The product is
 // formed with q clamped to the table's range and the exits applied after,
 // so that the code has no data-dependent branch around the table access.
-FP_HD ElResult convert_wq(uint64_t w, int64_t q, const uint64_t* tab, bool allow_abort) {
+FP_HD ElResult convert_wq(uint64_t w, int64_t q, const Pow5& tab, bool allow_abort) {
   const int qc = q < FP_POW5_QMIN ? FP_POW5_QMIN : (q > FP_POW5_QMAX ? FP_POW5_QMAX : (int)q);
   ElResult r = eisel_lemire(w, qc, tab, allow_abort);
   if (q < FP_POW5_QMIN) r.bits = 0;
@@ -195,8 +212,7 @@ struct FieldResult {
 // and feed a sticky flag.  With a nonzero sticky flag the value lies in
 // (w 10^q, (w+1) 10^q), and if both ends round to the same double that is
 // the answer (Section 10); otherwise the field is left pending.
-FP_HD FieldResult parse_short_field(const uint8_t* s, int n,
-                                                         const uint64_t* tab) {
+FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   FieldResult r;
   r.two_mul = 0;
   r.is_long = 0;
@@ -445,27 +461,34 @@ FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
 #pragma unroll
     for (int j = 0; j < 6; j++) x[j] = fshr(W[j], W[j + 1], sh);
   }
-  // the last '.' of the window; one before the significand is not ours
-  int dpos = -1;
-#pragma unroll
-  for (int j = 0; j < 6; j++) {
-    const uint32_t dz = zero_bytes(x[j] ^ 0x2E2E2E2Eu);
-    if (dz) dpos = 4 * j + ((31 - clz32(dz)) >> 3);
-  }
+  // bytes before the significand become '0'
   const int tsig = 24 - Ls;  // window index of the first significand byte
-  if (dpos < tsig) dpos = -1;
-  // bytes before the significand become '0'; then the bytes up to the point
-  // move one place toward the end, over it (a '0' enters at the front)
-  uint32_t prev = 0x30303030u;
 #pragma unroll
   for (int j = 0; j < 6; j++) {
     const int fill = 8 * (tsig - 4 * j);
     const uint32_t m = fshl_clamp(0u, 0xFFFFFFFFu, (uint32_t)(fill > 0 ? fill : 0));
-    const uint32_t xj = (x[j] & m) | (0x30303030u & ~m);
+    x[j] = (x[j] & m) | (0x30303030u & ~m);
+  }
+  // the point: the first non-digit of the window (the first flagged byte of
+  // a word is exact); anything else that is not a digit, or a second point,
+  // is still there after the point is removed and fails the check below
+  int dpos = -1;
+#pragma unroll
+  for (int j = 5; j >= 0; j--) {
+    const uint32_t f = nondigit_flags(x[j]);
+    if (f) dpos = 4 * j + (ctz32(f) >> 3);
+  }
+  if (dpos >= 0 && tile[w0 + dpos] != '.') return false;  // (dpos >= tsig: text byte)
+  // the bytes up to the point move one place toward the end, over it (a '0'
+  // enters at the front)
+  uint32_t prev = 0x30303030u;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
     int c = dpos + 1 - 4 * j;  // bytes of word j at or before the point
     c = c < 0 ? 0 : (c > 4 ? 4 : c);
     const uint32_t M = 0xFFFFu >> (16 - 4 * c);
     const uint32_t sel = (0x6543u & M) | (0x7654u & ~M);
+    const uint32_t xj = x[j];
     x[j] = byte_perm(prev, xj, sel);
     prev = xj;
   }

@@ -143,7 +143,7 @@ __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c ==
 
 // Parse one field starting at f (at most lim bytes remain in the buffer).
 __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim, uint32_t delim,
-                                       const uint64_t* tab, Big D, Big P, Big B) {
+                                       const Pow5& tab, Big D, Big P, Big B) {
   LongResult r;
   r.bignum = 0;
   r.error = 0;
@@ -341,8 +341,8 @@ __device__ __forceinline__ void resolve(const LaunchParams& p, unsigned long lon
     return;
   }
   const uint8_t* f = d.base + d.o + off;
-  LongResult r = parse_long_field(f, d.len - off, p.delim & 0xFFu,
-                                  reinterpret_cast<const uint64_t*>(fp_pow5_table_dev), D, P, B);
+  const uint64_t* t = reinterpret_cast<const uint64_t*>(fp_pow5_table_dev);
+  LongResult r = parse_long_field(f, d.len - off, p.delim & 0xFFu, Pow5{t, 2, t + 1}, D, P, B);
   if (r.error) atomicCAS(&p.ctl->error, 0u, DERR_INTERNAL);
   p.out_bits[oi] = r.bits;
   p.out_status[oi] = r.status;

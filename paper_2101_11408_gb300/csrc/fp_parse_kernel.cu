@@ -44,7 +44,7 @@ struct Layout {
   static constexpr int TILE_ALLOC = (TILE + 16 + 127) / 128 * 128;  // + over-read slack
   static constexpr int SEG_PER_THREAD = C / 16 / NT;  // 16-byte granules per thread
   static constexpr int S_CAP = STAGE;  // field starts listed at a time (denser chunks: windows)
-  static constexpr int TABLE_BYTES = 2 * FP_POW5_ENTRIES * 8;
+  static constexpr int TABLE_BYTES = FP_POW5_ENTRIES * 8;  // high words only
   static constexpr int OFF_TABLE = 0;
   static constexpr int OFF_TILE = (TABLE_BYTES + 127) / 128 * 128;
   static constexpr int OFF_S = OFF_TILE + NSTAGE * TILE_ALLOC;
@@ -207,12 +207,11 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       }
     }
   }
-  // The power-of-five table, once per block (Appendix table; 10,416 bytes).
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(fp_pow5_table_dev);
-    uint4* dst = reinterpret_cast<uint4*>(table);
-    for (int i = tid; i < FP_POW5_ENTRIES; i += NT) dst[i] = src[i];
-  }
+  // The high words of the power-of-five table, once per block (Appendix
+  // table; 5,208 bytes); the low words, needed only for a second product,
+  // are read from global memory.
+  for (int i = tid; i < FP_POW5_ENTRIES; i += NT) table[i] = fp_pow5_table_dev[2 * i];
+  const Pow5 pow5{table, 1, reinterpret_cast<const uint64_t*>(fp_pow5_table_dev) + 1};
   __syncthreads();
 
   // path counters of the current chunk (flushed to shared memory per chunk)
@@ -405,7 +404,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       ft.w = 0;
       ft.q = 0;
       const bool ok = parse_fast(tile, s, e, ft);
-      const ElResult r = convert_wq(ft.w ? ft.w : 1ull, ok ? ft.q : 0, table, true);
+      const ElResult r = convert_wq(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
       c_el += ok;
       c_two += ok & (uint32_t)r.two_mul;
       bits = ft.w ? (r.bits | ft.sign) : ft.sign;
@@ -417,7 +416,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     auto parse_general = [&](int s, int e, unsigned long long& bits, uint8_t& status) {
       if (e - s <= LMAX) {
         c_slow++;
-        const FieldResult r = parse_short_field(tile + s, e - s, table);
+        const FieldResult r = parse_short_field(tile + s, e - s, pow5);
         c_two += r.two_mul;
         c_long += r.is_long;
         c_long_ok += r.long_settled;
@@ -567,6 +566,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
 
 template __global__ void parse_kernel<4096>(const LaunchParams);
 template __global__ void parse_kernel<8192>(const LaunchParams);
+template __global__ void parse_kernel<12288>(const LaunchParams);
 template __global__ void parse_kernel<16384>(const LaunchParams);
 
 template <int C>
@@ -587,6 +587,7 @@ cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaS
   switch (chunk_bytes) {
     case 4096: return launch_parse_c<4096>(p, grid, stream);
     case 8192: return launch_parse_c<8192>(p, grid, stream);
+    case 12288: return launch_parse_c<12288>(p, grid, stream);
     case 16384: return launch_parse_c<16384>(p, grid, stream);
     default: return cudaErrorInvalidValue;
   }
@@ -596,6 +597,7 @@ int parse_smem_bytes(int chunk_bytes) {
   switch (chunk_bytes) {
     case 4096: return Layout<4096>::TOTAL;
     case 8192: return Layout<8192>::TOTAL;
+    case 12288: return Layout<12288>::TOTAL;
     case 16384: return Layout<16384>::TOTAL;
     default: return -1;
   }
@@ -614,6 +616,7 @@ cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm) {
   switch (chunk_bytes) {
     case 4096: return occupancy_c<4096>(blocks_per_sm);
     case 8192: return occupancy_c<8192>(blocks_per_sm);
+    case 12288: return occupancy_c<12288>(blocks_per_sm);
     case 16384: return occupancy_c<16384>(blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }

@@ -123,7 +123,7 @@ def test_unaligned_pointers_and_guard_bytes():
             assert_parity(text[:cut], offset=offset)
 
 
-@pytest.mark.parametrize("chunk", [4096, 8192, 16384])
+@pytest.mark.parametrize("chunk", [4096, 8192, 12288, 16384])
 def test_fields_straddling_chunks(chunk):
     before = fp.get_config()
     try:
@@ -211,7 +211,7 @@ def test_queue_overflow_path():
         fp.set_config(**before)
 
 
-@pytest.mark.parametrize("chunk", [4096, 8192, 16384])
+@pytest.mark.parametrize("chunk", [4096, 8192, 12288, 16384])
 @pytest.mark.parametrize("per_sm", [1, 0])
 def test_launch_configurations(chunk, per_sm):
     before = fp.get_config()
@@ -333,7 +333,7 @@ def test_autotune_picks_a_valid_config(tmp_path):
         t = to_device(workloads.bulk_mixed_text(200000, 81))
         path = str(tmp_path / "tune.json")
         c = fp.autotune(t, cache_path=path)
-        assert c["chunk_bytes"] in (4096, 8192, 16384)
+        assert c["chunk_bytes"] in (4096, 8192, 12288, 16384)
         assert os.path.exists(path)
         fp.set_config(**before)
         c2 = fp.autotune(t, cache_path=path)  # loaded from the cache
