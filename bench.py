@@ -342,6 +342,202 @@ def run_ours(args, world, rank, dist) -> None:
     print(json.dumps(line), flush=True)
 
 
+BATCH_WORKLOAD = ("batched: 4096 independent newline-separated buffers of uniform [0,1) %.17g "
+                  "values, sizes lognormal (sigma 2) clipped to [1 KiB, 64 MiB], about 2 GiB in "
+                  "total, packed in one allocation with every start alignment mod 16")
+
+
+def _time_steps(torch, stream, fn, steps: int, warmup: int) -> float:
+    """ms per step of fn() on `stream`, CUDA events, after warm-up."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_batch(args, world, rank, dist) -> None:
+    """Many uneven buffers in one persistent launch, replayed from a CUDA
+    graph, against the same buffers with one launch per buffer."""
+    import torch
+
+    import paper_2101_11408_gb300 as fp
+    from paper_2101_11408_gb300 import workloads
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fp._lib.load()
+    t = time.perf_counter()
+    texts = workloads.batch_buffers(args.nbuf, args.batch_bytes,
+                                    seed=workloads.SEED_BASE + 4 + 1000 * rank)
+    packed, starts = workloads.pack_buffers(texts)
+    lens = [len(x) for x in texts]
+    B = sum(lens)
+    log("rank %d: %d buffers, %d bytes in %.1f s" % (rank, len(texts), B, time.perf_counter() - t))
+    h_packed = torch.from_numpy(packed).pin_memory()
+    d_packed = h_packed.to(dev)
+    views = [d_packed[s:s + n] for s, n in zip(starts, lens)]
+    offs = [0]
+    for n in lens:
+        offs.append(offs[-1] + n)
+    cap = max(offs[-1], 1)
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+    st = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(len(texts), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    # autotune the chunk size and blocks per SM on the largest buffer
+    big = max(range(len(texts)), key=lambda b: lens[b])
+    tuned = fp.autotune(views[big])
+
+    # the per-buffer form writes its own copy of the results, compared below
+    out1 = torch.empty(cap, dtype=torch.float64, device=dev)
+    st1 = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt1 = torch.zeros(len(texts), dtype=torch.int64, device=dev)
+    cnt1_rows = [cnt1[b:b + 1] for b in range(len(texts))]
+    out1_rows = [(out1[offs[b]:offs[b + 1]], st1[offs[b]:offs[b + 1]]) for b in range(len(texts))]
+
+    def per_buffer():
+        for b in range(len(texts)):
+            o, s_ = out1_rows[b]
+            fp.parse_f64_into(views[b], o, s_, cnt1_rows[b], stream=stream)
+
+    plan_g = fp.BatchPlan(views, out, st, offs, cnt, graph=True)
+    plan_p = fp.BatchPlan(views, out, st, offs, cnt, graph=False)
+
+    def batch_call():
+        fp.parse_f64_batch_into(views, out, st, offs, cnt, stream=stream)
+
+    # parity: graph replay == per-buffer launches (all fields), and the oracle
+    # on a sample of buffers
+    out.fill_(-1.0)
+    plan_g.launch(stream)
+    per_buffer()
+    torch.cuda.synchronize()
+    if fp.get_error():
+        raise SystemExit("bench: device error flag set")
+    if not torch.equal(cnt, cnt1):
+        raise SystemExit("bench: batched field counts differ from per-buffer counts")
+    counts = cnt.cpu().tolist()
+    mask = torch.zeros(cap, dtype=torch.bool, device=dev)
+    for b in range(len(texts)):
+        mask[offs[b]:offs[b] + counts[b]] = True
+    if not (torch.equal(out.view(torch.int64)[mask], out1.view(torch.int64)[mask])
+            and torch.equal(st[mask], st1[mask])):
+        raise SystemExit("bench: batched results differ from per-buffer results")
+    N = int(sum(counts))
+    checked = 0
+    if rank == 0 and not args.skip_check:
+        import oracle
+        rnd = np.random.default_rng(5)
+        sample = sorted(set(rnd.choice(len(texts), 48, replace=False).tolist()) | {big})
+        for b in sample:
+            rb, rs = oracle.parse_buffer(texts[b])
+            got = out[offs[b]:offs[b] + counts[b]].cpu().numpy().view(np.uint64)
+            if not (rb.size == counts[b] and np.array_equal(got, rb) and
+                    np.array_equal(st[offs[b]:offs[b] + counts[b]].cpu().numpy(), rs)):
+                raise SystemExit("bench: buffer %d differs from the oracle" % b)
+            checked += int(rb.size)
+
+    sampler = ClockSampler(local).start() if rank == 0 else None
+    t_end = time.perf_counter() + args.clock_settle
+    while time.perf_counter() < t_end:
+        plan_g.launch(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_graph = _time_steps(torch, stream, lambda: plan_g.launch(stream), args.steps, args.warmup)
+    if dist is not None:
+        dist.barrier()
+        tt = torch.tensor([ms_graph], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_graph = float(tt.item())
+    clocks = sampler.stop() if sampler else None
+    few = max(3, min(args.steps, 10))
+    ms_plan = _time_steps(torch, stream, lambda: plan_p.launch(stream), args.steps, args.warmup)
+    ms_call = _time_steps(torch, stream, batch_call, few, 3)
+    t0 = time.perf_counter()
+    ms_per = _time_steps(torch, stream, per_buffer, few, 3)
+    wall_per = (time.perf_counter() - t0) / (few + 3) * 1e3
+
+    # end to end: packed host text -> device, graph replay, counts and exact
+    # results per buffer -> host, every step
+    e2e = None
+    if not args.skip_e2e:
+        h_out = torch.empty(N, dtype=torch.float64).pin_memory()
+        h_st = torch.empty(N, dtype=torch.uint8).pin_memory()
+        h_cnt = torch.empty(len(texts), dtype=torch.int64).pin_memory()
+        dst = [0]
+        for c in counts:
+            dst.append(dst[-1] + c)
+
+        def e2e_step():
+            d_packed.copy_(h_packed, non_blocking=True)
+            plan_g.launch(stream)
+            h_cnt.copy_(cnt, non_blocking=True)
+            stream.synchronize()
+            cs = h_cnt.tolist()
+            for b in range(len(texts)):
+                if cs[b]:
+                    h_out[dst[b]:dst[b] + cs[b]].copy_(out[offs[b]:offs[b] + cs[b]], non_blocking=True)
+                    h_st[dst[b]:dst[b] + cs[b]].copy_(st[offs[b]:offs[b] + cs[b]], non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(3):
+            e2e_step()
+        steps = min(args.steps, args.e2e_steps)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            e2e_step()
+        dt = (time.perf_counter() - t0) / steps
+        e2e = {"value": world * B / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(packed.size),
+               "d2h_bytes_per_step": 9 * N + 8 * len(texts), "steps": steps,
+               "api": "one host->device copy of the packed buffers, fp_batch_plan_launch (graph), "
+                      "one copy of the counts, then exact per-buffer result copies"}
+    if rank != 0:
+        return
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = B + 9 * N
+    gbs = lambda ms: world * B / (ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": gbs(ms_graph), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_graph,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "buffers": len(texts), "text_bytes": B,
+                   "numbers": N, "min_buffer": min(lens), "max_buffer": max(lens),
+                   "mfloats_per_s": world * N / (ms_graph / 1e3) / 1e6,
+                   "l2": "no flush: each step reads %.0f MB of text, more than the L2" % (B / 1e6),
+                   "autotuned": tuned, "checked_fields": checked,
+                   "parallelism": "replicas: one independent batch per GPU"},
+        "forms": {
+            "graph_replay": {"ms": ms_graph, "GB/s": gbs(ms_graph), "launch": "one cudaGraphLaunch"},
+            "plan": {"ms": ms_plan, "GB/s": gbs(ms_plan), "launch": "memset + 2 kernels"},
+            "batch_call": {"ms": ms_call, "GB/s": gbs(ms_call),
+                           "launch": "fp_parse_f64_batch: descriptors built and uploaded per call"},
+            "per_buffer": {"ms": ms_per, "GB/s": gbs(ms_per), "host_ms": wall_per,
+                           "launch": "%d fp_parse_f64 calls (2 kernels each)" % len(texts)},
+        },
+        "roofline": {"bound": "hbm", "achieved": alg_bytes / (ms_graph / 1e3) / 1e9, "peak": peak,
+                     "unit": "GB/s", "frac": alg_bytes / (ms_graph / 1e3) / 1e9 / peak,
+                     "traffic": None, "kernel": "graph: memset + parse_kernel + fallback_kernel",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,6 +553,10 @@ def main() -> None:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--workload", choices=["bulk", "batch"], default="bulk",
+                    help="bulk: one 10M-number buffer (default); batch: 4096 uneven buffers")
+    ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")
+    ap.add_argument("--batch-bytes", type=int, default=2 << 30, help="batch: total text bytes")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
@@ -370,6 +570,8 @@ def main() -> None:
         dist.init_process_group("nccl")
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "batch":
+        run_batch(args, world, rank, dist)
     else:
         run_ours(args, world, rank, dist)
     if dist is not None:

@@ -154,6 +154,105 @@ FP_API fp_err_t fp_parse_f64_batch(const char *const *texts, const size_t *lens,
                             struct CUstream_st *stream);
 
 /*
+ * Batch plans: the descriptors of a fixed set of buffers uploaded once, with
+ * their own scratch, so that one call launches the whole batch with no host
+ * work beyond two memsets and two kernel launches -- a sequence that can be
+ * captured into a CUDA graph and replayed.  (Same results as
+ * fp_parse_f64_batch with the same arguments.)
+ *
+ * fp_batch_plan_create -- arguments as for fp_parse_f64_batch, minus the
+ *   stream, plus `flags`; the buffers and output arrays must stay valid for
+ *   the plan's life.  Synchronous; allocates device memory; the chunk size
+ *   and blocks per SM are those of fp_get_config at this call.  With
+ *   FP_PLAN_GRAPH in `flags` the launch sequence is captured once into a
+ *   CUDA graph here, and each fp_batch_plan_launch replays it with one
+ *   cudaGraphLaunch.  *plan receives the plan.
+ * fp_batch_plan_launch -- queue the parse of every buffer of the plan on
+ *   `stream`.  Launches of one plan must not overlap on the GPU.  Plan
+ *   launches add nothing to fp_get_stats or fp_timing_read.
+ * fp_batch_plan_destroy -- synchronise and free the plan (NULL is ignored).
+ */
+typedef struct fp_batch_plan fp_batch_plan;
+#define FP_PLAN_GRAPH 1u
+FP_API fp_err_t fp_batch_plan_create(const char *const *texts, const size_t *lens, uint32_t nbuf,
+                                     char delim, double *out_f64, uint8_t *out_status,
+                                     const uint64_t *out_offsets, uint64_t *out_counts,
+                                     uint32_t flags, fp_batch_plan **plan);
+FP_API fp_err_t fp_batch_plan_launch(fp_batch_plan *plan, struct CUstream_st *stream);
+FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
+
+/*
+ * Request server: continuous batching of parse requests held in HOST memory.
+ *   (The paper has no counterpart: it measures one buffer at a time.  This is
+ *   the serving form of the same parse.)
+ * One scheduler thread per server owns one device-memory arena of
+ * `device_budget` bytes, cut into a text region (1 B per unit), a value
+ * region (8 B per unit) and a status region (1 B per unit); a request of
+ * `len` bytes holds len units, rounded up to 256, from admission to
+ * completion.  Requests are admitted first-come first-served as arena space
+ * frees up (a request that does not fit waits, and so do those behind it);
+ * each admitted request's text is copied to the device at once, so copies
+ * overlap the launches in flight.  Whenever one of `max_inflight` launch
+ * slots is free, every admitted request not yet launched (at most
+ * `max_batch`) goes into one persistent batched launch on that slot's
+ * stream; when it ends, the field counts come back, then exactly that many
+ * values and statuses per request, straight into the caller's host arrays,
+ * and the request's units are released.  Results equal those of
+ * fp_parse_f64 on the same text, alone or in any mix.
+ * Besides the arena, each slot's stream holds the parse scratch of up to
+ * one budget's worth of chunks (24 B per 4 KiB of budget/10, plus the
+ * fallback queue) and two small pinned arrays.
+ *
+ * fp_server_create -- start a server on the current device.  cfg fields:
+ *   device_budget  bytes for the arena (>= 4 KiB; allocated here at once)
+ *   max_batch      most requests in one launch, 1..65536
+ *   max_inflight   launches in flight at once, 1..8
+ *   delim          field separator besides '\n'
+ * fp_server_submit -- queue one request and return at once.
+ *   host_text    len bytes of host memory (pinned copies fastest)
+ *   host_f64     host array of fp_max_fields(len) doubles (or at least as
+ *                many as the text has fields: exactly that many are written)
+ *   host_status  host array of as many bytes
+ *   request_id   receives the request's id
+ *   All three arrays must stay valid and untouched until the request is
+ *   waited for.  FP_ERR_BUDGET if len units exceed the whole arena.
+ * fp_server_wait -- wait up to timeout_ns (< 0: no limit, 0: poll) for a
+ *   request; on completion fills *info, forgets the request and returns
+ *   the request's own error (FP_OK when parsed); FP_ERR_TIMEOUT if it is
+ *   not done yet (the request stays); FP_ERR_ARG for an unknown id.
+ * fp_server_get_stats -- totals since creation.
+ * fp_server_destroy -- wait for every submitted request, stop the thread,
+ *   free everything (NULL is ignored).
+ * Times are CLOCK_MONOTONIC nanoseconds.
+ */
+typedef struct fp_server fp_server;
+typedef struct {
+  uint64_t device_budget;
+  uint32_t max_batch;
+  uint32_t max_inflight;
+  char delim;
+} fp_server_config_t;
+typedef struct {
+  uint64_t count;      /* fields in the text (= values written) */
+  int32_t error;       /* fp_err_t of this request */
+  uint32_t batch_size; /* requests in the launch that parsed it */
+  int64_t submit_ns, admit_ns, launch_ns, done_ns;
+} fp_request_info_t;
+typedef struct {
+  uint64_t submitted, completed, launches, bytes, fields;
+  uint64_t peak_units;     /* most arena units held at once */
+  uint64_t peak_requests;  /* most requests admitted at once */
+  uint64_t max_batch_seen; /* largest launch */
+} fp_server_stats_t;
+FP_API fp_err_t fp_server_create(const fp_server_config_t *cfg, fp_server **server);
+FP_API fp_err_t fp_server_submit(fp_server *server, const char *host_text, size_t len,
+                                 double *host_f64, uint8_t *host_status, uint64_t *request_id);
+FP_API fp_err_t fp_server_wait(fp_server *server, uint64_t request_id, int64_t timeout_ns,
+                               fp_request_info_t *info);
+FP_API fp_err_t fp_server_get_stats(fp_server *server, fp_server_stats_t *out);
+FP_API fp_err_t fp_server_destroy(fp_server *server);
+
+/*
  * fp_get_stats -- copy the path counters of `stream` into *host_out
  * (host memory).  Synchronises `stream`.  If reset != 0 the counters are
  * zeroed afterwards.
@@ -240,8 +339,7 @@ FP_API fp_err_t fp_parse_f64_host(const char *host_text, size_t len, char delim,
  *   <= 65,536 * chunk_bytes: 1 GiB at the default 16 KiB chunks); beyond that
  *   it returns FP_ERR_CAPACITY and queues nothing.  The first call on each
  *   device looks up the array's device address (cudaGetSymbolAddress) and the
- *   launch shape; make that first call before capturing the stream into a
- *   CUDA graph.
+ *   launch shape.
  *   Every call on every stream shares the one array and clears its control
  *   part on `stream` first: calls whose work overlaps on the GPU (different
  *   streams without ordering) race and give wrong results.  Order them, or

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (STATUS_INVALID, STATUS_OK, STATUS_OVERFLOW, STATUS_UNDERFLOW, Config,
                    FpError, Stats)
 
-__all__ = ["parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
+__all__ = ["BatchPlan", "Server", "parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
            "parse_f64_batch_into", "max_fields", "stats", "get_error", "set_config",
            "get_config", "autotune", "timing_enable", "timing_read", "shutdown", "library_path", "FpError", "STATUS_OK",
            "STATUS_INVALID", "STATUS_OVERFLOW", "STATUS_UNDERFLOW"]
@@ -162,6 +162,108 @@ def parse_f64_batch(texts, delim=b"\n", stream=None):
     counts = cnt.cpu().tolist()
     return [(out[offs[b]:offs[b] + counts[b]], st[offs[b]:offs[b] + counts[b]])
             for b in range(len(texts))]
+
+
+class BatchPlan:
+    """A fixed set of device buffers parsed by one replayable launch
+    (fp_batch_plan_*); with graph=True the launch is one CUDA graph replay.
+    Keeps references to the buffers and outputs."""
+
+    def __init__(self, texts, out_f64, out_status, out_offsets, out_counts, delim=b"\n",
+                 graph=False):
+        nbuf = len(texts)
+        for t in texts:
+            _check_text(t)
+        ptrs = (ctypes.c_void_p * nbuf)(*[t.data_ptr() if t.numel() else None for t in texts])
+        lens = (ctypes.c_size_t * nbuf)(*[t.numel() for t in texts])
+        offs = (ctypes.c_uint64 * (nbuf + 1))(*[int(o) for o in out_offsets])
+        self._keep = (texts, out_f64, out_status, out_counts)
+        self._h = ctypes.c_void_p()
+        _lib.check(_lib.load().fp_batch_plan_create(ptrs, lens, nbuf, _delim_byte(delim),
+                                                    out_f64.data_ptr(), out_status.data_ptr(),
+                                                    offs, out_counts.data_ptr(),
+                                                    1 if graph else 0, ctypes.byref(self._h)),
+                   "fp_batch_plan_create")
+
+    def launch(self, stream=None) -> None:
+        _lib.check(_lib.load().fp_batch_plan_launch(self._h, _stream_handle(stream)),
+                   "fp_batch_plan_launch")
+
+    def close(self) -> None:
+        if self._h:
+            _lib.load().fp_batch_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server on the current device
+    (fp_server_*).  Requests are host tensors: uint8 text, float64 values and
+    uint8 statuses (pinned memory copies fastest); the server keeps
+    references to them until they are waited for."""
+
+    def __init__(self, device_budget: int = 40_000_000_000, max_batch: int = 1024,
+                 max_inflight: int = 3, delim=b"\n"):
+        cfg = _lib.ServerConfig(device_budget, max_batch, max_inflight, _delim_byte(delim))
+        self._h = ctypes.c_void_p()
+        _lib.check(_lib.load().fp_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
+                   "fp_server_create")
+        self._keep = {}
+
+    def submit(self, host_text: torch.Tensor, host_f64: torch.Tensor,
+               host_status: torch.Tensor) -> int:
+        for t, dt in ((host_text, torch.uint8), (host_f64, torch.float64),
+                      (host_status, torch.uint8)):
+            if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("server requests are contiguous host tensors")
+        n = host_text.numel()
+        rid = ctypes.c_uint64()
+        _lib.check(_lib.load().fp_server_submit(self._h, host_text.data_ptr() if n else None, n,
+                                                host_f64.data_ptr(), host_status.data_ptr(),
+                                                ctypes.byref(rid)), "fp_server_submit")
+        self._keep[rid.value] = (host_text, host_f64, host_status)
+        return rid.value
+
+    def wait(self, request_id: int, timeout_s: float | None = None) -> dict | None:
+        """Info dict of a finished request (count, error, batch_size and the
+        CLOCK_MONOTONIC ns of submit/admit/launch/done), or None on timeout."""
+        info = _lib.RequestInfo()
+        t = -1 if timeout_s is None else int(timeout_s * 1e9)
+        rc = _lib.load().fp_server_wait(self._h, request_id, t, ctypes.byref(info))
+        if rc == _lib.FP_ERR_TIMEOUT:
+            return None
+        self._keep.pop(request_id, None)
+        if rc != _lib.FP_OK and info.error == 0:
+            _lib.check(rc, "fp_server_wait")
+        return info.as_dict()
+
+    def stats(self) -> dict:
+        s = _lib.ServerStats()
+        _lib.check(_lib.load().fp_server_get_stats(self._h, ctypes.byref(s)), "fp_server_get_stats")
+        return s.as_dict()
+
+    def close(self) -> None:
+        if self._h:
+            _lib.load().fp_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def stats(reset: bool = False, stream=None) -> dict:

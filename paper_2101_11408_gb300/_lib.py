@@ -18,7 +18,9 @@ STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
 # every symbol include/fpparse.h declares
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
-           "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_shutdown",
+           "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
+           "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_server_create", "fp_server_submit",
+           "fp_server_wait", "fp_server_get_stats", "fp_server_destroy", "fp_shutdown",
            "fp_strerror"]
 
 
@@ -34,6 +36,30 @@ class Stats(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("fallback_queue", ctypes.c_uint32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("max_inflight", ctypes.c_uint32), ("delim", ctypes.c_char)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("error", ctypes.c_int32),
+                ("batch_size", ctypes.c_uint32), ("submit_ns", ctypes.c_int64),
+                ("admit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64),
+                ("done_ns", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "submitted", "completed", "launches", "bytes", "fields", "peak_units", "peak_requests",
+        "max_batch_seen")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 class FpError(RuntimeError):
@@ -88,6 +114,26 @@ def load(build_if_missing: bool = True):
         lib.fp_parse_f64_host.restype = ctypes.c_int
         lib.fp_parse_f64_noalloc.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
         lib.fp_parse_f64_noalloc.restype = ctypes.c_int
+        lib.fp_batch_plan_create.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_char, vp, u8p,
+                                             vp, vp, ctypes.c_uint32,
+                                             ctypes.POINTER(ctypes.c_void_p)]
+        lib.fp_batch_plan_create.restype = ctypes.c_int
+        lib.fp_batch_plan_launch.argtypes = [vp, vp]
+        lib.fp_batch_plan_launch.restype = ctypes.c_int
+        lib.fp_batch_plan_destroy.argtypes = [vp]
+        lib.fp_batch_plan_destroy.restype = ctypes.c_int
+        lib.fp_server_create.argtypes = [ctypes.POINTER(ServerConfig),
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        lib.fp_server_create.restype = ctypes.c_int
+        lib.fp_server_submit.argtypes = [vp, vp, sz, vp, u8p, ctypes.POINTER(ctypes.c_uint64)]
+        lib.fp_server_submit.restype = ctypes.c_int
+        lib.fp_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64,
+                                       ctypes.POINTER(RequestInfo)]
+        lib.fp_server_wait.restype = ctypes.c_int
+        lib.fp_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        lib.fp_server_get_stats.restype = ctypes.c_int
+        lib.fp_server_destroy.argtypes = [vp]
+        lib.fp_server_destroy.restype = ctypes.c_int
         lib.fp_shutdown.argtypes = []
         lib.fp_shutdown.restype = ctypes.c_int
         lib.fp_strerror.argtypes = [ctypes.c_int]

@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfpparse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fp_parse_kernel.cu", "fp_fallback_kernel.cu", "fp_api.cu", "fp_noalloc.cu"]
+SOURCES = ["fp_parse_kernel.cu", "fp_fallback_kernel.cu", "fp_api.cu", "fp_noalloc.cu",
+           "fp_server.cu"]
 HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "pow5_table.inc",
            os.path.join(INCLUDE, "fpparse.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -68,7 +69,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
     if force or procs or _stale(LIB, objs):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-pthread"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

@@ -14,6 +14,7 @@
 
 #include "../../include/fpparse.h"
 #include "fp_device.cuh"
+#include "fp_internal.h"
 #include "fp_launch.h"
 #include "fp_types.cuh"
 
@@ -292,6 +293,112 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   return FP_OK;
 }
 
+// One persistent launch over nbuf device buffers; range(b) gives buffer b's
+// output range (first entry, capacity) in out_f64 / out_status.
+template <class Range>
+fp_err_t batch_impl(const char* const* texts, const size_t* lens, uint32_t nbuf, char delim,
+                    double* out_f64, uint8_t* out_status, uint64_t* out_counts,
+                    cudaStream_t stream, Range range) {
+  if (!texts || !lens || !out_counts) return FP_ERR_ARG;
+  if (nbuf == 0 || nbuf > MAX_BUFS) return FP_ERR_ARG;
+  bool any = false;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    if (lens[b] >= MAX_LEN) return FP_ERR_ARG;
+    if (lens[b] > 0 && !texts[b]) return FP_ERR_ARG;
+    any |= range(b).second > 0;
+  }
+  if (any && (!out_f64 || !out_status)) return FP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Config cfg = g_cfg;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  unsigned long long total = 0, bytes = 0;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    total += chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
+    bytes += lens[b];
+  }
+  Scratch* s = nullptr;
+  e = get_scratch(stream, total, nbuf, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  p.nbuf = nbuf;
+  p.delim = (unsigned char)delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
+  p.out_status = out_status;
+  if (nbuf == 1) {
+    const auto r = range(0);
+    fill_desc(p.one, texts[0], lens[0], 0, total, r.first, r.second, out_counts);
+  } else {
+    // the staging buffer may still feed the previous call's upload
+    if (s->desc_pending) FP_CUDA(cudaEventSynchronize(s->desc_copied));
+    unsigned long long c = 0;
+    for (uint32_t b = 0; b < nbuf; b++) {
+      const unsigned long long nch =
+          chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
+      const auto r = range(b);
+      fill_desc(s->h_descs[b], texts[b], lens[b], c, nch, r.first, r.second, out_counts + b);
+      c += nch;
+    }
+    FP_CUDA(cudaMemcpyAsync(s->d_descs, s->h_descs, (size_t)nbuf * sizeof(BufDesc),
+                            cudaMemcpyHostToDevice, stream));
+    FP_CUDA(cudaEventRecord(s->desc_copied, stream));
+    s->desc_pending = true;
+    p.descs = s->d_descs;
+  }
+  return run(s, cfg, *di, p, total, bytes, stream);
+}
+
+}  // namespace
+
+// Entry points for the library's own host runtime (fp_internal.h).
+namespace fp {
+
+fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32_t nbuf,
+                            char delim, double* out_f64, uint8_t* out_status,
+                            const uint64_t* out_base, const uint64_t* out_cap,
+                            uint64_t* out_counts, cudaStream_t stream) {
+  if (!out_base || !out_cap) return FP_ERR_ARG;
+  return batch_impl(texts, lens, nbuf, delim, out_f64, out_status, out_counts, stream,
+                    [&](uint32_t b) { return std::make_pair(out_base[b], out_cap[b]); });
+}
+
+fp_err_t reserve_stream_scratch(cudaStream_t stream, unsigned long long chunks, uint32_t nbuf) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  Scratch* s = nullptr;
+  return get_scratch(stream, chunks, nbuf, g_cfg.fallback_queue, &s);
+}
+
+fp_err_t release_stream_scratch(cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  auto it = g_scratch.find(std::make_pair(dev, stream));
+  if (it == g_scratch.end()) return FP_OK;
+  if (it->second) {
+    cudaStreamSynchronize(stream);
+    free_scratch(it->second);
+  }
+  g_scratch.erase(it);
+  return FP_OK;
+}
+
+fp_err_t stream_error_word(cudaStream_t stream, unsigned int** word) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  auto it = g_scratch.find(std::make_pair(dev, stream));
+  if (it == g_scratch.end()) return FP_ERR_ARG;
+  *word = &it->second->ctl->error;
+  return FP_OK;
+}
+
+}  // namespace fp
+
+namespace {
 }  // namespace
 
 extern "C" {
@@ -333,57 +440,12 @@ fp_err_t fp_parse_f64_batch(const char* const* texts, const size_t* lens, uint32
                             struct CUstream_st* stream_) {
   if (!texts || !lens || !out_offsets || !out_counts) return FP_ERR_ARG;
   if (nbuf == 0 || nbuf > MAX_BUFS) return FP_ERR_ARG;
-  bool any = false;
-  for (uint32_t b = 0; b < nbuf; b++) {
-    if (lens[b] >= MAX_LEN) return FP_ERR_ARG;
-    if (lens[b] > 0 && !texts[b]) return FP_ERR_ARG;
+  for (uint32_t b = 0; b < nbuf; b++)
     if (out_offsets[b + 1] < out_offsets[b]) return FP_ERR_ARG;
-    any |= out_offsets[b + 1] > out_offsets[b];
-  }
-  if (any && (!out_f64 || !out_status)) return FP_ERR_ARG;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  std::lock_guard<std::mutex> lk(g_mu);
-  const Config cfg = g_cfg;
-  int dev = 0;
-  FP_CUDA(cudaGetDevice(&dev));
-  DeviceInfo* di = nullptr;
-  fp_err_t e = device_info(dev, &di);
-  if (e != FP_OK) return e;
-  unsigned long long total = 0, bytes = 0;
-  for (uint32_t b = 0; b < nbuf; b++) {
-    total += chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
-    bytes += lens[b];
-  }
-  Scratch* s = nullptr;
-  e = get_scratch(stream, total, nbuf, cfg.fallback_queue, &s);
-  if (e != FP_OK) return e;
-  LaunchParams p;
-  memset(&p, 0, sizeof(p));
-  p.nbuf = nbuf;
-  p.delim = (unsigned char)delim;
-  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
-  p.out_status = out_status;
-  if (nbuf == 1) {
-    fill_desc(p.one, texts[0], lens[0], 0, total, out_offsets[0], out_offsets[1] - out_offsets[0],
-              out_counts);
-  } else {
-    // the staging buffer may still feed the previous call's upload
-    if (s->desc_pending) FP_CUDA(cudaEventSynchronize(s->desc_copied));
-    unsigned long long c = 0;
-    for (uint32_t b = 0; b < nbuf; b++) {
-      const unsigned long long nch =
-          chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
-      fill_desc(s->h_descs[b], texts[b], lens[b], c, nch, out_offsets[b],
-                out_offsets[b + 1] - out_offsets[b], out_counts + b);
-      c += nch;
-    }
-    FP_CUDA(cudaMemcpyAsync(s->d_descs, s->h_descs, (size_t)nbuf * sizeof(BufDesc),
-                            cudaMemcpyHostToDevice, stream));
-    FP_CUDA(cudaEventRecord(s->desc_copied, stream));
-    s->desc_pending = true;
-    p.descs = s->d_descs;
-  }
-  return run(s, cfg, *di, p, total, bytes, stream);
+  return batch_impl(texts, lens, nbuf, delim, out_f64, out_status, out_counts,
+                    reinterpret_cast<cudaStream_t>(stream_), [&](uint32_t b) {
+                      return std::make_pair(out_offsets[b], out_offsets[b + 1] - out_offsets[b]);
+                    });
 }
 
 fp_err_t fp_get_stats(fp_stats_t* host_out, int reset, struct CUstream_st* stream_) {
@@ -680,5 +742,168 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
       fclose(f);
     }
   }
+  return FP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batch plans
+// ---------------------------------------------------------------------------
+struct fp_batch_plan {
+  int device;
+  LaunchParams p;                  // descriptors, outputs and scratch pointers
+  unsigned long long total_chunks;
+  unsigned long long total_bytes;
+  uint32_t chunk_bytes, ctas_per_sm;
+  void* dmem;                      // one allocation: ctl, look-back words, overflow list, queue, descriptors
+  size_t scratch_bytes;            // bytes cleared before each launch (ctl + look-back words)
+  int grid_parse, grid_fallback;
+  cudaGraphExec_t graph;           // the captured launch sequence, or null
+};
+
+namespace {
+fp_err_t plan_enqueue(fp_batch_plan* pl, cudaStream_t stream) {
+  FP_CUDA(cudaMemsetAsync(pl->dmem, 0, pl->scratch_bytes, stream));
+  FP_CUDA(fp::launch_parse(pl->p, (int)pl->chunk_bytes, pl->grid_parse, stream));
+  FP_CUDA(fp::launch_fallback(pl->p, pl->grid_fallback, stream));
+  return FP_OK;
+}
+
+// Capture the plan's launch sequence on a private stream and instantiate it.
+fp_err_t plan_capture(fp_batch_plan* pl) {
+  cudaStream_t cs = nullptr;
+  FP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  fp_err_t e = FP_OK;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    e = FP_ERR_CUDA;
+  } else {
+    e = plan_enqueue(pl, cs);
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);  // always end the capture
+    if (e == FP_OK && ce != cudaSuccess) e = FP_ERR_CUDA;
+  }
+  if (e == FP_OK && cudaGraphInstantiate(&pl->graph, g, 0) != cudaSuccess) {
+    pl->graph = nullptr;
+    e = FP_ERR_CUDA;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  return e;
+}
+}  // namespace
+
+extern "C" fp_err_t fp_batch_plan_create(const char* const* texts, const size_t* lens,
+                                         uint32_t nbuf, char delim, double* out_f64,
+                                         uint8_t* out_status, const uint64_t* out_offsets,
+                                         uint64_t* out_counts, uint32_t flags,
+                                         fp_batch_plan** plan) {
+  if (!plan || !texts || !lens || !out_offsets || !out_counts) return FP_ERR_ARG;
+  *plan = nullptr;
+  if (nbuf == 0 || nbuf > MAX_BUFS || (flags & ~FP_PLAN_GRAPH)) return FP_ERR_ARG;
+  bool any = false;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    if (lens[b] >= MAX_LEN) return FP_ERR_ARG;
+    if (lens[b] > 0 && !texts[b]) return FP_ERR_ARG;
+    if (out_offsets[b + 1] < out_offsets[b]) return FP_ERR_ARG;
+    any |= out_offsets[b + 1] > out_offsets[b];
+  }
+  if (any && (!out_f64 || !out_status)) return FP_ERR_ARG;
+  fp_config_t cfg;
+  fp_get_config(&cfg);
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    fp_err_t e = device_info(dev, &di);
+    if (e != FP_OK) return e;
+  }
+  std::vector<BufDesc> h(nbuf);
+  unsigned long long c = 0, bytes = 0;
+  for (uint32_t b = 0; b < nbuf; b++) {
+    const unsigned long long nch =
+        chunks_of(reinterpret_cast<uintptr_t>(texts[b]) & 15, lens[b], cfg.chunk_bytes);
+    fill_desc(h[b], texts[b], lens[b], c, nch, out_offsets[b], out_offsets[b + 1] - out_offsets[b],
+              out_counts + b);
+    c += nch;
+    bytes += lens[b];
+  }
+  const unsigned long long qcap = cfg.fallback_queue;
+  const size_t off_status = 256;
+  const size_t off_ovf = off_status + c * 8;
+  const size_t off_queue = off_ovf + 2 * c * 8;
+  const size_t off_desc = (off_queue + qcap * 8 + 255) & ~(size_t)255;
+  const size_t total = off_desc + (size_t)nbuf * sizeof(BufDesc);
+  fp_batch_plan* pl = new fp_batch_plan();
+  memset(&pl->p, 0, sizeof(pl->p));
+  pl->device = dev;
+  if (cudaMalloc(&pl->dmem, total) != cudaSuccess) {
+    delete pl;
+    return FP_ERR_CUDA;
+  }
+  unsigned char* base = static_cast<unsigned char*>(pl->dmem);
+  if (cudaMemcpy(base + off_desc, h.data(), (size_t)nbuf * sizeof(BufDesc),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(base, 0, off_ovf) != cudaSuccess) {
+    cudaFree(pl->dmem);
+    delete pl;
+    return FP_ERR_CUDA;
+  }
+  LaunchParams& p = pl->p;
+  p.nbuf = nbuf;
+  if (nbuf == 1) p.one = h[0];
+  p.descs = reinterpret_cast<const BufDesc*>(base + off_desc);
+  p.delim = (unsigned char)delim;
+  p.total_chunks = c;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
+  p.out_status = out_status;
+  p.ctl = reinterpret_cast<Ctl*>(base);
+  p.chunk_status = reinterpret_cast<unsigned long long*>(base + off_status);
+  p.epoch = 1;  // the look-back words are cleared before every launch
+  p.queue = reinterpret_cast<unsigned long long*>(base + off_queue);
+  p.qcap = qcap;
+  p.ovf = reinterpret_cast<unsigned long long*>(base + off_ovf);
+  p.ovf_cap = c;
+  pl->total_chunks = c;
+  pl->total_bytes = bytes;
+  pl->scratch_bytes = off_ovf;
+  pl->chunk_bytes = cfg.chunk_bytes;
+  const int occ = di->parse_occ.at((int)cfg.chunk_bytes);
+  const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
+  unsigned long long grid = (unsigned long long)di->sms * per_sm;
+  pl->grid_parse = (int)(grid > c ? c : grid);
+  pl->grid_fallback = di->sms * di->fb_occ;
+  pl->graph = nullptr;
+  if (flags & FP_PLAN_GRAPH) {
+    fp_err_t e = plan_capture(pl);
+    if (e != FP_OK) {
+      cudaFree(pl->dmem);
+      delete pl;
+      return e;
+    }
+  }
+  *plan = pl;
+  return FP_OK;
+}
+
+extern "C" fp_err_t fp_batch_plan_launch(fp_batch_plan* pl, struct CUstream_st* stream_) {
+  if (!pl) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (pl->graph) {
+    FP_CUDA(cudaGraphLaunch(pl->graph, stream));
+    return FP_OK;
+  }
+  return plan_enqueue(pl, stream);
+}
+
+extern "C" fp_err_t fp_batch_plan_destroy(fp_batch_plan* pl) {
+  if (!pl) return FP_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  cudaSetDevice(pl->device);
+  cudaDeviceSynchronize();
+  if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  cudaFree(pl->dmem);
+  if (prev >= 0) cudaSetDevice(prev);
+  delete pl;
   return FP_OK;
 }

@@ -1,0 +1,32 @@
+// fp_internal.h -- entry points that the library's own host runtime (the
+// request server) uses beside the C ABI.  Not exported.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fpparse.h"
+
+namespace fp {
+
+// fp_parse_f64_batch with explicit output ranges: buffer b writes entries
+// [out_base[b], out_base[b] + out_cap[b]) of out_f64 / out_status (ranges
+// of different buffers must not overlap) and its field count to
+// out_counts[b].
+fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32_t nbuf,
+                            char delim, double* out_f64, uint8_t* out_status,
+                            const uint64_t* out_base, const uint64_t* out_cap,
+                            uint64_t* out_counts, cudaStream_t stream);
+
+// Grow the scratch of (current device, stream) now, so that later calls of
+// up to `chunks` chunks and `nbuf` buffers allocate nothing.
+fp_err_t reserve_stream_scratch(cudaStream_t stream, unsigned long long chunks, uint32_t nbuf);
+
+// Synchronise `stream` and free its scratch (before the stream is destroyed).
+fp_err_t release_stream_scratch(cudaStream_t stream);
+
+// Device address of the error word of (current device, stream)'s scratch.
+fp_err_t stream_error_word(cudaStream_t stream, unsigned int** word);
+
+}  // namespace fp

@@ -1,0 +1,446 @@
+// fp_server.cu -- the request server of include/fpparse.h (fp_server_*):
+// continuous batching of host-memory parse requests on one GPU.
+//
+// One scheduler thread per server runs a polling loop of four steps:
+//   retire  a slot whose counts have arrived gets its exact result copies
+//           queued; a slot whose copies are done completes its requests and
+//           releases their arena units;
+//   take    new submissions move to the pending queue (FIFO);
+//   admit   pending requests get arena units in arrival order while they
+//           fit, and their text copies are queued on the copy stream;
+//   launch  each free slot takes every admitted request not yet launched
+//           (at most max_batch) and queues one persistent batched parse on
+//           its own stream, after the copies, then the counts' copy back.
+// Copies in both directions and the launches of different slots overlap on
+// the device; the loop only orders them with events.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/fpparse.h"
+#include "fp_arena.h"
+#include "fp_internal.h"
+
+namespace {
+
+constexpr uint64_t UNIT_ROUND = 256;       // units of a request are rounded up to this
+constexpr uint64_t MIN_BUDGET = 4096;
+constexpr uint32_t MAX_SLOTS = 8;
+constexpr uint32_t MAX_BATCH = 65536;
+constexpr unsigned long long MAX_LEN = 1ull << 40;
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t id = 0;
+  const char* h_text = nullptr;
+  size_t len = 0;
+  double* h_f64 = nullptr;
+  uint8_t* h_status = nullptr;
+  uint64_t off = 0, units = 0;  // arena range while admitted
+  fp_request_info_t info{};
+  bool done = false;
+};
+
+enum class Phase { FREE, PARSING, COPYING };
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_counts = nullptr, ev_done = nullptr;
+  uint64_t* d_counts = nullptr;  // max_batch field counts
+  uint64_t* h_counts = nullptr;  // pinned copy
+  unsigned int* d_err = nullptr; // the parse scratch's error word of this stream
+  unsigned int* h_err = nullptr; // pinned copy
+  Phase phase = Phase::FREE;
+  std::vector<Request*> reqs;
+  std::vector<const char*> texts;
+  std::vector<size_t> lens;
+  std::vector<uint64_t> base, cap;
+};
+
+}  // namespace
+
+struct fp_server {
+  fp_server_config_t cfg{};
+  int device = 0;
+  uint64_t units = 0;
+  void* dmem = nullptr;
+  char* d_text = nullptr;
+  double* d_f64 = nullptr;
+  uint8_t* d_status = nullptr;
+  fp::Arena arena{0};
+  cudaStream_t h2d = nullptr;
+  cudaEvent_t ev_h2d = nullptr;
+  std::vector<Slot> slots;
+  std::thread thread;
+
+  std::mutex mu;  // guards everything below up to `st`
+  std::condition_variable cv_submit, cv_done;
+  std::deque<Request*> incoming;
+  std::unordered_map<uint64_t, Request*> live;  // submitted, not yet waited for
+  uint64_t next_id = 1;
+  uint64_t outstanding = 0;                     // submitted, not yet completed
+  bool stop = false;
+  fp_server_stats_t st{};
+
+  // scheduler thread only
+  std::deque<Request*> pending, admitted;
+  uint64_t held_requests = 0;
+};
+
+namespace {
+
+void finish(fp_server* S, Request* r, fp_err_t err) {
+  r->info.error = (int32_t)err;
+  r->info.done_ns = now_ns();
+  if (r->units) S->arena.release(r->off, r->units);
+  r->units = 0;
+  S->held_requests--;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->done = true;
+    S->outstanding--;
+    S->st.completed++;
+    if (err == FP_OK) S->st.fields += r->info.count;
+  }
+  S->cv_done.notify_all();
+}
+
+void fail_slot(fp_server* S, Slot& sl, fp_err_t err) {
+  for (Request* r : sl.reqs) finish(S, r, err);
+  sl.reqs.clear();
+  sl.phase = Phase::FREE;
+}
+
+// Retire step for one slot; returns true if it changed state.
+bool retire(fp_server* S, Slot& sl) {
+  if (sl.phase == Phase::PARSING) {
+    const cudaError_t q = cudaEventQuery(sl.ev_counts);
+    if (q == cudaErrorNotReady) return false;
+    if (q != cudaSuccess) {
+      fail_slot(S, sl, FP_ERR_CUDA);
+      return true;
+    }
+    if (*sl.h_err) {  // a bounded device wait ran out: the batch's results are void
+      const fp_err_t e = (fp_err_t)*sl.h_err;
+      *sl.h_err = 0;
+      cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned int), sl.stream);
+      fail_slot(S, sl, e);
+      return true;
+    }
+    for (size_t i = 0; i < sl.reqs.size(); i++) {
+      Request* r = sl.reqs[i];
+      const uint64_t n = sl.h_counts[i];
+      r->info.count = n;
+      if (n > r->len) {  // cannot happen: a text of len bytes has at most len fields
+        r->info.error = FP_ERR_INTERNAL;
+        continue;
+      }
+      if (n) {
+        if (cudaMemcpyAsync(r->h_f64, S->d_f64 + r->off, n * sizeof(double),
+                            cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+            cudaMemcpyAsync(r->h_status, S->d_status + r->off, n, cudaMemcpyDeviceToHost,
+                            sl.stream) != cudaSuccess)
+          r->info.error = FP_ERR_CUDA;
+      }
+    }
+    if (cudaEventRecord(sl.ev_done, sl.stream) != cudaSuccess) {
+      fail_slot(S, sl, FP_ERR_CUDA);
+      return true;
+    }
+    sl.phase = Phase::COPYING;
+    return true;
+  }
+  if (sl.phase == Phase::COPYING) {
+    const cudaError_t q = cudaEventQuery(sl.ev_done);
+    if (q == cudaErrorNotReady) return false;
+    for (Request* r : sl.reqs) {
+      fp_err_t e = (fp_err_t)r->info.error;
+      if (q != cudaSuccess) e = FP_ERR_CUDA;
+      finish(S, r, e);
+    }
+    sl.reqs.clear();
+    sl.phase = Phase::FREE;
+    return true;
+  }
+  return false;
+}
+
+// Launch step for one free slot.
+void launch(fp_server* S, Slot& sl) {
+  const size_t k = std::min<size_t>(S->admitted.size(), S->cfg.max_batch);
+  sl.reqs.assign(S->admitted.begin(), S->admitted.begin() + k);
+  S->admitted.erase(S->admitted.begin(), S->admitted.begin() + k);
+  sl.texts.resize(k);
+  sl.lens.resize(k);
+  sl.base.resize(k);
+  sl.cap.resize(k);
+  for (size_t i = 0; i < k; i++) {
+    Request* r = sl.reqs[i];
+    sl.texts[i] = S->d_text + r->off;
+    sl.lens[i] = r->len;
+    sl.base[i] = r->off;
+    sl.cap[i] = r->len;  // fp_max_fields(len)
+  }
+  fp_err_t e = FP_OK;
+  if (cudaStreamWaitEvent(sl.stream, S->ev_h2d, 0) != cudaSuccess) e = FP_ERR_CUDA;
+  if (e == FP_OK)
+    e = fp::parse_batch_ranges(sl.texts.data(), sl.lens.data(), (uint32_t)k, S->cfg.delim,
+                               S->d_f64, S->d_status, sl.base.data(), sl.cap.data(), sl.d_counts,
+                               sl.stream);
+  if (e == FP_OK &&
+      (cudaMemcpyAsync(sl.h_counts, sl.d_counts, k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                       sl.stream) != cudaSuccess ||
+       cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                       sl.stream) != cudaSuccess ||
+       cudaEventRecord(sl.ev_counts, sl.stream) != cudaSuccess))
+    e = FP_ERR_CUDA;
+  if (e != FP_OK) {
+    fail_slot(S, sl, e);
+    return;
+  }
+  const int64_t t = now_ns();
+  for (Request* r : sl.reqs) {
+    r->info.launch_ns = t;
+    r->info.batch_size = (uint32_t)k;
+  }
+  sl.phase = Phase::PARSING;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->st.launches++;
+  S->st.max_batch_seen = std::max<uint64_t>(S->st.max_batch_seen, k);
+}
+
+void scheduler(fp_server* S) {
+  cudaSetDevice(S->device);
+  for (;;) {
+    bool progressed = false, busy = false;
+    for (Slot& sl : S->slots) {
+      progressed |= retire(S, sl);
+      busy |= sl.phase != Phase::FREE;
+    }
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      while (!S->incoming.empty()) {
+        S->pending.push_back(S->incoming.front());
+        S->incoming.pop_front();
+      }
+      if (S->stop && S->outstanding == 0) break;
+    }
+    bool admitted_any = false;
+    while (!S->pending.empty()) {
+      Request* r = S->pending.front();
+      uint64_t off = 0;
+      if (!S->arena.alloc(r->units, &off)) break;  // first come, first served
+      S->pending.pop_front();
+      r->off = off;
+      S->held_requests++;
+      r->info.admit_ns = now_ns();
+      if (r->len && cudaMemcpyAsync(S->d_text + off, r->h_text, r->len, cudaMemcpyHostToDevice,
+                                    S->h2d) != cudaSuccess) {
+        finish(S, r, FP_ERR_CUDA);
+        continue;
+      }
+      S->admitted.push_back(r);
+      admitted_any = true;
+    }
+    if (admitted_any) {
+      progressed = true;
+      if (cudaEventRecord(S->ev_h2d, S->h2d) != cudaSuccess) {
+        while (!S->admitted.empty()) {
+          finish(S, S->admitted.front(), FP_ERR_CUDA);
+          S->admitted.pop_front();
+        }
+      }
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->st.peak_units = std::max<uint64_t>(S->st.peak_units, S->arena.used_units());
+      S->st.peak_requests = std::max<uint64_t>(S->st.peak_requests, S->held_requests);
+    }
+    for (Slot& sl : S->slots) {
+      if (S->admitted.empty()) break;
+      if (sl.phase != Phase::FREE) continue;
+      launch(S, sl);
+      progressed = true;
+      busy = true;
+    }
+    if (progressed) continue;
+    if (busy || !S->admitted.empty()) {
+      std::this_thread::yield();
+    } else {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_submit.wait_for(lk, std::chrono::milliseconds(1),
+                            [&] { return !S->incoming.empty() || S->stop; });
+    }
+  }
+}
+
+void free_server(fp_server* S) {
+  cudaSetDevice(S->device);
+  for (Slot& sl : S->slots) {
+    if (sl.stream) {
+      cudaStreamSynchronize(sl.stream);
+      fp::release_stream_scratch(sl.stream);
+      cudaStreamDestroy(sl.stream);
+    }
+    if (sl.ev_counts) cudaEventDestroy(sl.ev_counts);
+    if (sl.ev_done) cudaEventDestroy(sl.ev_done);
+    cudaFree(sl.d_counts);
+    cudaFreeHost(sl.h_counts);
+    cudaFreeHost(sl.h_err);
+  }
+  if (S->h2d) {
+    cudaStreamSynchronize(S->h2d);
+    cudaStreamDestroy(S->h2d);
+  }
+  if (S->ev_h2d) cudaEventDestroy(S->ev_h2d);
+  cudaFree(S->dmem);
+  for (auto& kv : S->live) delete kv.second;
+  delete S;
+}
+
+}  // namespace
+
+#define SRV_CUDA(x)                 \
+  do {                              \
+    if ((x) != cudaSuccess) {       \
+      free_server(S);               \
+      return FP_ERR_CUDA;           \
+    }                               \
+  } while (0)
+
+extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** server) {
+  if (!cfg || !server) return FP_ERR_ARG;
+  *server = nullptr;
+  if (cfg->device_budget < MIN_BUDGET || cfg->max_batch < 1 || cfg->max_batch > MAX_BATCH ||
+      cfg->max_inflight < 1 || cfg->max_inflight > MAX_SLOTS)
+    return FP_ERR_ARG;
+  fp_server* S = new fp_server();
+  S->cfg = *cfg;
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    delete S;
+    return FP_ERR_CUDA;
+  }
+  // units: 1 text byte + 8 value bytes + 1 status byte each
+  S->units = cfg->device_budget / 10 / UNIT_ROUND * UNIT_ROUND;
+  if (S->units == 0) {
+    delete S;
+    return FP_ERR_ARG;
+  }
+  SRV_CUDA(cudaMalloc(&S->dmem, S->units * 10));
+  S->d_text = static_cast<char*>(S->dmem);
+  S->d_f64 = reinterpret_cast<double*>(S->d_text + S->units);
+  S->d_status = reinterpret_cast<uint8_t*>(S->d_text + 9 * S->units);
+  S->arena = fp::Arena(S->units);
+  SRV_CUDA(cudaStreamCreateWithFlags(&S->h2d, cudaStreamNonBlocking));
+  SRV_CUDA(cudaEventCreateWithFlags(&S->ev_h2d, cudaEventDisableTiming));
+  S->slots.resize(cfg->max_inflight);
+  // the most chunks one launch can hold: every unit of text at the smallest
+  // chunk size, plus one partial chunk per request at each end
+  const unsigned long long chunks = S->units / 4096 + 2ull * cfg->max_batch + 16;
+  for (Slot& sl : S->slots) {
+    SRV_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+    SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_counts, cudaEventDisableTiming));
+    SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
+    SRV_CUDA(cudaMalloc(&sl.d_counts, cfg->max_batch * sizeof(uint64_t)));
+    SRV_CUDA(cudaMallocHost(&sl.h_counts, cfg->max_batch * sizeof(uint64_t)));
+    SRV_CUDA(cudaMallocHost(&sl.h_err, sizeof(unsigned int)));
+    *sl.h_err = 0;
+    if (fp::reserve_stream_scratch(sl.stream, chunks, cfg->max_batch) != FP_OK ||
+        fp::stream_error_word(sl.stream, &sl.d_err) != FP_OK) {
+      free_server(S);
+      return FP_ERR_CUDA;
+    }
+    sl.reqs.reserve(cfg->max_batch);
+  }
+  SRV_CUDA(cudaDeviceSynchronize());
+  S->thread = std::thread(scheduler, S);
+  *server = S;
+  return FP_OK;
+}
+
+extern "C" fp_err_t fp_server_submit(fp_server* S, const char* host_text, size_t len,
+                                     double* host_f64, uint8_t* host_status,
+                                     uint64_t* request_id) {
+  if (!S || !request_id) return FP_ERR_ARG;
+  if (len >= MAX_LEN) return FP_ERR_ARG;
+  if (len > 0 && (!host_text || !host_f64 || !host_status)) return FP_ERR_ARG;
+  const uint64_t units = (std::max<uint64_t>(len, 1) + UNIT_ROUND - 1) / UNIT_ROUND * UNIT_ROUND;
+  if (units > S->units) return FP_ERR_BUDGET;
+  Request* r = new Request();
+  r->h_text = host_text;
+  r->len = len;
+  r->h_f64 = host_f64;
+  r->h_status = host_status;
+  r->units = units;
+  r->info.submit_ns = now_ns();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) {
+      delete r;
+      return FP_ERR_ARG;
+    }
+    r->id = S->next_id++;
+    S->live[r->id] = r;
+    S->incoming.push_back(r);
+    S->outstanding++;
+    S->st.submitted++;
+    S->st.bytes += len;
+  }
+  S->cv_submit.notify_one();
+  *request_id = r->id;
+  return FP_OK;
+}
+
+extern "C" fp_err_t fp_server_wait(fp_server* S, uint64_t id, int64_t timeout_ns,
+                                   fp_request_info_t* info) {
+  if (!S) return FP_ERR_ARG;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->live.find(id);
+  if (it == S->live.end()) return FP_ERR_ARG;
+  Request* r = it->second;
+  if (!r->done) {
+    if (timeout_ns == 0) return FP_ERR_TIMEOUT;
+    auto pred = [&] { return r->done; };
+    if (timeout_ns < 0) {
+      S->cv_done.wait(lk, pred);
+    } else if (!S->cv_done.wait_for(lk, std::chrono::nanoseconds(timeout_ns), pred)) {
+      return FP_ERR_TIMEOUT;
+    }
+  }
+  if (info) *info = r->info;
+  const fp_err_t e = (fp_err_t)r->info.error;
+  S->live.erase(it);
+  delete r;
+  return e;
+}
+
+extern "C" fp_err_t fp_server_get_stats(fp_server* S, fp_server_stats_t* out) {
+  if (!S || !out) return FP_ERR_ARG;
+  std::lock_guard<std::mutex> lk(S->mu);
+  *out = S->st;
+  return FP_OK;
+}
+
+extern "C" fp_err_t fp_server_destroy(fp_server* S) {
+  if (!S) return FP_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_submit.notify_all();
+  if (S->thread.joinable()) S->thread.join();
+  free_server(S);
+  return FP_OK;
+}

@@ -308,3 +308,22 @@ def csv_request(size: int, seed: int, pool: bytes | None = None) -> bytes:
 def csv_pool(pool_bytes: int = 64 << 20, seed: int = SEED_BASE + 5) -> bytes:
     return _cached("csvpool:%d:%d" % (pool_bytes, seed),
                    lambda: _pool_text(pool_bytes, seed, cols=8))
+
+
+def pack_buffers(texts: list[bytes], skew: bool = True) -> tuple[np.ndarray, list[int]]:
+    """Lay many buffers out in one byte array, as a caller holding them in one
+    allocation would: each starts on a 16-byte boundary plus (index mod 16)
+    bytes when `skew` (so every start alignment occurs), with 16 bytes of
+    digits between neighbours.  Returns (array, start offsets)."""
+    starts, pos = [], 0
+    for b, t in enumerate(texts):
+        pos = (pos + 15) & ~15
+        if skew:
+            pos += b % 16
+        starts.append(pos)
+        pos += len(t) + 16
+    arr = np.full(pos + 16, ord("7"), dtype=np.uint8)
+    for s, t in zip(starts, texts):
+        if t:
+            arr[s:s + len(t)] = np.frombuffer(t, dtype=np.uint8)
+    return arr, starts

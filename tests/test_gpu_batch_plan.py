@@ -1,0 +1,159 @@
+"""Batch plans (fp_batch_plan_*): many device buffers parsed by one
+persistent launch that is set up once and replayed, directly or from a CUDA
+graph.  Their results must equal the per-buffer entry point's and the
+oracle's, bit for bit, on every replay and after the buffers' contents
+change between replays.
+"""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2101_11408_gb300 as fp
+from paper_2101_11408_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_texts(count, seed):
+    rnd = random.Random(seed)
+    texts = []
+    for i in range(count):
+        k = rnd.randrange(5)
+        if k == 0:
+            texts.append(b"")
+        elif k == 1:
+            texts.append(workloads.uniform_text(rnd.randrange(1, 3000), seed * 1000 + i))
+        elif k == 2:
+            texts.append(workloads.bulk_mixed_text(rnd.randrange(1, 30000), seed * 1000 + i))
+        elif k == 3:
+            texts.append(workloads.hard_case_text(rnd.randrange(1, 400), seed * 1000 + i))
+        else:
+            texts.append(b"1.5,,2e5\n-0\n.25e-400\nx\n")
+    return texts
+
+
+def pack_to_device(texts):
+    arr, starts = workloads.pack_buffers(texts)
+    d = torch.from_numpy(arr).cuda()
+    return d, [d[s:s + len(t)] for s, t in zip(starts, texts)]
+
+
+def outputs(texts):
+    offs = [0]
+    for t in texts:
+        offs.append(offs[-1] + len(t))
+    cap = max(offs[-1], 1)
+    out = torch.full((cap,), -3.0, dtype=torch.float64, device="cuda")
+    st = torch.full((cap,), 0xEE, dtype=torch.uint8, device="cuda")
+    cnt = torch.full((len(texts),), -1, dtype=torch.int64, device="cuda")
+    return offs, out, st, cnt
+
+
+def check_against_oracle(texts, offs, out, st, cnt, delim=b"\n"):
+    counts = cnt.cpu().tolist()
+    allv = out.cpu().numpy().view(np.uint64)
+    alls = st.cpu().numpy()
+    for b, t in enumerate(texts):
+        rb, rs = oracle.parse_buffer(t, delim)
+        assert counts[b] == rb.size, "buffer %d: %d fields, oracle %d" % (b, counts[b], rb.size)
+        assert np.array_equal(allv[offs[b]:offs[b] + counts[b]], rb), "buffer %d values" % b
+        assert np.array_equal(alls[offs[b]:offs[b] + counts[b]], rs), "buffer %d statuses" % b
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_plan_matches_oracle_on_every_replay(graph):
+    texts = mixed_texts(80, 11)
+    _, views = pack_to_device(texts)
+    offs, out, st, cnt = outputs(texts)
+    plan = fp.BatchPlan(views, out, st, offs, cnt, delim=b",", graph=graph)
+    try:
+        for _ in range(3):
+            out.fill_(-3.0)
+            st.fill_(0xEE)
+            cnt.fill_(-1)
+            plan.launch()
+            torch.cuda.synchronize()
+            check_against_oracle(texts, offs, out, st, cnt, b",")
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_replay_reads_the_buffers_current_contents(graph):
+    a = [workloads.bulk_mixed_text(5000, 21), workloads.hard_case_text(300, 22)]
+    b = [workloads.uniform_text(5000, 23), workloads.bulk_mixed_text(300, 24)]
+    n = max(len(x) for x in a + b) + 64
+    # same buffers, same lengths: pad each pair to a common length with a
+    # run of newlines (empty trailing fields are INVALID, on both sides)
+    a = [x + b"\n" * (n - len(x)) for x in a]
+    b = [x + b"\n" * (n - len(x)) for x in b]
+    d, views = pack_to_device(a)
+    offs, out, st, cnt = outputs(a)
+    plan = fp.BatchPlan(views, out, st, offs, cnt, graph=graph)
+    try:
+        plan.launch()
+        torch.cuda.synchronize()
+        check_against_oracle(a, offs, out, st, cnt)
+        for v, x in zip(views, b):
+            v.copy_(torch.frombuffer(bytearray(x), dtype=torch.uint8))
+        plan.launch()
+        torch.cuda.synchronize()
+        check_against_oracle(b, offs, out, st, cnt)
+    finally:
+        plan.close()
+
+
+def test_plan_equals_batch_call_and_per_buffer_calls():
+    texts = mixed_texts(300, 31)
+    _, views = pack_to_device(texts)
+    offs, out, st, cnt = outputs(texts)
+    plan = fp.BatchPlan(views, out, st, offs, cnt, graph=True)
+    plan.launch()
+    offs2, out2, st2, cnt2 = outputs(texts)
+    fp.parse_f64_batch_into(views, out2, st2, offs2, cnt2)
+    torch.cuda.synchronize()
+    assert torch.equal(cnt, cnt2)
+    counts = cnt.cpu().tolist()
+    for b, v in enumerate(views):
+        vals, s = fp.parse_f64(v)
+        k = counts[b]
+        assert vals.numel() == k
+        assert torch.equal(out[offs[b]:offs[b] + k].view(torch.int64), vals.view(torch.int64))
+        assert torch.equal(out2[offs[b]:offs[b] + k].view(torch.int64), vals.view(torch.int64))
+        assert torch.equal(st[offs[b]:offs[b] + k], s)
+    plan.close()
+
+
+def test_single_buffer_plan_and_capacity_limit():
+    text = workloads.uniform_text(1000, 41)
+    _, views = pack_to_device([text])
+    out = torch.full((400,), -1.0, dtype=torch.float64, device="cuda")
+    st = torch.full((400,), 9, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    plan = fp.BatchPlan(views, out, st, [100, 300], cnt, graph=True)
+    plan.launch()
+    torch.cuda.synchronize()
+    rb, _ = oracle.parse_buffer(text)
+    assert int(cnt.item()) == 1000
+    got = out.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got[100:300], rb[:200])
+    assert (out[:100].cpu() == -1.0).all() and (out[300:].cpu() == -1.0).all()
+    assert (st[:100].cpu() == 9).all() and (st[300:].cpu() == 9).all()
+    plan.close()
+
+
+def test_plan_on_the_batched_workload_sample():
+    """A 64 MiB slice of the 4096-buffer workload's size law (lognormal,
+    sigma 2), every buffer checked against the oracle."""
+    texts = workloads.batch_buffers(512, 64 << 20, hi=8 << 20, seed=workloads.SEED_BASE + 44)
+    _, views = pack_to_device(texts)
+    offs, out, st, cnt = outputs(texts)
+    plan = fp.BatchPlan(views, out, st, offs, cnt, graph=True)
+    plan.launch()
+    plan.launch()
+    torch.cuda.synchronize()
+    check_against_oracle(texts, offs, out, st, cnt)
+    plan.close()
