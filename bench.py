@@ -538,6 +538,187 @@ def run_batch(args, world, rank, dist) -> None:
     print(json.dumps(line), flush=True)
 
 
+SERVE_WORKLOAD = ("serving: Poisson arrivals of CSV requests (8 comma-separated columns of uniform "
+                  "[0,1) %.17g values, newline rows), sizes lognormal (median 1 MiB, sigma 1.85) clipped "
+                  "to [4 KiB, 256 MiB], admitted under a 40 GB device-memory budget, at 25/50/90% "
+                  "of the server's peak offered load")
+
+
+def _percentile_ms(lat_ns, q):
+    return float(np.percentile(np.asarray(lat_ns, dtype=np.float64), q)) / 1e6
+
+
+def run_serve(args, world, rank, dist) -> None:
+    """The request server against the plain per-request path, both fed the
+    same Poisson arrival traces of host-memory requests."""
+    import ctypes
+
+    import torch
+
+    import paper_2101_11408_gb300 as fp
+    from paper_2101_11408_gb300 import workloads
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    lib = fp._lib.load()
+    rng = np.random.default_rng(workloads.SEED_BASE + 6 + 1000 * rank)
+    R = args.serve_bodies
+    sizes = np.clip(np.exp(np.log(1 << 20) + 1.85 * rng.standard_normal(R)), 4 << 10,
+                    256 << 20).astype(np.int64)
+    t = time.perf_counter()
+    pool = workloads.csv_pool()
+    bodies = []
+    for j in range(R):
+        text = workloads.csv_request(int(sizes[j]), workloads.SEED_BASE + 7000 + j, pool)
+        a = np.frombuffer(text, dtype=np.uint8)
+        fields = int(np.count_nonzero((a == 44) | (a == 10))) + 1  # no empty fields, no trailing separator
+        h = torch.frombuffer(bytearray(text), dtype=torch.uint8).pin_memory()
+        bodies.append((h, torch.empty(fields, dtype=torch.float64).pin_memory(),
+                       torch.empty(fields, dtype=torch.uint8).pin_memory(), fields))
+    lens = np.array([b[0].numel() for b in bodies], dtype=np.int64)
+    mean_bytes = float(lens.mean())
+    mean_fields = float(np.mean([b[3] for b in bodies]))
+    log("rank %d: %d request bodies, %.1f MB (mean %.2f MB, max %.1f MB) in %.1f s" % (
+        rank, R, lens.sum() / 1e6, mean_bytes / 1e6, lens.max() / 1e6, time.perf_counter() - t))
+
+    srv = fp.Server(device_budget=args.serve_budget, max_batch=args.serve_batch,
+                    max_inflight=args.serve_inflight, delim=b",")
+    stream = torch.cuda.current_stream()
+    cnt = ctypes.c_uint64()
+
+    def plain_one(j):
+        h, v, s_, fields = bodies[j]
+        rc = lib.fp_parse_f64_host(h.data_ptr(), h.numel(), b",", v.data_ptr(), s_.data_ptr(),
+                                   ctypes.byref(cnt), stream.cuda_stream)
+        if rc != 0 or cnt.value != fields:
+            raise SystemExit("bench: plain path failed (%d, %d fields of %d)" % (rc, cnt.value,
+                                                                                fields))
+
+    def run_server(order, arr_ns):
+        n = len(order)
+        t0 = time.monotonic_ns() + 2_000_000
+        infos = [None] * n
+        rids = [0] * n
+        last = {}
+        for i in range(n):
+            j = int(order[i])
+            p = last.get(j)
+            if p is not None and infos[p] is None:  # the body's arrays are about to be reused
+                infos[p] = srv.wait(rids[p])
+            ta = t0 + int(arr_ns[i])
+            while time.monotonic_ns() < ta:
+                pass
+            h, v, s_, _ = bodies[j]
+            rids[i] = srv.submit(h, v, s_)
+            last[j] = i
+        for i in range(n):
+            if infos[i] is None:
+                infos[i] = srv.wait(rids[i])
+        for i, inf in enumerate(infos):
+            if inf["error"] or inf["count"] != bodies[int(order[i])][3]:
+                raise SystemExit("bench: server request %d failed: %r" % (i, inf))
+        lat = [inf["done_ns"] - (t0 + int(arr_ns[i])) for i, inf in enumerate(infos)]
+        span = max(inf["done_ns"] for inf in infos) - t0
+        return lat, span, [inf["batch_size"] for inf in infos]
+
+    def run_plain(order, arr_ns):
+        n = len(order)
+        t0 = time.monotonic_ns() + 2_000_000
+        lat = [0] * n
+        for i in range(n):
+            ta = t0 + int(arr_ns[i])
+            while time.monotonic_ns() < ta:
+                pass
+            plain_one(int(order[i]))
+            lat[i] = time.monotonic_ns() - ta
+        return lat, time.monotonic_ns() - t0
+
+    def perm_order(n, seed):
+        r = np.random.default_rng(seed)
+        return np.concatenate([r.permutation(R) for _ in range((n + R - 1) // R)])[:n]
+
+    # correctness: every body once through the server and once alone, against
+    # each other, and a sample of bodies against the oracle
+    order0 = np.arange(R)
+    run_server(order0, np.zeros(R))
+    ref_bits = [b[1].numpy().view(np.uint64).copy() for b in bodies]
+    for j in range(R):
+        plain_one(j)
+        if not np.array_equal(bodies[j][1].numpy().view(np.uint64), ref_bits[j]):
+            raise SystemExit("bench: body %d differs between the server and the plain path" % j)
+    checked = 0
+    if rank == 0 and not args.skip_check:
+        import oracle
+        for j in sorted(range(R), key=lambda j: lens[j])[:: max(1, R // 24)][:24]:
+            rb, _ = oracle.parse_buffer(bytes(bodies[j][0].numpy()), b",")
+            if not np.array_equal(rb, ref_bits[j]):
+                raise SystemExit("bench: body %d differs from the oracle" % j)
+            checked += int(rb.size)
+
+    # peak: closed-loop bursts (every arrival at time 0)
+    reps = 3
+    order = perm_order(R * reps, 11)
+    lat, span, _ = run_server(order, np.zeros(len(order)))
+    peak_server = float(lens[order].sum()) / (span / 1e9) / 1e9
+    t0 = time.perf_counter()
+    for j in order[:R]:
+        plain_one(int(j))
+    peak_plain = float(lens[order[:R]].sum()) / (time.perf_counter() - t0) / 1e9
+    log("peak: server %.1f GB/s, plain %.1f GB/s" % (peak_server, peak_plain))
+
+    sampler = ClockSampler(local).start() if rank == 0 else None
+    s0 = srv.stats()
+    levels = []
+    for k, load in enumerate((0.25, 0.5, 0.9)):
+        rate = load * peak_server * 1e9 / mean_bytes  # requests per second
+        n = int(min(args.serve_max_requests, max(2 * R, rate * args.serve_seconds)))
+        r = np.random.default_rng(100 + k)
+        arr = np.cumsum(r.exponential(1e9 / rate, size=n))
+        arr -= arr[0]
+        order = perm_order(n, 200 + k)
+        nbytes = float(lens[order].sum())
+        lat_s, span_s, batch = run_server(order, arr)
+        lat_p, span_p = run_plain(order, arr)
+        levels.append({
+            "load": load, "offered_GBps": load * peak_server, "requests": n,
+            "seconds": float(arr[-1]) / 1e9,
+            "server": {"GBps": nbytes / (span_s / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_s, 50),
+                       "p99_ms": _percentile_ms(lat_s, 99), "mean_batch": float(np.mean(batch))},
+            "plain": {"GBps": nbytes / (span_p / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_p, 50),
+                      "p99_ms": _percentile_ms(lat_p, 99)},
+        })
+        log("load %.2f: %r" % (load, levels[-1]))
+    s1 = srv.stats()
+    clocks = sampler.stop() if sampler else None
+    srv.close()
+    if rank != 0:
+        return
+    top = levels[-1]
+    line = {
+        "metric": METRIC, "value": top["server"]["GBps"], "unit": UNIT, "n_gpus": world,
+        "steps": len(levels), "warmup": args.warmup, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD, "bodies": R, "mean_request_bytes": mean_bytes,
+                   "max_request_bytes": int(lens.max()), "device_budget": args.serve_budget,
+                   "max_batch": args.serve_batch, "max_inflight": args.serve_inflight,
+                   "checked_fields": checked,
+                   "l2": "requests stream from host memory; no L2 reuse between requests",
+                   "parallelism": "replicas: one independent server per GPU"},
+        "p50_ms": top["server"]["p50_ms"], "p99_ms": top["server"]["p99_ms"],
+        "peak": {"server_GBps": peak_server, "plain_GBps": peak_plain},
+        "levels": levels,
+        "e2e": {"value": top["server"]["GBps"], "unit": UNIT,
+                "h2d_bytes_per_step": int(mean_bytes), "d2h_bytes_per_step": int(9 * mean_fields),
+                "api": "fp_server_submit / fp_server_wait on pinned host buffers: every serving "
+                       "number is host to host (a step is one request, sizes are means)"},
+        "gpu_launches": 2 * (s1["launches"] - s0["launches"]),
+        "server_stats": s1,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,8 +734,15 @@ def main() -> None:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
-    ap.add_argument("--workload", choices=["bulk", "batch"], default="bulk",
-                    help="bulk: one 10M-number buffer (default); batch: 4096 uneven buffers")
+    ap.add_argument("--workload", choices=["bulk", "batch", "serve"], default="bulk",
+                    help="bulk: one 10M-number buffer (default); batch: 4096 uneven buffers; "
+                         "serve: Poisson request traces through the request server")
+    ap.add_argument("--serve-bodies", type=int, default=256, help="serve: distinct requests")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: trace length")
+    ap.add_argument("--serve-max-requests", type=int, default=60000)
+    ap.add_argument("--serve-budget", type=int, default=40_000_000_000)
+    ap.add_argument("--serve-batch", type=int, default=1024)
+    ap.add_argument("--serve-inflight", type=int, default=3)
     ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")
     ap.add_argument("--batch-bytes", type=int, default=2 << 30, help="batch: total text bytes")
     args = ap.parse_args()
@@ -572,6 +760,8 @@ def main() -> None:
         run_reference(args, world, rank)
     elif args.workload == "batch":
         run_batch(args, world, rank, dist)
+    elif args.workload == "serve":
+        run_serve(args, world, rank, dist)
     else:
         run_ours(args, world, rank, dist)
     if dist is not None:

@@ -210,9 +210,10 @@ FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
  *   delim          field separator besides '\n'
  * fp_server_submit -- queue one request and return at once.
  *   host_text    len bytes of host memory (pinned copies fastest)
- *   host_f64     host array of fp_max_fields(len) doubles (or at least as
- *                many as the text has fields: exactly that many are written)
- *   host_status  host array of as many bytes
+ *   host_f64     host array of out_cap doubles
+ *   host_status  host array of out_cap bytes
+ *   out_cap      entries the two arrays hold: the first min(fields, out_cap)
+ *                results are written (fp_max_fields(len) always suffices)
  *   request_id   receives the request's id
  *   All three arrays must stay valid and untouched until the request is
  *   waited for.  FP_ERR_BUDGET if len units exceed the whole arena.
@@ -233,7 +234,7 @@ typedef struct {
   char delim;
 } fp_server_config_t;
 typedef struct {
-  uint64_t count;      /* fields in the text (= values written) */
+  uint64_t count;      /* fields in the text (min(count, out_cap) written) */
   int32_t error;       /* fp_err_t of this request */
   uint32_t batch_size; /* requests in the launch that parsed it */
   int64_t submit_ns, admit_ns, launch_ns, done_ns;
@@ -246,7 +247,8 @@ typedef struct {
 } fp_server_stats_t;
 FP_API fp_err_t fp_server_create(const fp_server_config_t *cfg, fp_server **server);
 FP_API fp_err_t fp_server_submit(fp_server *server, const char *host_text, size_t len,
-                                 double *host_f64, uint8_t *host_status, uint64_t *request_id);
+                                 double *host_f64, uint8_t *host_status, size_t out_cap,
+                                 uint64_t *request_id);
 FP_API fp_err_t fp_server_wait(fp_server *server, uint64_t request_id, int64_t timeout_ns,
                                fp_request_info_t *info);
 FP_API fp_err_t fp_server_get_stats(fp_server *server, fp_server_stats_t *out);

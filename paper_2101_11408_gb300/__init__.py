@@ -204,8 +204,9 @@ class BatchPlan:
 class Server:
     """Continuous-batching request server on the current device
     (fp_server_*).  Requests are host tensors: uint8 text, float64 values and
-    uint8 statuses (pinned memory copies fastest); the server keeps
-    references to them until they are waited for."""
+    uint8 statuses (pinned memory copies fastest); the first min(fields,
+    len(values), len(statuses)) results are written.  The server keeps
+    references to the tensors until they are waited for."""
 
     def __init__(self, device_budget: int = 40_000_000_000, max_batch: int = 1024,
                  max_inflight: int = 3, delim=b"\n"):
@@ -222,9 +223,11 @@ class Server:
             if t.device.type != "cpu" or t.dtype != dt or not t.is_contiguous():
                 raise ValueError("server requests are contiguous host tensors")
         n = host_text.numel()
+        cap = min(host_f64.numel(), host_status.numel())
         rid = ctypes.c_uint64()
         _lib.check(_lib.load().fp_server_submit(self._h, host_text.data_ptr() if n else None, n,
-                                                host_f64.data_ptr(), host_status.data_ptr(),
+                                                host_f64.data_ptr() if cap else None,
+                                                host_status.data_ptr() if cap else None, cap,
                                                 ctypes.byref(rid)), "fp_server_submit")
         self._keep[rid.value] = (host_text, host_f64, host_status)
         return rid.value

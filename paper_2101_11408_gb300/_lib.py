@@ -125,7 +125,8 @@ def load(build_if_missing: bool = True):
         lib.fp_server_create.argtypes = [ctypes.POINTER(ServerConfig),
                                          ctypes.POINTER(ctypes.c_void_p)]
         lib.fp_server_create.restype = ctypes.c_int
-        lib.fp_server_submit.argtypes = [vp, vp, sz, vp, u8p, ctypes.POINTER(ctypes.c_uint64)]
+        lib.fp_server_submit.argtypes = [vp, vp, sz, vp, u8p, sz,
+                                         ctypes.POINTER(ctypes.c_uint64)]
         lib.fp_server_submit.restype = ctypes.c_int
         lib.fp_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int64,
                                        ctypes.POINTER(RequestInfo)]

@@ -50,6 +50,7 @@ struct Request {
   size_t len = 0;
   double* h_f64 = nullptr;
   uint8_t* h_status = nullptr;
+  size_t out_cap = 0;           // entries of h_f64 / h_status
   uint64_t off = 0, units = 0;  // arena range while admitted
   fp_request_info_t info{};
   bool done = false;
@@ -143,12 +144,13 @@ bool retire(fp_server* S, Slot& sl) {
     }
     for (size_t i = 0; i < sl.reqs.size(); i++) {
       Request* r = sl.reqs[i];
-      const uint64_t n = sl.h_counts[i];
-      r->info.count = n;
-      if (n > r->len) {  // cannot happen: a text of len bytes has at most len fields
+      const uint64_t count = sl.h_counts[i];
+      r->info.count = count;
+      if (count > r->len) {  // cannot happen: a text of len bytes has at most len fields
         r->info.error = FP_ERR_INTERNAL;
         continue;
       }
+      const uint64_t n = std::min<uint64_t>(count, r->out_cap);
       if (n) {
         if (cudaMemcpyAsync(r->h_f64, S->d_f64 + r->off, n * sizeof(double),
                             cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
@@ -371,11 +373,12 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
 }
 
 extern "C" fp_err_t fp_server_submit(fp_server* S, const char* host_text, size_t len,
-                                     double* host_f64, uint8_t* host_status,
+                                     double* host_f64, uint8_t* host_status, size_t out_cap,
                                      uint64_t* request_id) {
   if (!S || !request_id) return FP_ERR_ARG;
   if (len >= MAX_LEN) return FP_ERR_ARG;
-  if (len > 0 && (!host_text || !host_f64 || !host_status)) return FP_ERR_ARG;
+  if (len > 0 && !host_text) return FP_ERR_ARG;
+  if (out_cap > 0 && (!host_f64 || !host_status)) return FP_ERR_ARG;
   const uint64_t units = (std::max<uint64_t>(len, 1) + UNIT_ROUND - 1) / UNIT_ROUND * UNIT_ROUND;
   if (units > S->units) return FP_ERR_BUDGET;
   Request* r = new Request();
@@ -383,6 +386,7 @@ extern "C" fp_err_t fp_server_submit(fp_server* S, const char* host_text, size_t
   r->len = len;
   r->h_f64 = host_f64;
   r->h_status = host_status;
+  r->out_cap = out_cap;
   r->units = units;
   r->info.submit_ns = now_ns();
   {

@@ -241,6 +241,8 @@ def hard_case_text(n: int = 1_000_000, seed: int = SEED_BASE + 3) -> bytes:
 # ---------------------------------------------------------------------------
 
 def _pool_text(nbytes: int, seed: int, sep: bytes = b"\n", cols: int = 1) -> bytes:
+    """About nbytes of uniform [0,1) %.17g values (the 10,000-number
+    workload's content), one per line, or `cols` comma-separated per row."""
     n = nbytes // 19 + 16
     vals = uniform_lines(n, seed)
     if cols == 1:
@@ -286,7 +288,7 @@ def lognormal_sizes(count: int, total: int, lo: int, hi: int, sigma: float,
 def batch_buffers(count: int = 4096, total: int = 2 << 30, lo: int = 1 << 10,
                   hi: int = 64 << 20, seed: int = SEED_BASE + 4,
                   pool_bytes: int = 64 << 20) -> list[bytes]:
-    """count independent newline-separated uniform buffers, lognormal sizes
+    """count independent newline-separated buffers, lognormal sizes
     (sigma 2.0) in [lo, hi] summing to about `total` bytes.  Content is cut
     from a pool of uniform %.17g text."""
     sizes = lognormal_sizes(count, total, lo, hi, 2.0, seed)
