@@ -37,12 +37,38 @@ UNIT = "GB/s"
 WORKLOAD = ("bulk mixed text, 10M numbers newline-separated: 40% uniform [0,1) at 17 "
             "significant digits, 30% coordinates (lat/lon, 12-16 fractional digits), 20% "
             "integers in [0,2^63), 10% d.ddddE+-xxx with exponents in [-340,320]")
+UNIFORM_WORKLOAD = ("uniform: 10,000 doubles uniform in [0,1) printed with %.17g, newline-separated "
+                    "(about 190 KB), one buffer")
+HARD_WORKLOAD = ("hard cases, 1M strings: 50% with 20-800 significant digits, 30% exact midpoints "
+                 "between adjacent doubles in full decimal (exact, +1, -1 in the last digit), 20% "
+                 "subnormal and near-DBL_MAX values with 17-25 digits")
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1000 * 1000
 
 
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Seed of rank's shard: every rank parses its own, independent input."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's);
+    x itself when not distributed."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(world: int, bytes_per_rank: int, steps: int, max_ms: float) -> float:
+    """Whole-job GB/s: every rank's bytes over the slowest rank's time."""
+    return world * bytes_per_rank * steps / (max_ms / 1e3) / 1e9
 
 
 def measured_hbm_peak():
@@ -58,13 +84,27 @@ PARSE_KERNEL_SOURCES = ("fp_parse_kernel.cu", "fp_device.cuh", "fp_sync.cuh", "f
                         "pow5_table.inc")
 
 
-def kernel_source_sha() -> str:
-    """Hash of the sources the parse kernel is compiled from."""
+def _code_only(src: bytes) -> bytes:
+    """C/C++ source with comments and blank lines removed (a comment edit
+    does not change the compiled kernel)."""
+    import re
+    text = src.decode("utf-8", "replace")
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    lines = [ln.rstrip() for ln in text.splitlines()]
+    return "\n".join(ln for ln in lines if ln.strip()).encode()
+
+
+def kernel_source_sha(read=None) -> str:
+    """Hash of the code (comments removed) the parse kernel is compiled from."""
     d = os.path.join(ROOT, "paper_2101_11408_gb300", "csrc")
+    if read is None:
+        def read(name):
+            with open(os.path.join(d, name), "rb") as f:
+                return f.read()
     h = hashlib.sha256()
     for name in PARSE_KERNEL_SOURCES:
-        with open(os.path.join(d, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        h.update(name.encode() + b"\0" + _code_only(read(name)))
     return h.hexdigest()[:16]
 
 
@@ -79,7 +119,12 @@ def profiled_traffic(kernel: str):
         for line in f:
             if ":" in line and line.strip().startswith("- "):
                 k, v = line.strip()[2:].split(":", 1)
-                vals[k.strip()] = v.strip().strip("`")
+                v = v.strip()
+                if v.startswith("`"):
+                    v = v[1:].split("`", 1)[0]
+                else:
+                    v = v.split(" ", 1)[0] if v else v
+                vals[k.strip()] = v
     if vals.get("source_sha") != kernel_source_sha():
         return None
     try:
@@ -157,14 +202,24 @@ def oracle_time(sample: bytes, threads: int) -> float:
     return time.perf_counter() - t
 
 
-def cpu_baseline(text: bytes, target_bytes: int = 64 << 20) -> dict:
+def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0) -> dict:
+    """The oracle on every host core, on a prefix of the workload sized for
+    about `seconds` of work (from a 1 MB calibration), repeated when the
+    whole text takes less."""
     cores = os.cpu_count() or 1
-    sample = cut_at_line(text, target_bytes)
-    dt = oracle_time(sample, cores)
-    return {"value": len(sample) / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "first %d bytes (%.1f MB, cut at a line break) of the bulk mixed "
-                      "workload, one pass, %d threads, %.2f s" % (len(sample), len(sample) / 1e6,
-                                                                  cores, dt)}
+    calib = cut_at_line(text, 1 << 20)
+    rate = len(calib) / oracle_time(calib, cores)
+    sample = cut_at_line(text, int(min(64 << 20, max(1 << 20, rate * seconds))))
+    passes = max(1, int(rate * seconds / max(len(sample), 1) / 4))
+    t = time.perf_counter()
+    for _ in range(passes):
+        oracle_time(sample, cores)
+    dt = time.perf_counter() - t
+    return {"value": passes * len(sample) / dt / 1e9, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": "first %d bytes (%.2f MB, cut at a line break) of the %s workload, %d "
+                      "pass(es), %d threads, %.2f s" % (len(sample), len(sample) / 1e6, kind,
+                                                      passes, cores, dt)}
 
 
 def run_reference(args, world, rank) -> None:
@@ -173,7 +228,13 @@ def run_reference(args, world, rank) -> None:
         return
     from paper_2101_11408_gb300 import workloads
     cores = os.cpu_count() or 1
-    text = workloads.bulk_mixed_text(args.n, workloads.SEED_BASE + 2)
+    kind = args.workload if args.workload in ("uniform", "hard") else "bulk"
+    gen, n_default, wl_desc, sid = {
+        "uniform": (workloads.uniform_text, 10_000, UNIFORM_WORKLOAD, 1),
+        "bulk": (workloads.bulk_mixed_text, 10_000_000, WORKLOAD, 2),
+        "hard": (workloads.hard_case_text, 1_000_000, HARD_WORKLOAD, 3)}[kind]
+    n = args.n or n_default
+    text = gen(n, workloads.SEED_BASE + sid)
     calib = cut_at_line(text, 4 << 20)
     rate = len(calib) / oracle_time(calib, cores)
     per_step = int(min(64 << 20, max(1 << 20, rate * args.reference_seconds /
@@ -187,12 +248,12 @@ def run_reference(args, world, rank) -> None:
     dt = time.perf_counter() - t
     value = len(sample) * args.steps / dt / 1e9
     desc = ("oracle (exact big-number C parser) on %d host threads; each step parses the "
-            "first %d bytes (cut at a line break) of the bulk mixed workload" % (cores, len(sample)))
+            "first %d bytes (cut at a line break) of the %s workload" % (cores, len(sample), kind))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "numbers": args.n,
+        "data": "synthetic", "config": {"workload": wl_desc, "numbers": n,
                                         "text_bytes": len(text)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": desc},
@@ -210,9 +271,16 @@ def run_ours(args, world, rank, dist) -> None:
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     fp._lib.load()
-    seed = workloads.SEED_BASE + 2 + 1000 * rank
+    kind = args.workload
+    seed = shard_seed(workloads.SEED_BASE + {"uniform": 1, "bulk": 2, "hard": 3}[kind], rank)
+    gen = {"uniform": workloads.uniform_text, "bulk": workloads.bulk_mixed_text,
+           "hard": workloads.hard_case_text}[kind]
+    n_default = {"uniform": 10_000, "bulk": 10_000_000, "hard": 1_000_000}[kind]
+    desc = {"uniform": UNIFORM_WORKLOAD, "bulk": WORKLOAD, "hard": HARD_WORKLOAD}[kind]
+    # a small input sits in L2: flush it between steps and time each step alone
+    flush = kind == "uniform"
     t = time.perf_counter()
-    text = workloads.bulk_mixed_text(args.n, seed)
+    text = gen(args.n or n_default, seed)
     log("rank %d: generated %d bytes in %.1f s" % (rank, len(text), time.perf_counter() - t))
     B = len(text)
     host_text = torch.frombuffer(bytearray(text), dtype=torch.uint8)
@@ -252,27 +320,40 @@ def run_ours(args, world, rank, dist) -> None:
 
     fp.timing_enable(True)
     fp.timing_read(stream)  # reset the sums
+    s_before = fp.stats(reset=True, stream=stream)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    step_ms = []
+    if flush:
+        scrub = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for a, b in evs:
+            scrub.fill_(1)  # evict the text and results from L2, outside the timed pair
+            a.record(stream)
+            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        elapsed_ms = sum(step_ms)
+    else:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        elapsed_ms = e0.elapsed_time(e1)
     if dist is not None:
         dist.barrier()
-    elapsed_ms = e0.elapsed_time(e1)
     kt = fp.timing_read(stream)
     fp.timing_enable(False)
     clocks = sampler.stop() if sampler else None
     if dist is not None:
-        tt = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
-    value = world * B * args.steps / (elapsed_ms / 1e3) / 1e9
+        elapsed_ms = max_over_ranks(dist, elapsed_ms, dev)
+    value = whole_job_gbs(world, B, args.steps, elapsed_ms)
 
     # end to end: host text -> device, parse, results -> host, every step
     e2e = None
@@ -291,9 +372,7 @@ def run_ours(args, world, rank, dist) -> None:
             n_host = fp.parse_f64_host_into(h_text, h_out, h_st, stream=stream)
         dt = time.perf_counter() - t
         if dist is not None:
-            tt = torch.tensor([dt], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+            dt = max_over_ranks(dist, dt, dev)
         assert n_host == N
         if rank == 0 and check_fields:
             assert np.array_equal(h_out[:check_fields].numpy().view(np.uint64),
@@ -309,17 +388,21 @@ def run_ours(args, world, rank, dist) -> None:
     parse_ms = kt["parse_ms"] / max(kt["calls"], 1)
     fb_ms = kt["fallback_ms"] / max(kt["calls"], 1)
     achieved = alg_bytes / (parse_ms / 1e3) / 1e9
-    traffic = profiled_traffic("parse_kernel")
+    traffic = profiled_traffic("parse_kernel") if kind == "bulk" else None
     cfg = fp.get_config()
     s = fp.stats(reset=True, stream=stream)
+    l2 = ("no flush: each step reads %.0f MB of text and writes %.0f MB of results, more than "
+          "the %.0f MB L2" % (B / 1e6, 9 * N / 1e6, L2_BYTES / 1e6))
+    if flush:
+        l2 = ("flushed: a %.0f MB device buffer is written before every step, outside that "
+              "step's event pair" % (2 * L2_BYTES / 1e6))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "numbers": N, "text_bytes": B,
+        "config": {"workload": desc, "numbers": N, "text_bytes": B,
                    "mfloats_per_s": world * N * args.steps / (elapsed_ms / 1e3) / 1e6,
-                   "l2": "no flush: each step reads %.0f MB of text and writes %.0f MB of "
-                         "results, more than the %.0f MB L2" % (B / 1e6, 9 * N / 1e6, L2_BYTES / 1e6),
+                   "l2": l2,
                    "parallelism": "replicas: one independent shard per GPU",
                    "chunk_bytes": cfg["chunk_bytes"], "ctas_per_sm": cfg["ctas_per_sm"],
                    "checked_fields": check_fields},
@@ -335,10 +418,20 @@ def run_ours(args, world, rank, dist) -> None:
             "fields", "one_multiply", "two_multiplies", "general_tokenizer", "long_fields",
             "long_settled", "fallback", "fallback_bignum")},
     }
+    if step_ms:
+        line["us_per_call"] = {"median": 1e3 * statistics.median(step_ms),
+                               "p99": 1e3 * float(np.percentile(step_ms, 99)),
+                               "min": 1e3 * min(step_ms)}
+    if kind == "hard":
+        fb = s["fallback"] // max(s["calls"], 1)
+        line["fallback"] = {"rate": fb / max(N, 1), "items_per_step": fb,
+                            "items_per_s": fb / (fb_ms / 1e3) if fb_ms > 0 else None,
+                            "kernel_ms": fb_ms,
+                            "long_field_rate": (s["long_fields"] // max(s["calls"], 1)) / max(N, 1)}
     if e2e:
         line["e2e"] = e2e
     if not args.skip_baseline:
-        line["cpu_baseline"] = cpu_baseline(text)
+        line["cpu_baseline"] = cpu_baseline(text, kind)
     print(json.dumps(line), flush=True)
 
 
@@ -376,7 +469,7 @@ def run_batch(args, world, rank, dist) -> None:
     fp._lib.load()
     t = time.perf_counter()
     texts = workloads.batch_buffers(args.nbuf, args.batch_bytes,
-                                    seed=workloads.SEED_BASE + 4 + 1000 * rank)
+                                    seed=shard_seed(workloads.SEED_BASE + 4, rank))
     packed, starts = workloads.pack_buffers(texts)
     lens = [len(x) for x in texts]
     B = sum(lens)
@@ -456,9 +549,7 @@ def run_batch(args, world, rank, dist) -> None:
     ms_graph = _time_steps(torch, stream, lambda: plan_g.launch(stream), args.steps, args.warmup)
     if dist is not None:
         dist.barrier()
-        tt = torch.tensor([ms_graph], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_graph = float(tt.item())
+        ms_graph = max_over_ranks(dist, ms_graph, dev)
     clocks = sampler.stop() if sampler else None
     few = max(3, min(args.steps, 10))
     ms_plan = _time_steps(torch, stream, lambda: plan_p.launch(stream), args.steps, args.warmup)
@@ -561,7 +652,7 @@ def run_serve(args, world, rank, dist) -> None:
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     lib = fp._lib.load()
-    rng = np.random.default_rng(workloads.SEED_BASE + 6 + 1000 * rank)
+    rng = np.random.default_rng(shard_seed(workloads.SEED_BASE + 6, rank))
     R = args.serve_bodies
     sizes = np.clip(np.exp(np.log(1 << 20) + 1.85 * rng.standard_normal(R)), 4 << 10,
                     256 << 20).astype(np.int64)
@@ -725,7 +816,8 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=10_000_000, help="numbers per shard")
+    ap.add_argument("--n", type=int, default=0,
+                    help="numbers per shard (0: the workload's own size)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--clock-settle", type=float, default=1.0,
                     help="seconds of untimed steps before the timed region")
@@ -734,9 +826,11 @@ def main() -> None:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
-    ap.add_argument("--workload", choices=["bulk", "batch", "serve"], default="bulk",
-                    help="bulk: one 10M-number buffer (default); batch: 4096 uneven buffers; "
-                         "serve: Poisson request traces through the request server")
+    ap.add_argument("--workload", choices=["bulk", "uniform", "hard", "batch", "serve"],
+                    default="bulk",
+                    help="bulk: one 10M-number buffer (default); uniform: 10,000 numbers; hard: "
+                         "1M hard cases; batch: 4096 uneven buffers; serve: Poisson request "
+                         "traces through the request server")
     ap.add_argument("--serve-bodies", type=int, default=256, help="serve: distinct requests")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: trace length")
     ap.add_argument("--serve-max-requests", type=int, default=60000)

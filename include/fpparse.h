@@ -6,8 +6,8 @@
  * Section 1 of Lemire, "Number Parsing at a Gigabyte per Second").  Every
  * step runs in CUDA kernels on the device: field indexing, significand and
  * exponent parsing (Section 4), the truncated power-of-five product of
- * Algorithm 1 (Sections 6-9), the 19-digit truncation check for long
- * significands (Section 10) and an exact big-number fallback for the rare
+ * Algorithm 1 (Section 5, justified in Sections 6-10), the 19-digit truncation check for long
+ * significands (Section 11) and an exact big-number fallback for the rare
  * cases those cannot settle.  There is no CPU fallback.
  *
  * Conventions shared by every entry point
@@ -31,7 +31,7 @@
  *
  * Grammar of a field (Section 4; the library's reading):
  *     [ \t\r]*  [+-]?  ( d+ ( '.' d* )? | '.' d+ )  ( [eE] [+-]? d+ )?  [ \t\r]*
- * Digits may be arbitrarily many (Section 10: up to 768 significant digits
+ * Digits may be arbitrarily many (Section 11: up to 768 significant digits
  * can matter; all of them are honoured).  An explicit exponent of magnitude
  * above 10^15 saturates, which is exact for fields shorter than ~10^15 bytes.
  *
@@ -94,7 +94,7 @@ typedef struct {
     uint64_t bytes;           /* text bytes parsed                               */
     uint64_t one_multiply;    /* fast-path Algorithm 1 runs with one 64x64 product */
     uint64_t two_multiplies;  /* Algorithm 1 runs that needed the second product   */
-    uint64_t long_fields;     /* more than 19 significant digits (Section 10)    */
+    uint64_t long_fields;     /* more than 19 significant digits (Section 11)    */
     uint64_t long_settled;    /* ... settled by the w / w+1 check                */
     uint64_t fallback;        /* fields resolved by the exact fallback kernel    */
     uint64_t fallback_bignum; /* ... that needed a big-number comparison         */
@@ -111,7 +111,7 @@ typedef struct {
 FP_API size_t fp_max_fields(size_t len);
 
 /*
- * fp_parse_f64 -- parse every field of one buffer (Sections 4-10).
+ * fp_parse_f64 -- parse every field of one buffer (Sections 4-11).
  *   text        device pointer to len bytes (any alignment; may be NULL iff len == 0)
  *   len         bytes in the buffer (< 2^40)
  *   delim       the second separator besides '\n'

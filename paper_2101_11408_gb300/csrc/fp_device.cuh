@@ -1,8 +1,8 @@
 // fp_device.cuh -- device-side building blocks of the parser (sm_103a).
 //
-// Algorithm 1 of the paper (Sections 6-9) on a decimal significand w < 2^64
+// Algorithm 1 of the paper (Section 5; its steps are justified in Sections 6-10) on a decimal significand w < 2^64
 // and exponent q, against the 128-bit power-of-five table; the field
-// grammar of Section 4; the 19-digit truncation check of Section 10.
+// grammar of Section 4; the 19-digit truncation check of Section 11.
 #pragma once
 #include <cstdint>
 
@@ -85,7 +85,7 @@ FP_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 // The power-of-five table as the kernels see it: the high words, possibly a
 // dense copy in shared memory (hi_stride 1) or the interleaved table itself
 // (hi_stride 2), and the low words read from the interleaved table (only
-// needed for the second product, Section 7).
+// needed for the second product, Sections 7-8).
 struct Pow5 {
   const uint64_t* hi;
   int hi_stride;
@@ -113,7 +113,7 @@ struct ElResult {
 FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort) {
   ElResult r;
   r.two_mul = 0;
-  // Normalise the decimal significand into [2^63, 2^64) (Section 7).
+  // Normalise the decimal significand into [2^63, 2^64) (Algorithm 1).
   int l = clz64(w);
   w <<= l;
   const uint64_t thi = tab.hi[(q - FP_POW5_QMIN) * tab.hi_stride];
@@ -121,7 +121,7 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   uint64_t lo = w * thi;
   uint64_t hi = mulhi64(w, thi);
   // Unless the low 9 bits of the high word are all ones, the top 55 bits
-  // are exact and one product suffices (Sections 7 and 8).
+  // are exact and one product suffices (Sections 8 and 9).
   if ((hi & 0x1FF) == 0x1FF) {
     const uint64_t tlo = load_lo(tab.lo + 2 * (q - FP_POW5_QMIN));
     uint64_t h2 = mulhi64(w, tlo);
@@ -140,12 +140,12 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   const int u = (int)(hi >> 63);
   uint64_t m = hi >> (u + 9);
   // Biased binary exponent: floor(log2 10^q) = (217706 q) >> 16 for
-  // q in (-400, 350) (Section 9), plus 63 - l + u, plus the bias 1023.
+  // q in (-400, 350) (Section 10), plus 63 - l + u, plus the bias 1023.
   int E = ((217706 * q) >> 16) + 63 - l + u + 1023;
   if (E <= 0) {
-    // Subnormal (Section 8.3): the 54-bit m sits 2-E places above the
+    // Subnormal (Section 9.3): the 54-bit m sits 2-E places above the
     // 2^-1074 grid; shift by 1-E, then round on the last bit.  No ties are
-    // possible here (Section 5).  Rounding up to 2^52 yields the smallest
+    // possible here (Section 6).  Rounding up to 2^52 yields the smallest
     // normal number, whose bit pattern is that same integer.
     if (E <= -63) {
       r.bits = 0;
@@ -157,7 +157,7 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
     r.bits = m;
     return r;
   }
-  // Ties to even (Sections 7.1 and 8.1): only for q in [-4, 23], when the
+  // Ties to even (Sections 8.1 and 9.1): only for q in [-4, 23], when the
   // product below m's lowest bit is zero (second word <= 1 and the bits of
   // the high word under m all zero) and m ends in binary 01: clear the
   // rounding bit so that the round step does not go up.
@@ -211,7 +211,7 @@ struct FieldResult {
 // accumulated into w; later digits only move the exponent (integer part)
 // and feed a sticky flag.  With a nonzero sticky flag the value lies in
 // (w 10^q, (w+1) 10^q), and if both ends round to the same double that is
-// the answer (Section 10); otherwise the field is left pending.
+// the answer (Section 11); otherwise the field is left pending.
 FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   FieldResult r;
   r.two_mul = 0;
@@ -315,7 +315,7 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
 
 
 // ---------------------------------------------------------------------------
-// SWAR fast path (Section 4; eight digits at a time as in the appendix's
+// SWAR fast path (Section 4; eight digits at a time as in Appendix D's
 // string functions, with GPU byte-dot-product instructions for the values)
 // ---------------------------------------------------------------------------
 

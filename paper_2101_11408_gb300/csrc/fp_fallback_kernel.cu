@@ -1,16 +1,16 @@
 // fp_fallback_kernel.cu -- exact resolution of the fields the parse kernel
-// could not settle (Section 10 "higher-precision approach"; the design here
+// could not settle (Section 11 "higher-precision approach"; the design here
 // is this library's own: a big-number comparison against midpoints).
 //
 // A field arrives here when it is longer than the parse kernel's limit, when
 // Algorithm 1 gave up (second product word all ones outside [-27, 55]), or
-// when its 19-digit truncation w and w+1 round differently (Section 10).
+// when its 19-digit truncation w and w+1 round differently (Section 11).
 //
 // Method, per field (one thread per field, limbs in shared memory):
 //   1. tokenize the whole field from global memory (Section 4 grammar);
 //   2. D = its first 800 significant digits, with one extra digit 1 appended
 //      when any later digit is nonzero.  Every midpoint between adjacent
-//      doubles has at most 768 significant digits (Section 10), so D 10^E and
+//      doubles has at most 768 significant digits (Section 11), so D 10^E and
 //      the exact value lie on the same side of every midpoint;
 //   3. candidate x = the rounded truncated product of the 19-digit prefix
 //      (within one unit of the answer);

@@ -15,7 +15,7 @@
 //   3. parse  : one thread per field: the SWAR tokenizer for the common
 //               shape (eight digits per step), else the general tokenizer of
 //               Section 4; quick exits and Algorithm 1 against the table
-//               held in shared memory; the w / w+1 check of Section 10;
+//               held in shared memory; the w / w+1 check of Section 11;
 //               results are staged in shared memory;
 //   4. prefix : look back over the preceding chunks for this chunk's first
 //               field index (after parsing, when the predecessors have mostly

@@ -1,13 +1,13 @@
 """Generate pow5_table.inc: the 651 x 128-bit power-of-five table T[q].
 
 T[q] for q in [-342, 308] (Appendix "Table Generation Script" defines the
-three regimes; Sections 7 and 8 derive them):
+three regimes; Sections 8 and 9 derive them):
 
-* q >= 0 (Section 7): 5^q scaled by a power of two into [2^127, 2^128),
+* q >= 0 (Section 8): 5^q scaled by a power of two into [2^127, 2^128),
   truncated (bits below the top 128 dropped).
-* -27 <= q <= -1 (Section 8.1): the rounded-up reciprocal
+* -27 <= q <= -1 (Section 9.1): the rounded-up reciprocal
   ceil(2^b / 5^-q) with b = 127 + ceil(log2 5^-q); it lies in [2^127, 2^128).
-* q < -27 (Section 8.2): the top 128 bits of ceil(2^(2b) / 5^-q) with
+* q < -27 (Section 9.2): the top 128 bits of ceil(2^(2b) / 5^-q) with
   b = 64 + ceil(log2 5^-q).
 
 Each entry is stored as two 64-bit words, the more significant first, at
@@ -54,7 +54,7 @@ def render() -> str:
     lines = [
         "/* Generated by gen_pow5_table.py -- do not edit.",
         " * T[q], q in [-342, 308]: word 2*(q+342) is the high 64 bits, word",
-        " * 2*(q+342)+1 the low 64 bits (Appendix table script; Sections 7-8).",
+        " * 2*(q+342)+1 the low 64 bits (Appendix B; Sections 8-9).",
         " * Use as:  const unsigned long long t[2 * FP_POW5_ENTRIES] = { FP_POW5_TABLE_VALUES }; */",
         "#define FP_POW5_QMIN (-342)",
         "#define FP_POW5_QMAX 308",

@@ -3,7 +3,7 @@
 This module only draws random numbers and prints them as text; it holds none
 of the parsing arithmetic, and both the oracle and the GPU path consume its
 output.  The paper measures on the "canada" coordinate file, a "uniform"
-[0,1) set and an "integer" set (Section 11); those files are not available,
+[0,1) set and an "integer" set (Section 12); those files are not available,
 so the generators below stand in for them:
 
 * ``uniform_text``  -- %.17g of U[0,1) doubles, newline-separated (the

@@ -264,7 +264,7 @@ def test_stats_path_frequencies():
 
 
 def test_long_check_settles_most():
-    """Section 10: truncating to 19 digits and checking w and w+1 settles
+    """Section 11: truncating to 19 digits and checking w and w+1 settles
     about 99.7-99.8% of long random significands."""
     rnd = random.Random(8)
     lines = []

@@ -83,7 +83,7 @@ def test_paper_worked_examples(inp, expected, where):
 
 
 def test_768_digit_midpoint_rounds_up():
-    """Section 10: 2^-1022 + 2^-1074 + 2^-1075 needs 768 significant digits and
+    """Section 11: 2^-1022 + 2^-1074 + 2^-1075 needs 768 significant digits and
     is a tie that rounds to the even neighbour 2^-1022 + 2^-1073."""
     V = Fraction(2) ** -1022 + Fraction(2) ** -1074 + Fraction(2) ** -1075
     n = V.numerator * 5 ** 1075  # V = n / 10^1075 exactly
@@ -116,7 +116,7 @@ def test_exact_integers_up_to_2_53():
 
 
 def test_exact_powers_of_ten():
-    """Section 5: 10^q is exact in binary64 for q in [0, 22], not for 23."""
+    """Section 6: 10^q is exact in binary64 for q in [0, 22], not for 23."""
     for k in range(0, 23):
         for s in ("1e%d" % k, "1" + "0" * k, "0.1e%d" % (k + 1)):
             b, st = parse(s)

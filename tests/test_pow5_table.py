@@ -31,7 +31,7 @@ def test_generated_include_is_current():
 
 
 def test_table_size():
-    """651 entries of 16 bytes (Section 11 quotes about 10 KiB)."""
+    """651 entries of 16 bytes (Section 12 quotes about 10 KiB)."""
     t = gen.table()
     assert len(t) == 651 and 16 * len(t) == 10416
 
@@ -56,7 +56,7 @@ def test_every_entry_is_normalised():
 
 
 def test_positive_powers_exact_up_to_55():
-    """Section 7: 5^q < 2^128 for q <= 55, so the stored 128 bits are exact."""
+    """Section 8: 5^q < 2^128 for q <= 55, so the stored 128 bits are exact."""
     for q in range(0, 56):
         v = gen.table_entry(q)
         p = 5 ** q
@@ -65,7 +65,7 @@ def test_positive_powers_exact_up_to_55():
 
 
 def test_near_reciprocals_are_ceilings():
-    """Section 8.1: c = ceil(2^b / 5^-q), b = 127 + ceil(log2 5^-q)."""
+    """Section 9.1: c = ceil(2^b / 5^-q), b = 127 + ceil(log2 5^-q)."""
     for q in range(-27, 0):
         d = 5 ** (-q)
         c = gen.table_entry(q)
@@ -95,7 +95,7 @@ def test_insane_table(row):
 
 
 def test_near_high_words_have_few_trailing_zeros():
-    """Section 8.1: the high words for q in [-17,-1] have at most 2 trailing
+    """Section 9.1: the high words for q in [-17,-1] have at most 2 trailing
     zeros, and the odd ones are exactly the rows of Table insane."""
     odd = []
     for q in range(-17, 0):
@@ -107,7 +107,7 @@ def test_near_high_words_have_few_trailing_zeros():
 
 
 def test_exponent_formula():
-    """Section 9: (217706 q) >> 16 == q + floor(log2 5^q) == floor(log2 10^q)
+    """Section 10: (217706 q) >> 16 == q + floor(log2 5^q) == floor(log2 10^q)
     for every q in (-400, 350)."""
     for q in range(-399, 350):
         if q >= 0:
