@@ -1,4 +1,4 @@
-"""Exact CPU oracle for decimal text -> binary64 parsing.
+"""Exact CPU oracle for decimal text -> binary64 (and binary32) parsing.
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may use this package; the library under
@@ -7,11 +7,15 @@ CPU-baseline leg of ``bench.py`` may use this package; the library under
 through ctypes.
 
 Functions follow the problem statement of the paper (Section 1: nearest
-binary64, ties to even; Section 4: the string grammar and its explicit
-bounds).  Parity status: pinned by the paper's worked examples, by closed
-forms (exact integers, exact powers of ten, constructed midpoints between
-adjacent doubles) and by CPython's correctly rounded ``float()``; see
-``tests/test_oracle_pins.py``.
+binary64, ties to even; Section 2: the binary64 and binary32 formats;
+Section 4: the string grammar and its explicit bounds).  Parity status: the
+binary64 functions are pinned by the paper's worked examples, by closed forms
+(exact integers, exact powers of ten, constructed midpoints between adjacent
+doubles) and by CPython's correctly rounded ``float()``
+(``tests/test_oracle_pins.py``); the binary32 functions by float32 round
+trips, constructed float32 midpoints, exact integers and powers of ten,
+range boundaries and a neighbour-comparison brute force
+(``tests/test_oracle_f32_pins.py``).
 """
 from __future__ import annotations
 
@@ -63,6 +67,12 @@ def _load():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
                 ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
             lib.oracle_parse_buffer.restype = ctypes.c_int
+            lib.oracle_parse_field_f32.argtypes = [
+                ctypes.c_char_p, ctypes.c_size_t,
+                ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint8)]
+            lib.oracle_parse_field_f32.restype = ctypes.c_int
+            lib.oracle_parse_buffer_f32.argtypes = lib.oracle_parse_buffer.argtypes
+            lib.oracle_parse_buffer_f32.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -79,17 +89,30 @@ def parse_field(s) -> tuple[int, int]:
     return bits.value, st.value
 
 
+def parse_field_f32(s) -> tuple[int, int]:
+    """Parse one field to binary32; returns (bit pattern, status)."""
+    if isinstance(s, str):
+        s = s.encode("utf-8")
+    lib = _load()
+    bits = ctypes.c_uint32()
+    st = ctypes.c_uint8()
+    if lib.oracle_parse_field_f32(s, len(s), ctypes.byref(bits), ctypes.byref(st)):
+        raise MemoryError("oracle ran out of memory")
+    return bits.value, st.value
+
+
 def count_fields(text: bytes, delim: bytes = b"\n") -> int:
     lib = _load()
     buf = np.frombuffer(text, dtype=np.uint8)
     return int(lib.oracle_count_fields(buf.ctypes.data, len(text), delim))
 
 
-def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None):
+def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None, f32: bool = False):
     """Parse every field of a buffer.
 
-    Returns (bits: uint64 array, status: uint8 array).  ``text`` is bytes or a
-    uint8 numpy array.
+    Returns (bits: uint64 array, status: uint8 array), or with f32=True
+    (bits: uint32 array of binary32 patterns, status).  ``text`` is bytes or
+    a uint8 numpy array.
     """
     lib = _load()
     if isinstance(text, (bytes, bytearray, memoryview)):
@@ -99,11 +122,12 @@ def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None):
     if nthreads is None:
         nthreads = os.cpu_count() or 1
     n = int(lib.oracle_count_fields(buf.ctypes.data, buf.size, delim))
-    bits = np.zeros(max(n, 1), dtype=np.uint64)
+    bits = np.zeros(max(n, 1), dtype=np.uint32 if f32 else np.uint64)
     st = np.zeros(max(n, 1), dtype=np.uint8)
     cnt = ctypes.c_uint64()
-    rc = lib.oracle_parse_buffer(buf.ctypes.data, buf.size, delim, bits.ctypes.data,
-                                 st.ctypes.data, bits.size, ctypes.byref(cnt), int(nthreads))
+    fn = lib.oracle_parse_buffer_f32 if f32 else lib.oracle_parse_buffer
+    rc = fn(buf.ctypes.data, buf.size, delim, bits.ctypes.data, st.ctypes.data, bits.size,
+            ctypes.byref(cnt), int(nthreads))
     if rc:
         raise MemoryError("oracle failed (capacity or memory)")
     assert cnt.value == n

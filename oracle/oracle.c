@@ -1,5 +1,6 @@
 /*
- * oracle.c -- exact decimal text -> nearest IEEE-754 binary64 (ties to even).
+ * oracle.c -- exact decimal text -> nearest IEEE-754 binary64 or binary32
+ * (ties to even).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the parity oracle for the GPU path:
  * only the test suite, the smoke check and the CPU-baseline leg of the
@@ -7,8 +8,9 @@
  * the CUDA library, and the CUDA library never calls it.
  *
  * What it computes is the plain definition of the problem (Section 1 and
- * Section 2 of the paper): the binary64 value nearest to the exact rational
- * value of the decimal string, with ties broken toward the even significand,
+ * Section 2 of the paper): the binary64 (or binary32, Section 2's other
+ * format) value nearest to the exact rational value of the decimal string,
+ * with ties broken toward the even significand,
  * signed zero and signed infinity kept (the sign is applied last, Algorithm 1
  * handles negatives by flipping the sign bit).  No table, no truncated
  * product, no fast path: the decimal value is held as an exact ratio of two
@@ -39,6 +41,21 @@ enum { OR_OK = 0, OR_INVALID = 1, OR_OVERFLOW = 2, OR_UNDERFLOW = 3 };
 #define OR_EXP_SAT 1000000000000000LL /* 10^15 */
 #define OR_QNAN_BITS 0x7FF8000000000000ULL
 #define OR_INF_BITS 0x7FF0000000000000ULL
+
+/* An IEEE-754 binary format (Section 2): p significand bits (the leading
+ * one included), normal exponents emin..emax, and the decimal-magnitude
+ * limits of the cheap range exits in convert_exact.                        */
+typedef struct {
+    int p;
+    int emin, emax;
+    int dec_ovf; /* nd-1+E >= dec_ovf  =>  V >= 10^dec_ovf, beyond the largest finite */
+    int dec_unf; /* nd+E <= dec_unf    =>  V < 10^dec_unf, below half the smallest subnormal */
+    uint64_t inf_bits, qnan_bits, sign_bit;
+} fmt;
+/* 1e309 > 2^1024 and 1e-324 < 2^-1075; 1e39 > 2^128 and 1e-46 < 2^-150. */
+static const fmt FMT64 = {53, -1022, 1023, 309, -324, OR_INF_BITS, OR_QNAN_BITS,
+                          0x8000000000000000ULL};
+static const fmt FMT32 = {24, -126, 127, 39, -46, 0x7F800000ULL, 0x7FC00000ULL, 0x80000000ULL};
 
 /* ------------------------------------------------------------------------ */
 /* Arbitrary-precision naturals: little-endian base-2^32 limbs, normalised   */
@@ -249,22 +266,22 @@ static int digit_at(const token *t, size_t k) {
 /* ------------------------------------------------------------------------ */
 
 /*
- * Nearest binary64 to D * 10^E for a natural D given by its significant
- * digits [first, last] of the token (first digit nonzero, last digit
- * nonzero).  Returns the unsigned bit pattern; writes the status.
+ * Nearest value of format f to D * 10^E for a natural D given by its
+ * significant digits [first, last] of the token (first digit nonzero, last
+ * digit nonzero).  Returns the unsigned bit pattern; writes the status.
  */
 static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t E,
-                              uint8_t *status, int *err) {
+                              const fmt *f, uint8_t *status, int *err) {
     size_t nd = last - first + 1;
     /* Cheap range exits, each by a wide margin:
      *   10^(nd-1+E) <= V < 10^(nd+E).
-     *   nd-1+E >= 309  =>  V >= 1e309 > 2^1024: rounds to infinity.
-     *   nd+E <= -324   =>  V < 1e-324 < 2^-1075: rounds to zero.            */
-    if ((int64_t)nd - 1 + E >= 309) {
+     *   nd-1+E >= dec_ovf  =>  V >= 10^dec_ovf > 2^(emax+1): rounds to infinity.
+     *   nd+E <= dec_unf    =>  V < 10^dec_unf < 2^(emin-p): rounds to zero.  */
+    if ((int64_t)nd - 1 + E >= f->dec_ovf) {
         *status = OR_OVERFLOW;
-        return OR_INF_BITS;
+        return f->inf_bits;
     }
-    if ((int64_t)nd + E <= -324) {
+    if ((int64_t)nd + E <= f->dec_unf) {
         *status = OR_UNDERFLOW;
         return 0;
     }
@@ -305,19 +322,20 @@ static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t
     }
     if (big_cmp(&num, &den) < 0) k -= 1;
 
-    /* Unit in the last place of the result: 2^e with e = max(k,-1022) - 52.
-     * Q = floor(V / 2^e) < 2^53 and R is the remainder of that division.    */
-    int64_t e = (k > -1022 ? k : -1022) - 52;
+    /* Unit in the last place of the result: 2^e with e = max(k,emin) - (p-1).
+     * Q = floor(V / 2^e) < 2^p and R is the remainder of that division.     */
+    const int pm1 = f->p - 1;
+    int64_t e = (k > f->emin ? k : f->emin) - pm1;
     if (big_copy(&num, &N) || big_copy(&den, &D)) goto oom;
     if (e >= 0) {
         if (big_shl(&den, (uint64_t)e)) goto oom;
     } else {
         if (big_shl(&num, (uint64_t)(-e))) goto oom;
     }
-    /* Binary long division, 53 quotient bits (Q < 2^53). */
+    /* Binary long division, p quotient bits (Q < 2^p). */
     uint64_t Q = 0;
-    if (big_copy(&tmp, &den) || big_shl(&tmp, 52)) goto oom;
-    for (int i = 52; i >= 0; i--) {
+    if (big_copy(&tmp, &den) || big_shl(&tmp, (uint64_t)pm1)) goto oom;
+    for (int i = pm1; i >= 0; i--) {
         if (big_cmp(&num, &tmp) >= 0) {
             big_sub(&num, &tmp);
             Q |= (uint64_t)1 << i;
@@ -328,23 +346,24 @@ static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t
     if (big_shl(&num, 1)) goto oom;
     int c = big_cmp(&num, &den);
     if (c > 0 || (c == 0 && (Q & 1))) Q += 1;
-    if (Q == ((uint64_t)1 << 53)) {
+    if (Q == ((uint64_t)1 << f->p)) {
         Q >>= 1;
         e += 1;
     }
-    if (e > 1023 - 52) {
+    if (e > f->emax - pm1) {
         *status = OR_OVERFLOW;
-        bits = OR_INF_BITS;
+        bits = f->inf_bits;
     } else if (Q == 0) {
         *status = OR_UNDERFLOW;
         bits = 0;
-    } else if (Q < ((uint64_t)1 << 52)) {
-        /* subnormal: exponent field 0, e == -1074 */
+    } else if (Q < ((uint64_t)1 << pm1)) {
+        /* subnormal: exponent field 0, e == emin - (p-1) */
         *status = OR_OK;
         bits = Q;
     } else {
+        /* biased exponent field = e + (p-1) + emax */
         *status = OR_OK;
-        bits = ((uint64_t)(e + 1075) << 52) | (Q - ((uint64_t)1 << 52));
+        bits = ((uint64_t)(e + pm1 + f->emax) << pm1) | (Q - ((uint64_t)1 << pm1));
     }
     big_free(&N);
     big_free(&D);
@@ -360,14 +379,15 @@ oom:
     big_free(&tmp);
     *err = 1;
     *status = OR_INVALID;
-    return OR_QNAN_BITS;
+    return f->qnan_bits;
 }
 
-/* One field.  Returns 0, or -1 if memory ran out. */
-int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *status) {
+/* One field in format f.  Returns 0, or -1 if memory ran out. */
+static int parse_field_fmt(const char *s, size_t n, const fmt *f, uint64_t *out_bits,
+                           uint8_t *status) {
     token t;
     if (tokenize(s, n, &t) != 0) {
-        *out_bits = OR_QNAN_BITS;
+        *out_bits = f->qnan_bits;
         *status = OR_INVALID;
         return 0;
     }
@@ -375,7 +395,7 @@ int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *sta
     /* strip leading zeros */
     size_t first = 0;
     while (first < total && digit_at(&t, first) == 0) first++;
-    uint64_t sign = t.negative ? 0x8000000000000000ULL : 0;
+    uint64_t sign = t.negative ? f->sign_bit : 0;
     if (first == total) { /* the value is zero */
         *out_bits = sign;
         *status = OR_OK;
@@ -388,10 +408,23 @@ int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *sta
      * E = explicit exponent - fraction digits + stripped trailing zeros.   */
     int64_t E = t.exp10 - (int64_t)t.n_frac + (int64_t)(total - 1 - last);
     int err = 0;
-    uint64_t bits = convert_exact(&t, first, last, E, status, &err);
+    uint64_t bits = convert_exact(&t, first, last, E, f, status, &err);
     *out_bits = bits | sign;
-    if (bits == OR_QNAN_BITS) *out_bits = bits;
+    if (bits == f->qnan_bits) *out_bits = bits;
     return err ? -1 : 0;
+}
+
+/* One field -> binary64.  Returns 0, or -1 if memory ran out. */
+int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *status) {
+    return parse_field_fmt(s, n, &FMT64, out_bits, status);
+}
+
+/* One field -> binary32 (the pattern in the low 32 bits). */
+int oracle_parse_field_f32(const char *s, size_t n, uint32_t *out_bits, uint8_t *status) {
+    uint64_t b = 0;
+    int rc = parse_field_fmt(s, n, &FMT32, &b, status);
+    *out_bits = (uint32_t)b;
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -413,7 +446,8 @@ typedef struct {
     char delim;
     size_t lo, hi; /* this worker parses fields whose first byte is in [lo,hi) */
     uint64_t first_index;
-    uint64_t *out_bits;
+    uint64_t *out_bits;   /* binary64 results, or */
+    uint32_t *out_bits32; /* binary32 results */
     uint8_t *status;
     int err;
 } work;
@@ -436,7 +470,13 @@ static void *worker(void *arg) {
         if (!starts_field(w->text, w->len, w->delim, p)) continue;
         size_t q = p;
         while (q < w->len && !is_sep(w->text[q], w->delim)) q++;
-        if (oracle_parse_field(w->text + p, q - p, &w->out_bits[idx], &w->status[idx])) w->err = 1;
+        int rc;
+        if (w->out_bits32) {
+            rc = oracle_parse_field_f32(w->text + p, q - p, &w->out_bits32[idx], &w->status[idx]);
+        } else {
+            rc = oracle_parse_field(w->text + p, q - p, &w->out_bits[idx], &w->status[idx]);
+        }
+        if (rc) w->err = 1;
         idx++;
         p = q; /* the loop increment steps over the separator */
     }
@@ -448,8 +488,9 @@ static void *worker(void *arg) {
  * entries; the number of fields is written to *count.  Returns 0, -1 on a
  * capacity or memory error.  nthreads <= 1 runs on the calling thread.
  */
-int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
-                        uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
+static int parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
+                        uint32_t *out_bits32, uint8_t *status, uint64_t cap, uint64_t *count,
+                        int nthreads) {
     uint64_t total = oracle_count_fields(text, len, delim);
     *count = total;
     if (total > cap) return -1;
@@ -470,6 +511,7 @@ int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_
         ws[i].lo = (size_t)((unsigned __int128)len * (unsigned)i / (unsigned)nthreads);
         ws[i].hi = (size_t)((unsigned __int128)len * (unsigned)(i + 1) / (unsigned)nthreads);
         ws[i].out_bits = out_bits;
+        ws[i].out_bits32 = out_bits32;
         ws[i].status = status;
         ws[i].first_index = before;
         before += count_starts(text, len, delim, ws[i].lo, ws[i].hi);
@@ -485,4 +527,15 @@ int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_
     free(ws);
     free(th);
     return rc ? -1 : 0;
+}
+
+int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
+                        uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
+    return parse_buffer(text, len, delim, out_bits, NULL, status, cap, count, nthreads);
+}
+
+/* As oracle_parse_buffer, to binary32. */
+int oracle_parse_buffer_f32(const char *text, size_t len, char delim, uint32_t *out_bits,
+                            uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
+    return parse_buffer(text, len, delim, NULL, out_bits, status, cap, count, nthreads);
 }
