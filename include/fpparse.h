@@ -188,20 +188,24 @@ FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
  * One scheduler thread per server owns one device-memory arena of
  * `device_budget` bytes, cut into a text region (1 B per unit), a value
  * region (8 B per unit) and a status region (1 B per unit); a request of
- * `len` bytes holds len units, rounded up to 256, from admission to
+ * `len` bytes holds len + 16 units, rounded up to 256, from admission to
  * completion.  Requests are admitted first-come first-served as arena space
- * frees up (a request that does not fit waits, and so do those behind it);
- * each admitted request's text is copied to the device at once, so copies
- * overlap the launches in flight.  Whenever one of `max_inflight` launch
- * slots is free, every admitted request not yet launched (at most
- * `max_batch`) goes into one persistent batched launch on that slot's
- * stream; when it ends, the field counts come back, then exactly that many
- * values and statuses per request, straight into the caller's host arrays,
- * and the request's units are released.  Results equal those of
+ * frees up (a request that does not fit waits, and so do those behind it).
+ * Whenever one of `max_inflight` launch slots is free, every admitted
+ * request not yet launched (at most `max_batch`) goes into one launch
+ * sequence on that slot's stream: a gather kernel copies the texts from
+ * host memory into the arena, the persistent batched parse and its
+ * fallback run, and a scatter kernel writes each request's first
+ * min(fields, out_cap) values and statuses straight into the caller's
+ * host arrays; then the request's units are released.  The kernels reach
+ * host memory directly when it is pinned (page-locked); texts and arrays in
+ * pageable memory are moved by copy calls instead (slower).  Different
+ * slots' sequences overlap on the device.  Results equal those of
  * fp_parse_f64 on the same text, alone or in any mix.
  * Besides the arena, each slot's stream holds the parse scratch of up to
  * one budget's worth of chunks (24 B per 4 KiB of budget/10, plus the
- * fallback queue) and two small pinned arrays.
+ * fallback queue), and pinned piece tables for its copy kernels (about
+ * 0.2% of budget/10).
  *
  * fp_server_create -- start a server on the current device.  cfg fields:
  *   device_budget  bytes for the arena (>= 4 KiB; allocated here at once)

@@ -2,17 +2,20 @@
 // continuous batching of host-memory parse requests on one GPU.
 //
 // One scheduler thread per server runs a polling loop of four steps:
-//   retire  a slot whose counts have arrived gets its exact result copies
-//           queued; a slot whose copies are done completes its requests and
-//           releases their arena units;
+//   retire  a slot whose launch has ended completes its requests (after
+//           copying back the results of any request whose host arrays the
+//           device cannot reach) and releases their arena units;
 //   take    new submissions move to the pending queue (FIFO);
 //   admit   pending requests get arena units in arrival order while they
-//           fit, and their text copies are queued on the copy stream;
+//           fit;
 //   launch  each free slot takes every admitted request not yet launched
-//           (at most max_batch) and queues one persistent batched parse on
-//           its own stream, after the copies, then the counts' copy back.
-// Copies in both directions and the launches of different slots overlap on
-// the device; the loop only orders them with events.
+//           (at most max_batch) and queues on its own stream: one gather
+//           kernel (texts, pinned host -> arena), the persistent batched
+//           parse and its fallback, one scatter kernel (each request's
+//           first min(count, cap) results, arena -> the caller's pinned
+//           arrays) and the copy of the counts.
+// The slots' streams overlap on the device: one batch's texts come in
+// while another is parsed and a third one's results go out.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -28,6 +31,7 @@
 
 #include "../../include/fpparse.h"
 #include "fp_arena.h"
+#include "fp_copy.h"
 #include "fp_internal.h"
 
 namespace {
@@ -51,10 +55,30 @@ struct Request {
   double* h_f64 = nullptr;
   uint8_t* h_status = nullptr;
   size_t out_cap = 0;           // entries of h_f64 / h_status
+  // device views of the host arrays (null: the device cannot reach them,
+  // so the copy calls move them)
+  const uint8_t* dv_text = nullptr;
+  unsigned long long* dv_f64 = nullptr;
+  uint8_t* dv_status = nullptr;
   uint64_t off = 0, units = 0;  // arena range while admitted
+  uint64_t text_off = 0;        // where the text starts: off + (h_text mod 16)
   fp_request_info_t info{};
   bool done = false;
 };
+
+// The address the device uses for host memory p, or null when p is not
+// pinned (page-locked) memory.
+template <class T>
+T* device_view(T* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return static_cast<T*>(a.devicePointer);
+}
 
 enum class Phase { FREE, PARSING, COPYING };
 
@@ -65,6 +89,15 @@ struct Slot {
   uint64_t* h_counts = nullptr;  // pinned copy
   unsigned int* d_err = nullptr; // the parse scratch's error word of this stream
   unsigned int* h_err = nullptr; // pinned copy
+  // piece tables in pinned host memory, read by the copy kernels
+  fp::CopyPiece* gpieces = nullptr;   // written here ...
+  fp::ScatterItem* sitems = nullptr;
+  fp::ScatterPiece* spieces = nullptr;
+  const fp::CopyPiece* gpieces_dv = nullptr;  // ... read there (device views)
+  const fp::ScatterItem* sitems_dv = nullptr;
+  const fp::ScatterPiece* spieces_dv = nullptr;
+  uint32_t cap_gpieces = 0, cap_spieces = 0;
+  bool unmapped_out = false;     // some request's results go back by copy calls
   Phase phase = Phase::FREE;
   std::vector<Request*> reqs;
   std::vector<const char*> texts;
@@ -83,8 +116,7 @@ struct fp_server {
   double* d_f64 = nullptr;
   uint8_t* d_status = nullptr;
   fp::Arena arena{0};
-  cudaStream_t h2d = nullptr;
-  cudaEvent_t ev_h2d = nullptr;
+  int sms = 1;
   std::vector<Slot> slots;
   std::thread thread;
 
@@ -150,6 +182,7 @@ bool retire(fp_server* S, Slot& sl) {
         r->info.error = FP_ERR_INTERNAL;
         continue;
       }
+      if (r->dv_f64) continue;  // already written by the scatter kernel
       const uint64_t n = std::min<uint64_t>(count, r->out_cap);
       if (n) {
         if (cudaMemcpyAsync(r->h_f64, S->d_f64 + r->off, n * sizeof(double),
@@ -158,6 +191,12 @@ bool retire(fp_server* S, Slot& sl) {
                             sl.stream) != cudaSuccess)
           r->info.error = FP_ERR_CUDA;
       }
+    }
+    if (!sl.unmapped_out) {
+      for (Request* r : sl.reqs) finish(S, r, (fp_err_t)r->info.error);
+      sl.reqs.clear();
+      sl.phase = Phase::FREE;
+      return true;
     }
     if (cudaEventRecord(sl.ev_done, sl.stream) != cudaSuccess) {
       fail_slot(S, sl, FP_ERR_CUDA);
@@ -190,19 +229,62 @@ void launch(fp_server* S, Slot& sl) {
   sl.lens.resize(k);
   sl.base.resize(k);
   sl.cap.resize(k);
-  for (size_t i = 0; i < k; i++) {
+  sl.unmapped_out = false;
+  fp_err_t e = FP_OK;
+  uint32_t ng = 0, ns = 0;
+  for (size_t i = 0; i < k && e == FP_OK; i++) {
     Request* r = sl.reqs[i];
-    sl.texts[i] = S->d_text + r->off;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(S->d_text) + r->text_off;
+    sl.texts[i] = reinterpret_cast<const char*>(dst);
     sl.lens[i] = r->len;
     sl.base[i] = r->off;
     sl.cap[i] = r->len;  // fp_max_fields(len)
+    // text in: by the gather kernel, else by a copy call
+    if (r->len && r->dv_text) {
+      for (uint64_t p = 0; p < r->len; p += fp::GATHER_PIECE) {
+        if (ng >= sl.cap_gpieces) {
+          e = FP_ERR_INTERNAL;
+          break;
+        }
+        const uint64_t nb = std::min<uint64_t>(fp::GATHER_PIECE, r->len - p);
+        sl.gpieces[ng++] = fp::CopyPiece{r->dv_text + p, dst + p, (uint32_t)nb, 0};
+      }
+    } else if (r->len && cudaMemcpyAsync(dst, r->h_text, r->len, cudaMemcpyHostToDevice,
+                                         sl.stream) != cudaSuccess) {
+      e = FP_ERR_CUDA;
+    }
+    // results out: by the scatter kernel, else by copy calls after the counts
+    const uint64_t cap = std::min<uint64_t>(r->out_cap, r->len);
+    if (r->dv_f64 && r->dv_status) {
+      sl.sitems[i] = fp::ScatterItem{reinterpret_cast<const unsigned long long*>(S->d_f64) + r->off,
+                                     S->d_status + r->off, r->dv_f64, r->dv_status,
+                                     reinterpret_cast<const unsigned long long*>(sl.d_counts) + i,
+                                     cap};
+      for (uint64_t f = 0; f < cap; f += fp::SCATTER_PIECE) {
+        if (ns >= sl.cap_spieces) {
+          e = FP_ERR_INTERNAL;
+          break;
+        }
+        sl.spieces[ns++] = fp::ScatterPiece{(uint32_t)i, 0, f};
+      }
+    } else {
+      r->dv_f64 = nullptr;
+      sl.unmapped_out = true;
+    }
   }
-  fp_err_t e = FP_OK;
-  if (cudaStreamWaitEvent(sl.stream, S->ev_h2d, 0) != cudaSuccess) e = FP_ERR_CUDA;
+  const int grid = S->sms * 4;
+  if (e == FP_OK &&
+      fp::launch_gather(sl.gpieces_dv, ng, (int)std::min<uint32_t>(ng ? ng : 1, grid), sl.stream) !=
+          cudaSuccess)
+    e = FP_ERR_CUDA;
   if (e == FP_OK)
     e = fp::parse_batch_ranges(sl.texts.data(), sl.lens.data(), (uint32_t)k, S->cfg.delim,
                                S->d_f64, S->d_status, sl.base.data(), sl.cap.data(), sl.d_counts,
                                sl.stream);
+  if (e == FP_OK &&
+      fp::launch_scatter(sl.sitems_dv, sl.spieces_dv, ns, (int)std::min<uint32_t>(ns ? ns : 1, grid),
+                         sl.stream) != cudaSuccess)
+    e = FP_ERR_CUDA;
   if (e == FP_OK &&
       (cudaMemcpyAsync(sl.h_counts, sl.d_counts, k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
                        sl.stream) != cudaSuccess ||
@@ -248,24 +330,14 @@ void scheduler(fp_server* S) {
       if (!S->arena.alloc(r->units, &off)) break;  // first come, first served
       S->pending.pop_front();
       r->off = off;
+      r->text_off = off + (reinterpret_cast<uintptr_t>(r->h_text) & 15);
       S->held_requests++;
       r->info.admit_ns = now_ns();
-      if (r->len && cudaMemcpyAsync(S->d_text + off, r->h_text, r->len, cudaMemcpyHostToDevice,
-                                    S->h2d) != cudaSuccess) {
-        finish(S, r, FP_ERR_CUDA);
-        continue;
-      }
       S->admitted.push_back(r);
       admitted_any = true;
     }
     if (admitted_any) {
       progressed = true;
-      if (cudaEventRecord(S->ev_h2d, S->h2d) != cudaSuccess) {
-        while (!S->admitted.empty()) {
-          finish(S, S->admitted.front(), FP_ERR_CUDA);
-          S->admitted.pop_front();
-        }
-      }
       std::lock_guard<std::mutex> lk(S->mu);
       S->st.peak_units = std::max<uint64_t>(S->st.peak_units, S->arena.used_units());
       S->st.peak_requests = std::max<uint64_t>(S->st.peak_requests, S->held_requests);
@@ -301,12 +373,10 @@ void free_server(fp_server* S) {
     cudaFree(sl.d_counts);
     cudaFreeHost(sl.h_counts);
     cudaFreeHost(sl.h_err);
+    cudaFreeHost(sl.gpieces);
+    cudaFreeHost(sl.sitems);
+    cudaFreeHost(sl.spieces);
   }
-  if (S->h2d) {
-    cudaStreamSynchronize(S->h2d);
-    cudaStreamDestroy(S->h2d);
-  }
-  if (S->ev_h2d) cudaEventDestroy(S->ev_h2d);
   cudaFree(S->dmem);
   for (auto& kv : S->live) delete kv.second;
   delete S;
@@ -345,8 +415,7 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
   S->d_f64 = reinterpret_cast<double*>(S->d_text + S->units);
   S->d_status = reinterpret_cast<uint8_t*>(S->d_text + 9 * S->units);
   S->arena = fp::Arena(S->units);
-  SRV_CUDA(cudaStreamCreateWithFlags(&S->h2d, cudaStreamNonBlocking));
-  SRV_CUDA(cudaEventCreateWithFlags(&S->ev_h2d, cudaEventDisableTiming));
+  SRV_CUDA(cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device));
   S->slots.resize(cfg->max_inflight);
   // the most chunks one launch can hold: every unit of text at the smallest
   // chunk size, plus one partial chunk per request at each end
@@ -359,6 +428,19 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
     SRV_CUDA(cudaMallocHost(&sl.h_counts, cfg->max_batch * sizeof(uint64_t)));
     SRV_CUDA(cudaMallocHost(&sl.h_err, sizeof(unsigned int)));
     *sl.h_err = 0;
+    // piece tables: every unit of a batch once, plus one partial piece per request
+    sl.cap_gpieces = (uint32_t)(S->units / fp::GATHER_PIECE + cfg->max_batch + 1);
+    sl.cap_spieces = (uint32_t)(S->units / fp::SCATTER_PIECE + cfg->max_batch + 1);
+    SRV_CUDA(cudaHostAlloc(&sl.gpieces, sl.cap_gpieces * sizeof(fp::CopyPiece), cudaHostAllocMapped));
+    SRV_CUDA(cudaHostAlloc(&sl.sitems, cfg->max_batch * sizeof(fp::ScatterItem), cudaHostAllocMapped));
+    SRV_CUDA(cudaHostAlloc(&sl.spieces, sl.cap_spieces * sizeof(fp::ScatterPiece), cudaHostAllocMapped));
+    sl.gpieces_dv = device_view(sl.gpieces);
+    sl.sitems_dv = device_view(sl.sitems);
+    sl.spieces_dv = device_view(sl.spieces);
+    if (!sl.gpieces_dv || !sl.sitems_dv || !sl.spieces_dv) {
+      free_server(S);
+      return FP_ERR_CUDA;
+    }
     if (fp::reserve_stream_scratch(sl.stream, chunks, cfg->max_batch) != FP_OK ||
         fp::stream_error_word(sl.stream, &sl.d_err) != FP_OK) {
       free_server(S);
@@ -379,7 +461,9 @@ extern "C" fp_err_t fp_server_submit(fp_server* S, const char* host_text, size_t
   if (len >= MAX_LEN) return FP_ERR_ARG;
   if (len > 0 && !host_text) return FP_ERR_ARG;
   if (out_cap > 0 && (!host_f64 || !host_status)) return FP_ERR_ARG;
-  const uint64_t units = (std::max<uint64_t>(len, 1) + UNIT_ROUND - 1) / UNIT_ROUND * UNIT_ROUND;
+  // len text bytes placed at the source's address mod 16 (+15), and len
+  // value / status slots (fp_max_fields)
+  const uint64_t units = (len + 16 + UNIT_ROUND - 1) / UNIT_ROUND * UNIT_ROUND;
   if (units > S->units) return FP_ERR_BUDGET;
   Request* r = new Request();
   r->h_text = host_text;
@@ -388,6 +472,11 @@ extern "C" fp_err_t fp_server_submit(fp_server* S, const char* host_text, size_t
   r->h_status = host_status;
   r->out_cap = out_cap;
   r->units = units;
+  r->dv_text = device_view(reinterpret_cast<const uint8_t*>(host_text));
+  if (out_cap) {
+    r->dv_f64 = device_view(reinterpret_cast<unsigned long long*>(host_f64));
+    r->dv_status = device_view(host_status);
+  }
   r->info.submit_ns = now_ns();
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -178,3 +178,28 @@ def test_output_capacity_bounds_the_copy():
     assert info["error"] == 0 and info["count"] == rb.size > 10
     assert np.array_equal(v[:7].numpy().view(np.uint64), rb[:7])
     assert (v[7:] == -5.0).all() and np.array_equal(s[:7].numpy(), rs[:7])
+
+
+def test_pageable_host_memory_takes_the_copy_path(texts, ref):
+    """Texts and result arrays that are not pinned are moved by copy calls
+    instead of the gather / scatter kernels; results are the same."""
+    with fp.Server(device_budget=1 << 30, max_batch=32, max_inflight=2, delim=b",") as srv:
+        reqs = []
+        for i, t in enumerate(texts[:60]):
+            n = max(len(t), 1)
+            ht = torch.frombuffer(bytearray(t), dtype=torch.uint8) if t else \
+                torch.empty(0, dtype=torch.uint8)
+            hv = torch.full((n,), -5.0, dtype=torch.float64)
+            hs = torch.full((n,), 0xEE, dtype=torch.uint8)
+            if i % 3 == 1:
+                ht = ht.pin_memory()          # pinned text, pageable results
+            elif i % 3 == 2:
+                hv, hs = hv.pin_memory(), hs.pin_memory()  # pageable text, pinned results
+            reqs.append((srv.submit(ht, hv, hs), hv, hs))
+        got = []
+        for rid, hv, hs in reqs:
+            info = srv.wait(rid, timeout_s=120)
+            assert info["error"] == 0
+            k = info["count"]
+            got.append((hv[:k].numpy().view(np.uint64).copy(), hs[:k].numpy().copy(), info))
+    assert_same(ref[:60], got)
