@@ -129,6 +129,22 @@ FP_API fp_err_t fp_parse_f64(const char *text, size_t len, char delim, double *o
                       uint8_t *out_status, uint64_t *out_count, struct CUstream_st *stream);
 
 /*
+ * fp_parse_f32 -- fp_parse_f64 with binary32 results: the nearest float,
+ *   ties to even (Section 2's 32-bit format; Algorithm 1's 32-bit case,
+ *   Section 5: 26 provably exact bits after one product, ties only for
+ *   q in [-17, 10]; the same 19-digit check and exact fallback, Section 11).
+ *   out_f32     device array, fp_max_fields(len) floats; field i -> out_f32[i]
+ *   Other arguments, statuses and asynchrony as fp_parse_f64; INVALID
+ *   fields get the quiet NaN 0x7FC00000.  The first call on a stream needing
+ *   more room than any before it also allocates 8 bytes per possible field
+ *   of scratch (where unsettled fields keep their text location until the
+ *   fallback kernel decides them).
+ */
+FP_API fp_err_t fp_parse_f32(const char *text, size_t len, char delim, float *out_f32,
+                             uint8_t *out_status, uint64_t *out_count,
+                             struct CUstream_st *stream);
+
+/*
  * fp_parse_f64_batch -- parse many independent buffers in one persistent
  * launch (work is split by chunk across all buffers, not by buffer).
  *   texts        HOST array of nbuf device pointers (NULL allowed iff lens[b] == 0)

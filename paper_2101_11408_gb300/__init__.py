@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (STATUS_INVALID, STATUS_OK, STATUS_OVERFLOW, STATUS_UNDERFLOW, Config,
                    FpError, Stats)
 
-__all__ = ["BatchPlan", "Server", "parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
+__all__ = ["BatchPlan", "Server", "parse_f32", "parse_f32_into", "parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
            "parse_f64_batch_into", "max_fields", "stats", "get_error", "set_config",
            "get_config", "autotune", "timing_enable", "timing_read", "shutdown", "library_path", "FpError", "STATUS_OK",
            "STATUS_INVALID", "STATUS_OVERFLOW", "STATUS_UNDERFLOW"]
@@ -87,6 +87,39 @@ def parse_f64(text: torch.Tensor, delim=b"\n", stream=None):
     if n is None:
         stream.synchronize()
         n = int(cnt.item())
+    return out[:n], st[:n]
+
+
+def parse_f32_into(text: torch.Tensor, out_f32: torch.Tensor, out_status: torch.Tensor,
+                   out_count: torch.Tensor, delim=b"\n", stream=None) -> None:
+    """As parse_f64_into, to binary32 (out_f32 float32)."""
+    _check_text(text)
+    n = text.numel()
+    if out_f32.dtype != torch.float32 or out_status.dtype != torch.uint8:
+        raise TypeError("out_f32 must be float32 and out_status uint8")
+    if n and (out_f32.numel() < n or out_status.numel() < n):
+        raise ValueError("output arrays need max_fields(len) entries")
+    lib = _lib.load()
+    rc = lib.fp_parse_f32(text.data_ptr() if n else None, n, _delim_byte(delim),
+                          out_f32.data_ptr() if n else None,
+                          out_status.data_ptr() if n else None, out_count.data_ptr(),
+                          _stream_handle(stream))
+    _lib.check(rc, "fp_parse_f32")
+
+
+def parse_f32(text: torch.Tensor, delim=b"\n", stream=None):
+    """Parse every field of a device buffer to binary32.  Returns (values
+    float32, status uint8) device tensors of the field count (synchronises)."""
+    _check_text(text)
+    dev = text.device
+    cap = max(text.numel(), 1)
+    out = torch.empty(cap, dtype=torch.float32, device=dev)
+    st = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    parse_f32_into(text, out, st, cnt, delim, stream)
+    if stream is not None:
+        stream.synchronize()
+    n = int(cnt.item())
     return out[:n], st[:n]
 
 

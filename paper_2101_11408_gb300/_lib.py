@@ -16,7 +16,7 @@ FP_OK, FP_ERR_ARG, FP_ERR_CAPACITY, FP_ERR_CUDA, FP_ERR_BUDGET, FP_ERR_TIMEOUT, 
 STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
 
 # every symbol include/fpparse.h declares
-EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f64_batch", "fp_get_stats",
+EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
            "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
            "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_server_create", "fp_server_submit",
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = True):
         lib.fp_max_fields.restype = sz
         lib.fp_parse_f64.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
         lib.fp_parse_f64.restype = ctypes.c_int
+        lib.fp_parse_f32.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
+        lib.fp_parse_f32.restype = ctypes.c_int
         lib.fp_parse_f64_batch.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_char, vp, u8p,
                                            vp, vp, vp]
         lib.fp_parse_f64_batch.restype = ctypes.c_int

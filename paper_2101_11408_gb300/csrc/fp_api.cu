@@ -57,8 +57,9 @@ Config g_cfg = initial_config();
 
 struct DeviceInfo {
   int sms = 0;
-  std::map<int, int> parse_occ;  // chunk bytes -> resident blocks per SM
-  int fb_occ = 0;
+  std::map<int, int> parse_occ;    // chunk bytes -> resident blocks per SM (binary64)
+  std::map<int, int> parse_occ32;  // the same for the binary32 kernels
+  int fb_occ = 0, fb_occ32 = 0;
   char name[256] = {0};
 };
 std::map<int, DeviceInfo> g_dev;
@@ -93,6 +94,9 @@ struct Scratch {
   uint8_t* stage_status = nullptr;
   unsigned long long* stage_count = nullptr;
   size_t stage_cap = 0;
+  // binary32 calls: pending fields' locations, indexed like the outputs
+  unsigned long long* loc = nullptr;
+  unsigned long long cap_loc = 0;
 };
 bool g_timing = false;
 
@@ -134,11 +138,15 @@ fp_err_t device_info(int dev, DeviceInfo** out) {
     snprintf(di.name, sizeof(di.name), "%s", prop.name);
     for (int c : {4096, 8192, 12288, 16384}) {
       int occ = 0;
-      FP_CUDA(fp::parse_occupancy(c, &occ));
+      FP_CUDA(fp::parse_occupancy(c, &occ, false));
       di.parse_occ[c] = std::max(occ, 1);
+      FP_CUDA(fp::parse_occupancy(c, &occ, true));
+      di.parse_occ32[c] = std::max(occ, 1);
     }
-    FP_CUDA(fp::fallback_occupancy(&di.fb_occ));
+    FP_CUDA(fp::fallback_occupancy(&di.fb_occ, false));
     di.fb_occ = std::max(di.fb_occ, 1);
+    FP_CUDA(fp::fallback_occupancy(&di.fb_occ32, true));
+    di.fb_occ32 = std::max(di.fb_occ32, 1);
     it = g_dev.emplace(dev, di).first;
   }
   *out = &it->second;
@@ -163,6 +171,7 @@ void free_scratch(Scratch* s) {
   cudaFree(s->stage_out);
   cudaFree(s->stage_status);
   cudaFree(s->stage_count);
+  cudaFree(s->loc);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
 }
@@ -246,9 +255,10 @@ void fill_desc(BufDesc& d, const char* text, size_t len, unsigned long long chun
   d.out_count = reinterpret_cast<unsigned long long*>(out_count);
 }
 
-// Queue the two kernels of one call.
+// Queue the two kernels of one call (binary32 results when f32).
 fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& p,
-             unsigned long long total_chunks, unsigned long long total_bytes, cudaStream_t stream) {
+             unsigned long long total_chunks, unsigned long long total_bytes, cudaStream_t stream,
+             bool f32 = false) {
   if (s->epoch >= fp::LB_EPOCH_MAX) {
     FP_CUDA(cudaMemsetAsync(s->chunk_status, 0, s->cap_chunks * sizeof(unsigned long long), stream));
     s->epoch = 1;
@@ -261,7 +271,8 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   p.ovf = s->ovf;
   p.ovf_cap = s->ovf_cap;
   p.total_chunks = total_chunks;
-  const int occ = di.parse_occ.at((int)cfg.chunk_bytes);
+  if (!p.loc) p.loc = p.out_bits;  // binary64: the location sits in the output slot
+  const int occ = (f32 ? di.parse_occ32 : di.parse_occ).at((int)cfg.chunk_bytes);
   const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
   unsigned long long grid = (unsigned long long)di.sms * per_sm;
   if (grid > total_chunks) grid = total_chunks;
@@ -276,9 +287,9 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
       for (cudaEvent_t& ev : s->ev[slot]) FP_CUDA(cudaEventCreate(&ev));
     FP_CUDA(cudaEventRecord(s->ev[slot][0], stream));
   }
-  FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream));
+  FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
   if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
-  FP_CUDA(fp::launch_fallback(p, di.sms * di.fb_occ, stream));
+  FP_CUDA(fp::launch_fallback(p, di.sms * (f32 ? di.fb_occ32 : di.fb_occ), stream, f32));
   if (timing) {
     FP_CUDA(cudaEventRecord(s->ev[slot][2], stream));
     s->ev_used[slot] = true;
@@ -432,6 +443,44 @@ fp_err_t fp_parse_f64(const char* text, size_t len, char delim, double* out_f64,
   p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
   p.out_status = out_status;
   return run(s, cfg, *di, p, nch, len, stream);
+}
+
+fp_err_t fp_parse_f32(const char* text, size_t len, char delim, float* out_f32,
+                      uint8_t* out_status, uint64_t* out_count, struct CUstream_st* stream_) {
+  if (len >= MAX_LEN) return FP_ERR_ARG;
+  if (!out_count) return FP_ERR_ARG;
+  if (len > 0 && (!text || !out_f32 || !out_status)) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Config cfg = g_cfg;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
+  const unsigned long long nch = chunks_of(t & 15, len, cfg.chunk_bytes);
+  Scratch* s = nullptr;
+  e = get_scratch(stream, nch, 1, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  if (len > s->cap_loc) {  // one location slot per possible field
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->loc);
+    s->loc = nullptr;
+    s->cap_loc = 0;
+    FP_CUDA(cudaMalloc(&s->loc, len * sizeof(unsigned long long)));
+    s->cap_loc = len;
+  }
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  fill_desc(p.one, text, len, 0, nch, 0, len, out_count);
+  p.descs = nullptr;
+  p.nbuf = 1;
+  p.delim = (unsigned char)delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f32);
+  p.out_status = out_status;
+  p.loc = s->loc;
+  return run(s, cfg, *di, p, nch, len, stream, true);
 }
 
 fp_err_t fp_parse_f64_batch(const char* const* texts, const size_t* lens, uint32_t nbuf,
@@ -863,6 +912,7 @@ extern "C" fp_err_t fp_batch_plan_create(const char* const* texts, const size_t*
   p.qcap = qcap;
   p.ovf = reinterpret_cast<unsigned long long*>(base + off_ovf);
   p.ovf_cap = c;
+  p.loc = p.out_bits;
   pl->total_chunks = c;
   pl->total_bytes = bytes;
   pl->scratch_bytes = off_ovf;

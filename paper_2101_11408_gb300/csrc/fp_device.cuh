@@ -35,7 +35,27 @@ enum : uint8_t {
 constexpr uint64_t QNAN_BITS = 0x7FF8000000000000ull;
 constexpr uint64_t INF_BITS = 0x7FF0000000000000ull;
 constexpr uint64_t SIGN_BIT = 0x8000000000000000ull;
-constexpr uint64_t EL_ABORT = ~0ull;  // never a positive binary64 pattern
+constexpr uint64_t EL_ABORT = ~0ull;  // never a positive binary64 or binary32 pattern
+
+// The two output formats (Section 2) as Algorithm 1 sees them: MBITS
+// stored significand bits, the bias, SHIFT = 64 - (MBITS + 3) so that
+// hi >> (u + SHIFT) keeps MBITS + 2 bits (one for rounding), the ties range
+// of q (Sections 6, 8.1, 9.1), the decimal-magnitude range exits of the
+// exact fallback, and the patterns of infinity, quiet NaN and the sign.
+struct F64 {
+  using word = unsigned long long;
+  static constexpr int MBITS = 52, BIAS = 1023, EMAX_FIELD = 2047, SHIFT = 9;
+  static constexpr int TIE_QMIN = -4, TIE_QMAX = 23;
+  static constexpr int DEC_OVF = 309, DEC_UNF = -324;  // 1e309 > 2^1024, 1e-324 < 2^-1075
+  static constexpr uint64_t INF = INF_BITS, QNAN = QNAN_BITS, SIGN = SIGN_BIT;
+};
+struct F32 {
+  using word = unsigned int;
+  static constexpr int MBITS = 23, BIAS = 127, EMAX_FIELD = 255, SHIFT = 38;
+  static constexpr int TIE_QMIN = -17, TIE_QMAX = 10;
+  static constexpr int DEC_OVF = 39, DEC_UNF = -46;  // 1e39 > 2^128, 1e-46 < 2^-150
+  static constexpr uint64_t INF = 0x7F800000ull, QNAN = 0x7FC00000ull, SIGN = 0x80000000ull;
+};
 
 // Fields longer than this many bytes are handed to the fallback kernel.
 constexpr int LMAX = 64;
@@ -101,7 +121,7 @@ FP_HD uint64_t load_lo(const uint64_t* p) {
 }
 
 struct ElResult {
-  uint64_t bits;  // positive binary64 pattern, or EL_ABORT
+  uint64_t bits;  // positive pattern of the format, or EL_ABORT
   int two_mul;    // 1 if the second 64x64 product was needed
 };
 
@@ -110,6 +130,7 @@ struct ElResult {
 // product even where Algorithm 1 would give up; that value is then within
 // one unit in the last place of the correct result (the fallback kernel
 // uses it as its first candidate).
+template <class F = F64>
 FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort) {
   ElResult r;
   r.two_mul = 0;
@@ -120,9 +141,11 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   // z = (T[q] * w) / 2^64, truncated: first the product with the high word.
   uint64_t lo = w * thi;
   uint64_t hi = mulhi64(w, thi);
-  // Unless the low 9 bits of the high word are all ones, the top 55 bits
-  // are exact and one product suffices (Sections 8 and 9).
-  if ((hi & 0x1FF) == 0x1FF) {
+  // Unless the low SHIFT bits of the high word are all ones, the top
+  // MBITS + 3 bits (55 for binary64, 26 for binary32) are exact and one
+  // product suffices (Algorithm 1; Sections 8 and 9).
+  constexpr uint64_t LOWMASK = (1ull << F::SHIFT) - 1;
+  if ((hi & LOWMASK) == LOWMASK) {
     const uint64_t tlo = load_lo(tab.lo + 2 * (q - FP_POW5_QMIN));
     uint64_t h2 = mulhi64(w, tlo);
     lo += h2;
@@ -135,18 +158,18 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
     r.bits = EL_ABORT;
     return r;
   }
-  // 54 significant bits (53 plus one rounding bit) below a possible
-  // leading zero bit u of the 128-bit product.
+  // MBITS + 2 significant bits (the significand plus one rounding bit)
+  // below a possible leading zero bit u of the 128-bit product.
   const int u = (int)(hi >> 63);
-  uint64_t m = hi >> (u + 9);
+  uint64_t m = hi >> (u + F::SHIFT);
   // Biased binary exponent: floor(log2 10^q) = (217706 q) >> 16 for
-  // q in (-400, 350) (Section 10), plus 63 - l + u, plus the bias 1023.
-  int E = ((217706 * q) >> 16) + 63 - l + u + 1023;
+  // q in (-400, 350) (Section 10), plus 63 - l + u, plus the bias.
+  int E = ((217706 * q) >> 16) + 63 - l + u + F::BIAS;
   if (E <= 0) {
-    // Subnormal (Section 9.3): the 54-bit m sits 2-E places above the
-    // 2^-1074 grid; shift by 1-E, then round on the last bit.  No ties are
-    // possible here (Section 6).  Rounding up to 2^52 yields the smallest
-    // normal number, whose bit pattern is that same integer.
+    // Subnormal (Section 9.3): m sits 2-E places above the grid of the
+    // smallest subnormal; shift by 1-E, then round on the last bit.  No ties
+    // are possible here (Section 6).  Rounding up to 2^MBITS yields the
+    // smallest normal number, whose bit pattern is that same integer.
     if (E <= -63) {
       r.bits = 0;
       return r;
@@ -157,39 +180,44 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
     r.bits = m;
     return r;
   }
-  // Ties to even (Sections 8.1 and 9.1): only for q in [-4, 23], when the
+  // Ties to even (Sections 8.1 and 9.1): only for q in [TIE_QMIN,
+  // TIE_QMAX] ([-4, 23] for binary64, [-17, 10] for binary32), when the
   // product below m's lowest bit is zero (second word <= 1 and the bits of
   // the high word under m all zero) and m ends in binary 01: clear the
   // rounding bit so that the round step does not go up.
-  if (lo <= 1 && q >= -4 && q <= 23 && (m & 3) == 1 && (m << (u + 9)) == hi) m &= ~1ull;
+  if (lo <= 1 && q >= F::TIE_QMIN && q <= F::TIE_QMAX && (m & 3) == 1 &&
+      (m << (u + F::SHIFT)) == hi)
+    m &= ~1ull;
   m += (m & 1);
   m >>= 1;
-  if (m >= (1ull << 53)) {  // rounding carried into a new bit
-    m = 1ull << 52;
+  if (m >= (1ull << (F::MBITS + 1))) {  // rounding carried into a new bit
+    m = 1ull << F::MBITS;
     E += 1;
   }
-  if (E >= 2047) {
-    r.bits = INF_BITS;
+  if (E >= F::EMAX_FIELD) {
+    r.bits = F::INF;
     return r;
   }
-  r.bits = ((uint64_t)E << 52) | (m & ((1ull << 52) - 1));
+  r.bits = ((uint64_t)E << F::MBITS) | (m & ((1ull << F::MBITS) - 1));
   return r;
 }
 
 // Quick exits of Algorithm 1 plus the product, for w != 0.  The product is
 // formed with q clamped to the table's range and the exits applied after,
 // so that the code has no data-dependent branch around the table access.
+template <class F = F64>
 FP_HD ElResult convert_wq(uint64_t w, int64_t q, const Pow5& tab, bool allow_abort) {
   const int qc = q < FP_POW5_QMIN ? FP_POW5_QMIN : (q > FP_POW5_QMAX ? FP_POW5_QMAX : (int)q);
-  ElResult r = eisel_lemire(w, qc, tab, allow_abort);
+  ElResult r = eisel_lemire<F>(w, qc, tab, allow_abort);
   if (q < FP_POW5_QMIN) r.bits = 0;
-  if (q > FP_POW5_QMAX) r.bits = INF_BITS;
+  if (q > FP_POW5_QMAX) r.bits = F::INF;
   return r;
 }
 
+template <class F = F64>
 FP_HD uint8_t status_of(uint64_t pos_bits) {
   if (pos_bits == 0) return ST_UNDERFLOW;  // nonzero text, zero result
-  if (pos_bits == INF_BITS) return ST_OVERFLOW;
+  if (pos_bits == F::INF) return ST_OVERFLOW;
   return ST_OK;
 }
 
@@ -212,6 +240,7 @@ struct FieldResult {
 // and feed a sticky flag.  With a nonzero sticky flag the value lies in
 // (w 10^q, (w+1) 10^q), and if both ends round to the same double that is
 // the answer (Section 11); otherwise the field is left pending.
+template <class F = F64>
 FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   FieldResult r;
   r.two_mul = 0;
@@ -221,7 +250,7 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   while (i < n && is_ws(s[i])) i++;
   uint64_t sign = 0;
   if (i < n && (s[i] == '+' || s[i] == '-')) {
-    sign = (s[i] == '-') ? SIGN_BIT : 0;
+    sign = (s[i] == '-') ? F::SIGN : 0;
     i++;
   }
   uint64_t w = 0;
@@ -281,7 +310,7 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   while (i < n && is_ws(s[i])) i++;
   ok = ok && (i == n);
   if (!ok) {
-    r.bits = QNAN_BITS;
+    r.bits = F::QNAN;
     r.status = ST_INVALID;
     return r;
   }
@@ -291,11 +320,11 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
     return r;
   }
   const int64_t q = ex + exp_adj;
-  ElResult a = convert_wq(w, q, tab, true);
+  ElResult a = convert_wq<F>(w, q, tab, true);
   r.two_mul = (uint8_t)a.two_mul;
   if (sticky) {
     r.is_long = 1;
-    ElResult b = convert_wq(w + 1, q, tab, true);
+    ElResult b = convert_wq<F>(w + 1, q, tab, true);
     r.two_mul |= (uint8_t)b.two_mul;
     if (a.bits == EL_ABORT || b.bits != a.bits) {
       r.status = ST_PENDING;
@@ -309,7 +338,7 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
     return r;
   }
   r.bits = a.bits | sign;
-  r.status = status_of(a.bits);
+  r.status = status_of<F>(a.bits);
   return r;
 }
 

@@ -120,15 +120,16 @@ __device__ __forceinline__ int cmp_scaled(const Big& X, long long sx, const Big&
   return -cmp_shifted(Y, -d, X);
 }
 
-// M, e with value = M 2^e for a finite non-negative bit pattern.
-__device__ __forceinline__ void double_parts(uint64_t x, uint64_t& M, int& e) {
-  const uint64_t ef = x >> 52, fr = x & ((1ull << 52) - 1);
+// M, e with value = M 2^e for a finite non-negative bit pattern of F.
+template <class F>
+__device__ __forceinline__ void float_parts(uint64_t x, uint64_t& M, int& e) {
+  const uint64_t ef = x >> F::MBITS, fr = x & ((1ull << F::MBITS) - 1);
   if (ef == 0) {
     M = fr;
-    e = -1074;
+    e = 1 - F::BIAS - F::MBITS;  // the smallest subnormal's exponent
   } else {
-    M = fr | (1ull << 52);
-    e = (int)ef - 1075;
+    M = fr | (1ull << F::MBITS);
+    e = (int)ef - F::BIAS - F::MBITS;
   }
 }
 
@@ -142,6 +143,7 @@ struct LongResult {
 __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c == '\n' || c == delim; }
 
 // Parse one field starting at f (at most lim bytes remain in the buffer).
+template <class F>
 __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim, uint32_t delim,
                                        const Pow5& tab, Big D, Big P, Big B) {
   LongResult r;
@@ -152,7 +154,7 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
   while (i < lim && is_ws(f[i])) i++;
   uint64_t sign = 0;
   if (i < lim && (f[i] == '+' || f[i] == '-')) {
-    sign = f[i] == '-' ? SIGN_BIT : 0;
+    sign = f[i] == '-' ? F::SIGN : 0;
     i++;
   }
   const unsigned long long int_start = i;
@@ -188,7 +190,7 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
   while (i < lim && is_ws(f[i])) i++;
   ok = ok && (i == lim || is_sep(f[i], delim));
   if (!ok) {
-    r.bits = QNAN_BITS;
+    r.bits = F::QNAN;
     r.status = ST_INVALID;
     return r;
   }
@@ -208,12 +210,12 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
   // value = (digits first..last) * 10^E
   const long long E = ex - (long long)n_frac + (long long)(ndig - 1 - last);
   // ---- quick exits: 10^(nsig-1+E) <= V < 10^(nsig+E) -------------------
-  if (nsig - 1 + E >= 309) {
-    r.bits = INF_BITS | sign;
+  if (nsig - 1 + E >= F::DEC_OVF) {
+    r.bits = F::INF | sign;
     r.status = ST_OVERFLOW;
     return r;
   }
-  if (nsig + E <= -324) {
+  if (nsig + E <= F::DEC_UNF) {
     r.bits = sign;
     r.status = ST_UNDERFLOW;
     return r;
@@ -224,17 +226,17 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
   for (int k = 0; k < n19; k++) w = w * 10 + digit(first + k);
   const long long q19 = E + (nsig - n19);
   const bool sticky19 = nsig > 19;
-  ElResult a = convert_wq(w, q19, tab, true);
+  ElResult a = convert_wq<F>(w, q19, tab, true);
   if (a.bits != EL_ABORT) {
     if (!sticky19) {
       r.bits = a.bits | sign;
-      r.status = status_of(a.bits);
+      r.status = status_of<F>(a.bits);
       return r;
     }
-    ElResult b = convert_wq(w + 1, q19, tab, true);
+    ElResult b = convert_wq<F>(w + 1, q19, tab, true);
     if (b.bits == a.bits) {
       r.bits = a.bits | sign;
-      r.status = status_of(a.bits);
+      r.status = status_of<F>(a.bits);
       return r;
     }
   }
@@ -266,13 +268,13 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
       if (!big_mul_pow5(P, -ED)) goto fail;
     }
     // ---- 3. candidate ------------------------------------------------------
-    uint64_t x = convert_wq(w, q19, tab, false).bits;
-    // ---- 4. step to the nearest double -----------------------------------
+    uint64_t x = convert_wq<F>(w, q19, tab, false).bits;
+    // ---- 4. step to the nearest value of the format --------------------
     auto cmp_mid = [&](uint64_t lowbits, int& c) -> bool {
       // c = sign of V - midpoint(lowbits, lowbits + 1)
       uint64_t M;
       int e;
-      double_parts(lowbits, M, e);
+      float_parts<F>(lowbits, M, e);
       const uint64_t T = 2 * M + 1;
       if (ED >= 0) {
         B.n = 0;
@@ -288,7 +290,7 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
     };
     for (int iter = 0; iter < 8; iter++) {
       int c;
-      if (x < INF_BITS) {
+      if (x < F::INF) {
         if (!cmp_mid(x, c)) goto fail;
         if (c > 0) {
           x += 1;
@@ -315,20 +317,21 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
     goto fail;  // did not converge: an internal error
   done:
     r.bits = x | sign;
-    r.status = status_of(x);
+    r.status = status_of<F>(x);
     return r;
   }
 fail:
   r.error = 1;
-  r.bits = QNAN_BITS;
+  r.bits = F::QNAN;
   r.status = ST_INVALID;
   return r;
 }
 
+template <class F>
 __device__ __forceinline__ void resolve(const LaunchParams& p, unsigned long long oi, Big D, Big P,
                                         Big B, unsigned long long& n_items,
                                         unsigned long long& n_big) {
-  const unsigned long long loc = p.out_bits[oi];
+  const unsigned long long loc = p.loc[oi];
   const unsigned int dix = (unsigned int)(loc >> LOC_OFF_BITS);
   const unsigned long long off = loc & LOC_OFF_MASK;
   if (dix >= p.nbuf) {  // cannot happen for entries written by the parse kernel
@@ -342,14 +345,15 @@ __device__ __forceinline__ void resolve(const LaunchParams& p, unsigned long lon
   }
   const uint8_t* f = d.base + d.o + off;
   const uint64_t* t = reinterpret_cast<const uint64_t*>(fp_pow5_table_dev);
-  LongResult r = parse_long_field(f, d.len - off, p.delim & 0xFFu, Pow5{t, 2, t + 1}, D, P, B);
+  LongResult r = parse_long_field<F>(f, d.len - off, p.delim & 0xFFu, Pow5{t, 2, t + 1}, D, P, B);
   if (r.error) atomicCAS(&p.ctl->error, 0u, DERR_INTERNAL);
-  p.out_bits[oi] = r.bits;
+  reinterpret_cast<typename F::word*>(p.out_bits)[oi] = (typename F::word)r.bits;
   p.out_status[oi] = r.status;
   n_items++;
   n_big += r.bignum;
 }
 
+template <class F>
 __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
   extern __shared__ __align__(16) uint32_t limbs[];
   const int tid = threadIdx.x;
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
   const unsigned long long gthreads = (unsigned long long)gridDim.x * FB_NT;
   for (unsigned long long i = gtid; i < nq; i += gthreads) {
     const unsigned long long oi = p.queue[i];
-    resolve(p, oi, D, P, B, n_items, n_big);
+    resolve<F>(p, oi, D, P, B, n_items, n_big);
   }
   // Chunks whose pending fields did not fit the queue: one warp per chunk
   // scans its outputs for unlisted pending fields.
@@ -375,7 +379,7 @@ __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
     const unsigned long long ob = p.ovf[2 * c + 1];
     for (unsigned long long k = lane; k < n; k += 32) {
       if (p.out_status[ob + k] == ST_PENDING_SCAN) {
-        resolve(p, ob + k, D, P, B, n_items, n_big);
+        resolve<F>(p, ob + k, D, P, B, n_items, n_big);
         n_scan++;
       }
     }
@@ -405,26 +409,36 @@ __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
 
 int fallback_smem_bytes() { return 3 * LIMBS * FB_NT * 4; }
 
-cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream) {
+template <class F>
+static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream) {
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(fallback_kernel,
+    cudaError_t e = cudaFuncSetAttribute(fallback_kernel<F>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          fallback_smem_bytes());
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  fallback_kernel<<<grid, FB_NT, fallback_smem_bytes(), stream>>>(p);
+  fallback_kernel<F><<<grid, FB_NT, fallback_smem_bytes(), stream>>>(p);
   return cudaGetLastError();
 }
 
-}  // namespace fp
+cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32) {
+  return f32 ? launch_fallback_f<F32>(p, grid, stream) : launch_fallback_f<F64>(p, grid, stream);
+}
 
-namespace fp {
-cudaError_t fallback_occupancy(int* blocks_per_sm) {
-  cudaFuncSetAttribute(fallback_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       fallback_smem_bytes());
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fallback_kernel, FB_NT,
+template <class F>
+static cudaError_t fallback_occupancy_f(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(fallback_kernel<F>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       fallback_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fallback_kernel<F>, FB_NT,
                                                        fallback_smem_bytes());
 }
+
+cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32) {
+  return f32 ? fallback_occupancy_f<F32>(blocks_per_sm) : fallback_occupancy_f<F64>(blocks_per_sm);
+}
+
 }  // namespace fp

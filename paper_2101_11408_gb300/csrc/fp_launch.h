@@ -6,12 +6,15 @@
 
 namespace fp {
 
-cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream);
+// f32: binary32 results (4-byte values; pending locations in p.loc),
+// else binary64 (8-byte values; p.loc == p.out_bits).
+cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream,
+                         bool f32 = false);
 int parse_smem_bytes(int chunk_bytes);
-cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm);
+cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm, bool f32 = false);
 
-cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream);
+cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32 = false);
 int fallback_smem_bytes();
-cudaError_t fallback_occupancy(int* blocks_per_sm);
+cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32 = false);
 
 }  // namespace fp

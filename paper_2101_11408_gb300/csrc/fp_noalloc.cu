@@ -123,6 +123,7 @@ extern "C" fp_err_t fp_parse_f64_noalloc(const char* text, size_t len, char deli
   p.qcap = NOALLOC_QUEUE;
   p.ovf = reinterpret_cast<unsigned long long*>(base + OFF_OVF);
   p.ovf_cap = NOALLOC_MAX_CHUNKS;
+  p.loc = p.out_bits;
   const int per_sm = cfg.ctas_per_sm ? ((int)cfg.ctas_per_sm < slot->parse_occ ? (int)cfg.ctas_per_sm
                                                                               : slot->parse_occ)
                                      : slot->parse_occ;

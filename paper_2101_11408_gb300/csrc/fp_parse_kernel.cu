@@ -175,7 +175,7 @@ __device__ __forceinline__ bool is_sep_byte(uint32_t c, uint32_t delim) {
   return c == '\n' || c == delim;
 }
 
-template <int C>
+template <int C, class F>
 __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const LaunchParams p) {
   using L = Layout<C>;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -404,11 +404,13 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       ft.w = 0;
       ft.q = 0;
       const bool ok = parse_fast(tile, s, e, ft);
-      const ElResult r = convert_wq(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
+      const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
       c_el += ok;
       c_two += ok & (uint32_t)r.two_mul;
-      bits = ft.w ? (r.bits | ft.sign) : ft.sign;
-      status = ft.w ? status_of(r.bits) : ST_OK;
+      uint64_t sgn = ft.sign;  // the binary64 sign bit
+      if constexpr (F::MBITS != F64::MBITS) sgn = ft.sign ? F::SIGN : 0;
+      bits = ft.w ? (r.bits | sgn) : sgn;
+      status = ft.w ? status_of<F>(r.bits) : ST_OK;
       if (!ok || (ft.w && r.bits == EL_ABORT)) status = ST_GENERAL;
     };
     // The rest: the general tokenizer on the field's exact extent, else the
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     auto parse_general = [&](int s, int e, unsigned long long& bits, uint8_t& status) {
       if (e - s <= LMAX) {
         c_slow++;
-        const FieldResult r = parse_short_field(tile + s, e - s, pow5);
+        const FieldResult r = parse_short_field<F>(tile + s, e - s, pow5);
         c_two += r.two_mul;
         c_long += r.is_long;
         c_long_ok += r.long_settled;
@@ -437,11 +439,16 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     const unsigned long long lb_known = same_buf ? prev_inc : 0ull;
 
     unsigned long long base = 0, cap = 0;
-    unsigned long long* ob = nullptr;
+    typename F::word* ob = nullptr;
     uint8_t* os = nullptr;
     auto store_one = [&](uint32_t k, unsigned long long bits, uint8_t status) {
       if (k >= cap) return;
-      ob[k] = bits;
+      if constexpr (sizeof(typename F::word) == 8) {
+        ob[k] = bits;  // a pending field's location stays in its own slot
+      } else {
+        if (status == ST_PENDING) p.loc[d.out_base + base + k] = bits;
+        else ob[k] = (typename F::word)bits;
+      }
       if (status == ST_PENDING) {
         const unsigned long long slot = atomicAdd(&ctl->qcount, 1ull);
         if (slot < p.qcap) {
@@ -515,7 +522,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       if (lo == 0) {
         base = ms->lb_part[0];
         cap = d.out_cap > base ? d.out_cap - base : 0;
-        ob = p.out_bits + d.out_base + base;
+        ob = reinterpret_cast<typename F::word*>(p.out_bits) + d.out_base + base;
         os = p.out_status + d.out_base + base;
       }
       for (uint32_t k = warp * share + lane; k < k_end; k += 32)
@@ -564,33 +571,37 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   }
 }
 
-template __global__ void parse_kernel<4096>(const LaunchParams);
-template __global__ void parse_kernel<8192>(const LaunchParams);
-template __global__ void parse_kernel<12288>(const LaunchParams);
-template __global__ void parse_kernel<16384>(const LaunchParams);
-
-template <int C>
+template <int C, class F>
 static cudaError_t launch_parse_c(const LaunchParams& p, int grid, cudaStream_t stream) {
   static bool attr_set = false;  // the attribute is per function; set it once
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(parse_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(parse_kernel<C, F>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Layout<C>::TOTAL);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  parse_kernel<C><<<grid, NT, Layout<C>::TOTAL, stream>>>(p);
+  parse_kernel<C, F><<<grid, NT, Layout<C>::TOTAL, stream>>>(p);
   return cudaGetLastError();
 }
 
-// Host-side launch helper (same translation unit as the kernels).
-cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream) {
+template <class F>
+static cudaError_t launch_parse_f(const LaunchParams& p, int chunk_bytes, int grid,
+                                  cudaStream_t stream) {
   switch (chunk_bytes) {
-    case 4096: return launch_parse_c<4096>(p, grid, stream);
-    case 8192: return launch_parse_c<8192>(p, grid, stream);
-    case 12288: return launch_parse_c<12288>(p, grid, stream);
-    case 16384: return launch_parse_c<16384>(p, grid, stream);
+    case 4096: return launch_parse_c<4096, F>(p, grid, stream);
+    case 8192: return launch_parse_c<8192, F>(p, grid, stream);
+    case 12288: return launch_parse_c<12288, F>(p, grid, stream);
+    case 16384: return launch_parse_c<16384, F>(p, grid, stream);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// Host-side launch helper (same translation unit as the kernels).
+cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream,
+                         bool f32) {
+  return f32 ? launch_parse_f<F32>(p, chunk_bytes, grid, stream)
+             : launch_parse_f<F64>(p, chunk_bytes, grid, stream);
 }
 
 int parse_smem_bytes(int chunk_bytes) {
@@ -603,23 +614,30 @@ int parse_smem_bytes(int chunk_bytes) {
   }
 }
 
-template <int C>
+template <int C, class F>
 static cudaError_t occupancy_c(int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(parse_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(parse_kernel<C, F>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        Layout<C>::TOTAL);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, parse_kernel<C>, NT,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, parse_kernel<C, F>, NT,
                                                        Layout<C>::TOTAL);
 }
 
-cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm) {
+template <class F>
+static cudaError_t occupancy_f(int chunk_bytes, int* blocks_per_sm) {
   switch (chunk_bytes) {
-    case 4096: return occupancy_c<4096>(blocks_per_sm);
-    case 8192: return occupancy_c<8192>(blocks_per_sm);
-    case 12288: return occupancy_c<12288>(blocks_per_sm);
-    case 16384: return occupancy_c<16384>(blocks_per_sm);
+    case 4096: return occupancy_c<4096, F>(blocks_per_sm);
+    case 8192: return occupancy_c<8192, F>(blocks_per_sm);
+    case 12288: return occupancy_c<12288, F>(blocks_per_sm);
+    case 16384: return occupancy_c<16384, F>(blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm, bool f32) {
+  return f32 ? occupancy_f<F32>(chunk_bytes, blocks_per_sm)
+             : occupancy_f<F64>(chunk_bytes, blocks_per_sm);
 }
 
 }  // namespace fp

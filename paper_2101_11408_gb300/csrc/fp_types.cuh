@@ -38,7 +38,7 @@ struct LaunchParams {
   unsigned int nbuf;
   unsigned int delim;
   unsigned long long total_chunks;
-  unsigned long long* out_bits;  // the caller's double array, as bit patterns
+  unsigned long long* out_bits;  // the caller's double (or float) array, as bit patterns
   uint8_t* out_status;
   Ctl* ctl;
   unsigned long long* chunk_status;  // look-back words, one per chunk
@@ -48,6 +48,10 @@ struct LaunchParams {
   unsigned long long qcap;
   unsigned long long* ovf;           // overflow chunk list: (loc, out_base | n) pairs
   unsigned long long ovf_cap;
+  // where a pending field's text location is kept until the fallback kernel
+  // decides it, indexed like the outputs: out_bits itself for binary64
+  // (the 8-byte slot holds it), a side array for binary32
+  unsigned long long* loc;
 };
 
 // Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).
