@@ -15,7 +15,10 @@ doubles) and by CPython's correctly rounded ``float()``
 (``tests/test_oracle_pins.py``); the binary32 functions by float32 round
 trips, constructed float32 midpoints, exact integers and powers of ten,
 range boundaries and a neighbour-comparison brute force
-(``tests/test_oracle_f32_pins.py``).
+(``tests/test_oracle_f32_pins.py``); the grammars and the columnar layout by
+``tests/test_oracle_grammar_pins.py`` (the JSON number grammar's accepted
+and rejected forms, CPython's correctly rounded ``float.fromhex`` on
+hexadecimal floats, Appendix C's printed pairs, hand-checked layouts).
 """
 from __future__ import annotations
 
@@ -31,7 +34,8 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
-STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = 0, 1, 2, 3
+STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW, STATUS_BAD_SHAPE = 0, 1, 2, 3, 4
+GRAMMAR_DEFAULT, GRAMMAR_HEX, GRAMMAR_JSON = 0, 1, 2
 
 _lock = threading.Lock()
 _lib = None
@@ -73,6 +77,15 @@ def _load():
             lib.oracle_parse_field_f32.restype = ctypes.c_int
             lib.oracle_parse_buffer_f32.argtypes = lib.oracle_parse_buffer.argtypes
             lib.oracle_parse_buffer_f32.restype = ctypes.c_int
+            lib.oracle_parse_field_ex.argtypes = [
+                ctypes.c_char_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint8)]
+            lib.oracle_parse_field_ex.restype = ctypes.c_int
+            lib.oracle_parse_buffer_ex.argtypes = [
+                ctypes.c_void_p, ctypes.c_size_t, ctypes.c_char, ctypes.c_int, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+            lib.oracle_parse_buffer_ex.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -101,13 +114,29 @@ def parse_field_f32(s) -> tuple[int, int]:
     return bits.value, st.value
 
 
+def parse_field_ex(s, f32: bool = False, grammar: int = GRAMMAR_DEFAULT) -> tuple[int, int]:
+    """One field in either format under a grammar (GRAMMAR_DEFAULT, the
+    decimal grammar; GRAMMAR_HEX, that or a hexadecimal float; GRAMMAR_JSON,
+    the JSON number grammar).  Returns (bit pattern, status)."""
+    if isinstance(s, str):
+        s = s.encode("utf-8")
+    lib = _load()
+    bits = ctypes.c_uint64()
+    st = ctypes.c_uint8()
+    if lib.oracle_parse_field_ex(s, len(s), int(f32), int(grammar), ctypes.byref(bits),
+                                 ctypes.byref(st)):
+        raise MemoryError("oracle ran out of memory")
+    return bits.value, st.value
+
+
 def count_fields(text: bytes, delim: bytes = b"\n") -> int:
     lib = _load()
     buf = np.frombuffer(text, dtype=np.uint8)
     return int(lib.oracle_count_fields(buf.ctypes.data, len(text), delim))
 
 
-def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None, f32: bool = False):
+def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None, f32: bool = False,
+                 grammar: int = GRAMMAR_DEFAULT):
     """Parse every field of a buffer.
 
     Returns (bits: uint64 array, status: uint8 array), or with f32=True
@@ -125,13 +154,42 @@ def parse_buffer(text, delim: bytes = b"\n", nthreads: int | None = None, f32: b
     bits = np.zeros(max(n, 1), dtype=np.uint32 if f32 else np.uint64)
     st = np.zeros(max(n, 1), dtype=np.uint8)
     cnt = ctypes.c_uint64()
-    fn = lib.oracle_parse_buffer_f32 if f32 else lib.oracle_parse_buffer
-    rc = fn(buf.ctypes.data, buf.size, delim, bits.ctypes.data, st.ctypes.data, bits.size,
-            ctypes.byref(cnt), int(nthreads))
+    rc = lib.oracle_parse_buffer_ex(buf.ctypes.data, buf.size, delim, int(f32), int(grammar),
+                                    bits.ctypes.data, st.ctypes.data, bits.size,
+                                    ctypes.byref(cnt), int(nthreads))
     if rc:
         raise MemoryError("oracle failed (capacity or memory)")
     assert cnt.value == n
     return bits[:n], st[:n]
+
+
+def columnar(text, bits, status, columns: int, rows_cap: int, delim: bytes = b","):
+    """Column-major layout of row-order results (the fused CSV form): field i
+    of the buffer goes to column i mod K, row i div K, i.e. entry
+    (i mod K) * rows_cap + i div K.  A field whose terminator disagrees with
+    its column -- the last column must end at '\n' or at the end of the
+    buffer, every other column at `delim` -- gets STATUS_BAD_SHAPE (its value
+    is kept).  Returns (values, statuses) of K * rows_cap entries; entries no
+    field reaches are left as zero / 0xEE."""
+    buf = np.frombuffer(bytes(text), dtype=np.uint8)
+    n = bits.size
+    k = np.arange(n)
+    seps = np.nonzero((buf == ord("\n")) | (buf == ord(delim)))[0]
+    term = np.full(n, ord("\n"), dtype=np.uint8)  # the buffer's end counts as '\n'
+    m = min(n, seps.size)
+    term[:m] = buf[seps[:m]]
+    last_col = (k % columns) == columns - 1
+    bad = (term == ord("\n")) != last_col
+    st = status.copy()
+    st[bad] = STATUS_BAD_SHAPE
+    if n and (n - 1) // columns >= rows_cap:
+        raise ValueError("rows_cap too small")
+    out = np.zeros(columns * rows_cap, dtype=bits.dtype)
+    ost = np.full(columns * rows_cap, 0xEE, dtype=np.uint8)
+    dest = (k % columns) * rows_cap + k // columns
+    out[dest] = bits
+    ost[dest] = st
+    return out, ost
 
 
 def bits_to_float(bits: int) -> float:

@@ -199,57 +199,114 @@ static uint64_t big_bitlen(const big *a) {
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int negative;
+    int hex; /* hexadecimal significand, binary exponent */
     /* the digit characters of the significand, possibly split by one '.' */
     const char *int_digits;
     size_t n_int;
     const char *frac_digits;
     size_t n_frac;
-    int64_t exp10; /* explicit exponent, saturated */
+    int64_t exp10; /* explicit exponent (of 10, or of 2 when hex), saturated */
 } token;
+
+/* Field grammars (the library's readings):
+ *   OR_GRAMMAR_DEFAULT  the decimal grammar in the header comment;
+ *   OR_GRAMMAR_HEX      that, or a hexadecimal float (Appendix C's form as
+ *                       printed by %a; the binary exponent is optional, as
+ *                       strtod reads it):
+ *                         [ \t\r]* [+-]? 0[xX] ( h+ ( '.' h* )? | '.' h+ )
+ *                         ( [pP] [+-]? d+ )? [ \t\r]*
+ *   OR_GRAMMAR_JSON     the JSON number grammar, with blanks around it:
+ *                         [ \t\r]* '-'? ( '0' | [1-9] d* ) ( '.' d+ )?
+ *                         ( [eE] [+-]? d+ )? [ \t\r]*                       */
+enum { OR_GRAMMAR_DEFAULT = 0, OR_GRAMMAR_HEX = 1, OR_GRAMMAR_JSON = 2 };
 
 static int is_ws(char c) { return c == ' ' || c == '\t' || c == '\r'; }
 static int is_digit(char c) { return c >= '0' && c <= '9'; }
 
 /* returns 0 on a whole-field match, -1 otherwise */
-static int tokenize(const char *s, size_t n, token *t) {
+static int hex_value(char c) {
+    if (c >= '0' && c <= '9') return c - '0';
+    if (c >= 'a' && c <= 'f') return c - 'a' + 10;
+    if (c >= 'A' && c <= 'F') return c - 'A' + 10;
+    return -1;
+}
+
+/* The exponent part after 'e'/'p' at s[*pi]: [+-]? d+, saturated. */
+static int read_exponent(const char *s, size_t n, size_t *pi, int64_t *out) {
+    size_t i = *pi;
+    int eneg = 0;
+    if (i < n && (s[i] == '+' || s[i] == '-')) {
+        eneg = (s[i] == '-');
+        i++;
+    }
+    size_t nd = 0;
+    int64_t e = 0;
+    while (i < n && is_digit(s[i])) {
+        if (e < OR_EXP_SAT) e = e * 10 + (s[i] - '0');
+        if (e > OR_EXP_SAT) e = OR_EXP_SAT;
+        i++;
+        nd++;
+    }
+    if (nd == 0) return -1; /* the exponent needs digits */
+    *out = eneg ? -e : e;
+    *pi = i;
+    return 0;
+}
+
+static int tokenize(const char *s, size_t n, int grammar, token *t) {
     size_t i = 0;
     memset(t, 0, sizeof(*t));
     while (i < n && is_ws(s[i])) i++;
-    if (i < n && (s[i] == '+' || s[i] == '-')) {
+    if (i < n && (s[i] == '-' || (s[i] == '+' && grammar != OR_GRAMMAR_JSON))) {
         t->negative = (s[i] == '-');
         i++;
     }
-    t->int_digits = s + i;
-    while (i < n && is_digit(s[i])) {
-        i++;
-        t->n_int++;
-    }
-    if (i < n && s[i] == '.') {
-        i++;
-        t->frac_digits = s + i;
+    if (grammar == OR_GRAMMAR_HEX && i + 1 < n && s[i] == '0' && (s[i + 1] | 0x20) == 'x') {
+        t->hex = 1;
+        i += 2;
+        t->int_digits = s + i;
+        while (i < n && hex_value(s[i]) >= 0) {
+            i++;
+            t->n_int++;
+        }
+        if (i < n && s[i] == '.') {
+            i++;
+            t->frac_digits = s + i;
+            while (i < n && hex_value(s[i]) >= 0) {
+                i++;
+                t->n_frac++;
+            }
+        }
+        if (t->n_int + t->n_frac == 0) return -1;
+        if (i < n && (s[i] | 0x20) == 'p') {
+            i++;
+            if (read_exponent(s, n, &i, &t->exp10)) return -1;
+        }
+    } else {
+        t->int_digits = s + i;
         while (i < n && is_digit(s[i])) {
             i++;
-            t->n_frac++;
+            t->n_int++;
         }
-    }
-    if (t->n_int + t->n_frac == 0) return -1; /* needs at least one digit */
-    if (i < n && (s[i] == 'e' || s[i] == 'E')) {
-        i++;
-        int eneg = 0;
-        if (i < n && (s[i] == '+' || s[i] == '-')) {
-            eneg = (s[i] == '-');
+        if (grammar == OR_GRAMMAR_JSON) {
+            /* an integer part is required, without leading zeros */
+            if (t->n_int == 0) return -1;
+            if (t->n_int > 1 && t->int_digits[0] == '0') return -1;
+        }
+        if (i < n && s[i] == '.') {
             i++;
+            t->frac_digits = s + i;
+            while (i < n && is_digit(s[i])) {
+                i++;
+                t->n_frac++;
+            }
+            if (grammar == OR_GRAMMAR_JSON && t->n_frac == 0) return -1;
         }
-        size_t nd = 0;
-        int64_t e = 0;
-        while (i < n && is_digit(s[i])) {
-            if (e < OR_EXP_SAT) e = e * 10 + (s[i] - '0');
-            if (e > OR_EXP_SAT) e = OR_EXP_SAT;
+        if (t->n_int + t->n_frac == 0) return -1; /* needs at least one digit */
+        if (i < n && (s[i] == 'e' || s[i] == 'E')) {
             i++;
-            nd++;
+            if (read_exponent(s, n, &i, &t->exp10)) return -1;
         }
-        if (nd == 0) return -1; /* 'e' must be followed by digits */
-        t->exp10 = eneg ? -e : e;
     }
     while (i < n && is_ws(s[i])) i++;
     return i == n ? 0 : -1;
@@ -257,8 +314,8 @@ static int tokenize(const char *s, size_t n, token *t) {
 
 /* digit k (0-based) of the concatenated significand digit string */
 static int digit_at(const token *t, size_t k) {
-    if (k < t->n_int) return t->int_digits[k] - '0';
-    return t->frac_digits[k - t->n_int] - '0';
+    const char c = k < t->n_int ? t->int_digits[k] : t->frac_digits[k - t->n_int];
+    return t->hex ? hex_value(c) : c - '0';
 }
 
 /* ------------------------------------------------------------------------ */
@@ -266,50 +323,14 @@ static int digit_at(const token *t, size_t k) {
 /* ------------------------------------------------------------------------ */
 
 /*
- * Nearest value of format f to D * 10^E for a natural D given by its
- * significant digits [first, last] of the token (first digit nonzero, last
- * digit nonzero).  Returns the unsigned bit pattern; writes the status.
+ * Nearest value of format f to V = N / D (N, D > 0): k = floor(log2 V)
+ * exactly, then Q = floor(V / 2^e) with e = max(k, emin) - (p-1) by binary
+ * long division, rounded half to even on the remainder.  Returns the
+ * unsigned bit pattern and writes the status; frees N and D.
  */
-static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t E,
-                              const fmt *f, uint8_t *status, int *err) {
-    size_t nd = last - first + 1;
-    /* Cheap range exits, each by a wide margin:
-     *   10^(nd-1+E) <= V < 10^(nd+E).
-     *   nd-1+E >= dec_ovf  =>  V >= 10^dec_ovf > 2^(emax+1): rounds to infinity.
-     *   nd+E <= dec_unf    =>  V < 10^dec_unf < 2^(emin-p): rounds to zero.  */
-    if ((int64_t)nd - 1 + E >= f->dec_ovf) {
-        *status = OR_OVERFLOW;
-        return f->inf_bits;
-    }
-    if ((int64_t)nd + E <= f->dec_unf) {
-        *status = OR_UNDERFLOW;
-        return 0;
-    }
-
-    big N = {0}, D = {0}, num = {0}, den = {0}, tmp = {0};
+static uint64_t round_ratio(big *Np, big *Dp, const fmt *f, uint8_t *status, int *err) {
+    big N = *Np, D = *Dp, num = {0}, den = {0}, tmp = {0};
     uint64_t bits = 0;
-    *err = 0;
-
-    /* N = digits * 10^max(E,0),  D = 10^max(-E,0)  so that V = N / D. */
-    if (big_set_u64(&N, 0)) goto oom;
-    {
-        size_t k = first;
-        while (k <= last) {
-            uint32_t chunk = 0, mul = 1;
-            for (int j = 0; j < 9 && k <= last; j++, k++) {
-                chunk = chunk * 10 + (uint32_t)digit_at(t, k);
-                mul *= 10;
-            }
-            if (big_mul_add_small(&N, mul, chunk)) goto oom;
-        }
-    }
-    if (big_set_u64(&D, 1)) goto oom;
-    if (E >= 0) {
-        if (big_mul_pow10(&N, E)) goto oom;
-    } else {
-        if (big_mul_pow10(&D, -E)) goto oom;
-    }
-
     /* k = floor(log2 V).  With bn, bd the bit lengths,
      * V lies in (2^(bn-1-bd), 2^(bn-bd+1)), so k is bn-bd or bn-bd-1:
      * it is bn-bd exactly when N >= D * 2^(bn-bd).                          */
@@ -382,11 +403,109 @@ oom:
     return f->qnan_bits;
 }
 
-/* One field in format f.  Returns 0, or -1 if memory ran out. */
-static int parse_field_fmt(const char *s, size_t n, const fmt *f, uint64_t *out_bits,
+/*
+ * Nearest value of format f to D * 10^E for a natural D given by its
+ * significant digits [first, last] of the token (first digit nonzero, last
+ * digit nonzero).  Returns the unsigned bit pattern; writes the status.
+ */
+static uint64_t convert_exact(const token *t, size_t first, size_t last, int64_t E,
+                              const fmt *f, uint8_t *status, int *err) {
+    size_t nd = last - first + 1;
+    /* Cheap range exits, each by a wide margin:
+     *   10^(nd-1+E) <= V < 10^(nd+E).
+     *   nd-1+E >= dec_ovf  =>  V >= 10^dec_ovf > 2^(emax+1): rounds to infinity.
+     *   nd+E <= dec_unf    =>  V < 10^dec_unf < 2^(emin-p): rounds to zero.  */
+    if ((int64_t)nd - 1 + E >= f->dec_ovf) {
+        *status = OR_OVERFLOW;
+        return f->inf_bits;
+    }
+    if ((int64_t)nd + E <= f->dec_unf) {
+        *status = OR_UNDERFLOW;
+        return 0;
+    }
+
+    big N = {0}, D = {0};
+    *err = 0;
+
+    /* N = digits * 10^max(E,0),  D = 10^max(-E,0)  so that V = N / D. */
+    if (big_set_u64(&N, 0)) goto oom;
+    {
+        size_t k = first;
+        while (k <= last) {
+            uint32_t chunk = 0, mul = 1;
+            for (int j = 0; j < 9 && k <= last; j++, k++) {
+                chunk = chunk * 10 + (uint32_t)digit_at(t, k);
+                mul *= 10;
+            }
+            if (big_mul_add_small(&N, mul, chunk)) goto oom;
+        }
+    }
+    if (big_set_u64(&D, 1)) goto oom;
+    if (E >= 0) {
+        if (big_mul_pow10(&N, E)) goto oom;
+    } else {
+        if (big_mul_pow10(&D, -E)) goto oom;
+    }
+    return round_ratio(&N, &D, f, status, err);
+oom:
+    big_free(&N);
+    big_free(&D);
+    *err = 1;
+    *status = OR_INVALID;
+    return f->qnan_bits;
+}
+
+/*
+ * Nearest value of format f to H * 2^E2 for the natural H given by the
+ * significant hexadecimal digits [first, last] of the token (first and last
+ * digit nonzero).  A hexadecimal float is a dyadic rational, so the same
+ * exact rounding applies with D a power of two.
+ */
+static uint64_t convert_hex(const token *t, size_t first, size_t last, int64_t E2, const fmt *f,
+                            uint8_t *status, int *err) {
+    size_t nd = last - first + 1;
+    int top = digit_at(t, first), tb = 0;
+    while (top) {
+        tb++;
+        top >>= 1;
+    }
+    /* 2^(bl-1) <= H < 2^bl with bl = 4 (nd-1) + bits of the first digit.
+     *   bl-1+E2 >= emax+1  =>  V >= 2^(emax+1): rounds to infinity.
+     *   bl+E2 <= emin-p    =>  V < 2^(emin-p), half the smallest subnormal: 0. */
+    const int64_t bl = 4 * (int64_t)(nd - 1) + tb;
+    *err = 0;
+    if (bl - 1 + E2 >= f->emax + 1) {
+        *status = OR_OVERFLOW;
+        return f->inf_bits;
+    }
+    if (bl + E2 <= f->emin - f->p) {
+        *status = OR_UNDERFLOW;
+        return 0;
+    }
+    big N = {0}, D = {0};
+    if (big_set_u64(&N, 0)) goto oom;
+    for (size_t k = first; k <= last; k++)
+        if (big_mul_add_small(&N, 16, (uint32_t)digit_at(t, k))) goto oom;
+    if (big_set_u64(&D, 1)) goto oom;
+    if (E2 >= 0) {
+        if (big_shl(&N, (uint64_t)E2)) goto oom;
+    } else {
+        if (big_shl(&D, (uint64_t)(-E2))) goto oom;
+    }
+    return round_ratio(&N, &D, f, status, err);
+oom:
+    big_free(&N);
+    big_free(&D);
+    *err = 1;
+    *status = OR_INVALID;
+    return f->qnan_bits;
+}
+
+/* One field in format f under a grammar.  Returns 0, or -1 if memory ran out. */
+static int parse_field_fmt(const char *s, size_t n, const fmt *f, int grammar, uint64_t *out_bits,
                            uint8_t *status) {
     token t;
-    if (tokenize(s, n, &t) != 0) {
+    if (tokenize(s, n, grammar, &t) != 0) {
         *out_bits = f->qnan_bits;
         *status = OR_INVALID;
         return 0;
@@ -405,10 +524,18 @@ static int parse_field_fmt(const char *s, size_t n, const fmt *f, uint64_t *out_
     size_t last = total - 1;
     while (digit_at(&t, last) == 0) last--;
     /* V = (digits first..last) * 10^E,
-     * E = explicit exponent - fraction digits + stripped trailing zeros.   */
-    int64_t E = t.exp10 - (int64_t)t.n_frac + (int64_t)(total - 1 - last);
+     * E = explicit exponent - fraction digits + stripped trailing zeros;
+     * for a hexadecimal float V = (hex digits first..last) * 2^E with four
+     * binary places per hexadecimal digit.                                 */
     int err = 0;
-    uint64_t bits = convert_exact(&t, first, last, E, f, status, &err);
+    uint64_t bits;
+    if (t.hex) {
+        int64_t E2 = t.exp10 - 4 * (int64_t)t.n_frac + 4 * (int64_t)(total - 1 - last);
+        bits = convert_hex(&t, first, last, E2, f, status, &err);
+    } else {
+        int64_t E = t.exp10 - (int64_t)t.n_frac + (int64_t)(total - 1 - last);
+        bits = convert_exact(&t, first, last, E, f, status, &err);
+    }
     *out_bits = bits | sign;
     if (bits == f->qnan_bits) *out_bits = bits;
     return err ? -1 : 0;
@@ -416,15 +543,22 @@ static int parse_field_fmt(const char *s, size_t n, const fmt *f, uint64_t *out_
 
 /* One field -> binary64.  Returns 0, or -1 if memory ran out. */
 int oracle_parse_field(const char *s, size_t n, uint64_t *out_bits, uint8_t *status) {
-    return parse_field_fmt(s, n, &FMT64, out_bits, status);
+    return parse_field_fmt(s, n, &FMT64, OR_GRAMMAR_DEFAULT, out_bits, status);
 }
 
 /* One field -> binary32 (the pattern in the low 32 bits). */
 int oracle_parse_field_f32(const char *s, size_t n, uint32_t *out_bits, uint8_t *status) {
     uint64_t b = 0;
-    int rc = parse_field_fmt(s, n, &FMT32, &b, status);
+    int rc = parse_field_fmt(s, n, &FMT32, OR_GRAMMAR_DEFAULT, &b, status);
     *out_bits = (uint32_t)b;
     return rc;
+}
+
+/* One field, format (0 binary64, 1 binary32) and grammar (OR_GRAMMAR_*)
+ * chosen; the pattern is in the low bits of *out_bits. */
+int oracle_parse_field_ex(const char *s, size_t n, int f32, int grammar, uint64_t *out_bits,
+                          uint8_t *status) {
+    return parse_field_fmt(s, n, f32 ? &FMT32 : &FMT64, grammar, out_bits, status);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -449,6 +583,7 @@ typedef struct {
     uint64_t *out_bits;   /* binary64 results, or */
     uint32_t *out_bits32; /* binary32 results */
     uint8_t *status;
+    int grammar;
     int err;
 } work;
 
@@ -472,9 +607,12 @@ static void *worker(void *arg) {
         while (q < w->len && !is_sep(w->text[q], w->delim)) q++;
         int rc;
         if (w->out_bits32) {
-            rc = oracle_parse_field_f32(w->text + p, q - p, &w->out_bits32[idx], &w->status[idx]);
+            uint64_t b = 0;
+            rc = parse_field_fmt(w->text + p, q - p, &FMT32, w->grammar, &b, &w->status[idx]);
+            w->out_bits32[idx] = (uint32_t)b;
         } else {
-            rc = oracle_parse_field(w->text + p, q - p, &w->out_bits[idx], &w->status[idx]);
+            rc = parse_field_fmt(w->text + p, q - p, &FMT64, w->grammar, &w->out_bits[idx],
+                                 &w->status[idx]);
         }
         if (rc) w->err = 1;
         idx++;
@@ -490,7 +628,7 @@ static void *worker(void *arg) {
  */
 static int parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
                         uint32_t *out_bits32, uint8_t *status, uint64_t cap, uint64_t *count,
-                        int nthreads) {
+                        int nthreads, int grammar) {
     uint64_t total = oracle_count_fields(text, len, delim);
     *count = total;
     if (total > cap) return -1;
@@ -513,6 +651,7 @@ static int parse_buffer(const char *text, size_t len, char delim, uint64_t *out_
         ws[i].out_bits = out_bits;
         ws[i].out_bits32 = out_bits32;
         ws[i].status = status;
+        ws[i].grammar = grammar;
         ws[i].first_index = before;
         before += count_starts(text, len, delim, ws[i].lo, ws[i].hi);
     }
@@ -531,11 +670,21 @@ static int parse_buffer(const char *text, size_t len, char delim, uint64_t *out_
 
 int oracle_parse_buffer(const char *text, size_t len, char delim, uint64_t *out_bits,
                         uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
-    return parse_buffer(text, len, delim, out_bits, NULL, status, cap, count, nthreads);
+    return parse_buffer(text, len, delim, out_bits, NULL, status, cap, count, nthreads,
+                        OR_GRAMMAR_DEFAULT);
 }
 
 /* As oracle_parse_buffer, to binary32. */
 int oracle_parse_buffer_f32(const char *text, size_t len, char delim, uint32_t *out_bits,
                             uint8_t *status, uint64_t cap, uint64_t *count, int nthreads) {
-    return parse_buffer(text, len, delim, NULL, out_bits, status, cap, count, nthreads);
+    return parse_buffer(text, len, delim, NULL, out_bits, status, cap, count, nthreads,
+                        OR_GRAMMAR_DEFAULT);
+}
+
+/* Either format (binary32 patterns are stored as uint32), any grammar. */
+int oracle_parse_buffer_ex(const char *text, size_t len, char delim, int f32, int grammar,
+                           void *out_bits, uint8_t *status, uint64_t cap, uint64_t *count,
+                           int nthreads) {
+    return parse_buffer(text, len, delim, f32 ? NULL : (uint64_t *)out_bits,
+                        f32 ? (uint32_t *)out_bits : NULL, status, cap, count, nthreads, grammar);
 }
