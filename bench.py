@@ -195,25 +195,25 @@ def cut_at_line(text: bytes, nbytes: int) -> bytes:
     return text[:k] if k > 0 else text[:nbytes]
 
 
-def oracle_time(sample: bytes, threads: int) -> float:
+def oracle_time(sample: bytes, threads: int, f32: bool = False) -> float:
     import oracle
     t = time.perf_counter()
-    oracle.parse_buffer(sample, b"\n", nthreads=threads)
+    oracle.parse_buffer(sample, b"\n", nthreads=threads, f32=f32)
     return time.perf_counter() - t
 
 
-def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0) -> dict:
+def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0, f32: bool = False) -> dict:
     """The oracle on every host core, on a prefix of the workload sized for
     about `seconds` of work (from a 1 MB calibration), repeated when the
     whole text takes less."""
     cores = os.cpu_count() or 1
     calib = cut_at_line(text, 1 << 20)
-    rate = len(calib) / oracle_time(calib, cores)
+    rate = len(calib) / oracle_time(calib, cores, f32)
     sample = cut_at_line(text, int(min(64 << 20, max(1 << 20, rate * seconds))))
     passes = max(1, int(rate * seconds / max(len(sample), 1) / 4))
     t = time.perf_counter()
     for _ in range(passes):
-        oracle_time(sample, cores)
+        oracle_time(sample, cores, f32)
     dt = time.perf_counter() - t
     return {"value": passes * len(sample) / dt / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
@@ -285,21 +285,24 @@ def run_ours(args, world, rank, dist) -> None:
     B = len(text)
     host_text = torch.frombuffer(bytearray(text), dtype=torch.uint8)
     d_text = host_text.to(dev)
-    out = torch.empty(B, dtype=torch.float64, device=dev)
+    f32 = args.format == "f32"
+    out = torch.empty(B, dtype=torch.float32 if f32 else torch.float64, device=dev)
+    parse_into = fp.parse_f32_into if f32 else fp.parse_f64_into
+    vbytes = 4 if f32 else 8  # bytes of one result value
     st = torch.empty(B, dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     # one untimed parse, checked against the oracle on a prefix
-    fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+    parse_into(d_text, out, st, cnt, stream=stream)
     torch.cuda.synchronize()
     N = int(cnt.item())
     check_fields = 0
     if rank == 0 and not args.skip_check:
         import oracle
         prefix = cut_at_line(text, 4 << 20)
-        rb, rs = oracle.parse_buffer(prefix)
-        got = out[:rb.size].cpu().numpy().view(np.uint64)
+        rb, rs = oracle.parse_buffer(prefix, f32=f32)
+        got = out[:rb.size].cpu().numpy().view(np.uint32 if f32 else np.uint64)
         gst = st[:rb.size].cpu().numpy()
         if not (np.array_equal(got, rb) and np.array_equal(gst, rs)):
             raise SystemExit("bench: GPU output differs from the oracle")
@@ -309,13 +312,13 @@ def run_ours(args, world, rank, dist) -> None:
 
     sampler = ClockSampler(local).start() if rank == 0 else None
     for _ in range(args.warmup):
-        fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+        parse_into(d_text, out, st, cnt, stream=stream)
     # keep the GPU busy for a second before timing so the clock samples
     # describe the same steady state as the timed steps
     t_end = time.perf_counter() + args.clock_settle
     while time.perf_counter() < t_end:
         for _ in range(20):
-            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+            parse_into(d_text, out, st, cnt, stream=stream)
         torch.cuda.synchronize()
 
     fp.timing_enable(True)
@@ -332,7 +335,7 @@ def run_ours(args, world, rank, dist) -> None:
         for a, b in evs:
             scrub.fill_(1)  # evict the text and results from L2, outside the timed pair
             a.record(stream)
-            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+            parse_into(d_text, out, st, cnt, stream=stream)
             b.record(stream)
         torch.cuda.synchronize()
         step_ms = [a.elapsed_time(b) for a, b in evs]
@@ -342,7 +345,7 @@ def run_ours(args, world, rank, dist) -> None:
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            fp.parse_f64_into(d_text, out, st, cnt, stream=stream)
+            parse_into(d_text, out, st, cnt, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         elapsed_ms = e0.elapsed_time(e1)
@@ -357,7 +360,7 @@ def run_ours(args, world, rank, dist) -> None:
 
     # end to end: host text -> device, parse, results -> host, every step
     e2e = None
-    if not args.skip_e2e:
+    if not args.skip_e2e and not f32:
         h_text = host_text.pin_memory()
         h_out = torch.empty(B, dtype=torch.float64).pin_memory()
         h_st = torch.empty(B, dtype=torch.uint8).pin_memory()
@@ -384,11 +387,11 @@ def run_ours(args, world, rank, dist) -> None:
     if rank != 0:
         return
     peak, peak_kind = measured_hbm_peak()
-    alg_bytes = B + 9 * N
+    alg_bytes = B + (vbytes + 1) * N
     parse_ms = kt["parse_ms"] / max(kt["calls"], 1)
     fb_ms = kt["fallback_ms"] / max(kt["calls"], 1)
     achieved = alg_bytes / (parse_ms / 1e3) / 1e9
-    traffic = profiled_traffic("parse_kernel") if kind == "bulk" else None
+    traffic = profiled_traffic("parse_kernel") if kind == "bulk" and not f32 else None
     cfg = fp.get_config()
     s = fp.stats(reset=True, stream=stream)
     l2 = ("no flush: each step reads %.0f MB of text and writes %.0f MB of results, more than "
@@ -399,8 +402,9 @@ def run_ours(args, world, rank, dist) -> None:
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32" if f32 else "u64", "data": "synthetic",
         "config": {"workload": desc, "numbers": N, "text_bytes": B,
+                   "format": "binary32" if f32 else "binary64",
                    "mfloats_per_s": world * N * args.steps / (elapsed_ms / 1e3) / 1e6,
                    "l2": l2,
                    "parallelism": "replicas: one independent shard per GPU",
@@ -431,7 +435,7 @@ def run_ours(args, world, rank, dist) -> None:
     if e2e:
         line["e2e"] = e2e
     if not args.skip_baseline:
-        line["cpu_baseline"] = cpu_baseline(text, kind)
+        line["cpu_baseline"] = cpu_baseline(text, kind, f32=f32)
     print(json.dumps(line), flush=True)
 
 
@@ -837,6 +841,8 @@ def main() -> None:
     ap.add_argument("--serve-budget", type=int, default=40_000_000_000)
     ap.add_argument("--serve-batch", type=int, default=1024)
     ap.add_argument("--serve-inflight", type=int, default=3)
+    ap.add_argument("--format", choices=["f64", "f32"], default="f64",
+                    help="bulk/uniform/hard: binary64 (fp_parse_f64) or binary32 (fp_parse_f32)")
     ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")
     ap.add_argument("--batch-bytes", type=int, default=2 << 30, help="batch: total text bytes")
     args = ap.parse_args()
