@@ -80,8 +80,8 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-PARSE_KERNEL_SOURCES = ("fp_parse_kernel.cu", "fp_device.cuh", "fp_sync.cuh", "fp_types.cuh",
-                        "pow5_table.inc")
+PARSE_KERNEL_SOURCES = ("fp_parse_kernel.cu", "fp_parse_kernel.cuh", "fp_device.cuh",
+                        "fp_sync.cuh", "fp_types.cuh", "pow5_table.inc")
 
 
 def _code_only(src: bytes) -> bytes:

@@ -84,7 +84,8 @@ enum {
     FP_STATUS_OK = 0,        /* finite, or an exact zero                      */
     FP_STATUS_INVALID = 1,   /* not a number under the grammar; value is NaN  */
     FP_STATUS_OVERFLOW = 2,  /* finite text whose value rounds to +-infinity  */
-    FP_STATUS_UNDERFLOW = 3  /* nonzero text whose value rounds to +-0        */
+    FP_STATUS_UNDERFLOW = 3, /* nonzero text whose value rounds to +-0        */
+    FP_STATUS_BAD_SHAPE = 4  /* fp_parse_ex column-major: wrong terminator    */
 };
 
 /* Path counters, accumulated over calls on one stream (fp_get_stats).      */
@@ -143,6 +144,53 @@ FP_API fp_err_t fp_parse_f64(const char *text, size_t len, char delim, double *o
 FP_API fp_err_t fp_parse_f32(const char *text, size_t len, char delim, float *out_f32,
                              uint8_t *out_status, uint64_t *out_count,
                              struct CUstream_st *stream);
+
+/*
+ * fp_parse_ex -- one buffer with options beyond the decimal-to-binary64
+ *   default: the binary32 format, the hexadecimal-float or JSON grammar, and
+ *   column-major results for CSV blocks.  (The paper's Algorithm 1 covers
+ *   both formats, Section 5; hexadecimal floats are Appendix C's exact form;
+ *   Section 4 names JSON's stricter number grammar among the format
+ *   variants; the columnar layout has no counterpart in the paper.)
+ *   opt->delim     the second separator besides '\n'
+ *   opt->format    FP_FORMAT_F64 (out_values: doubles) or FP_FORMAT_F32 (floats)
+ *   opt->grammar   FP_GRAMMAR_DECIMAL: the decimal grammar above;
+ *                  FP_GRAMMAR_HEX: that, or a hexadecimal float
+ *                    [+-]? 0[xX] (h+ (. h*)? | . h+) ([pP] [+-]? d+)?
+ *                    (binary exponent optional; rounded exactly, ties to even);
+ *                  FP_GRAMMAR_JSON: the JSON number grammar
+ *                    -? (0 | [1-9] d*) (. d+)? ([eE] [+-]? d+)?
+ *                    ('+', leading zeros, "5." and ".5" are INVALID)
+ *   opt->columns   0: field i -> out_values[i] (fp_max_fields(len) entries);
+ *                  K >= 2 (< 2^24): field i -> column i mod K, row i div K,
+ *                    entry (i mod K) * rows_cap + (i div K); K * rows_cap
+ *                    entries; fields whose row is >= rows_cap are not stored
+ *                    (the count still counts them).  A field whose terminator
+ *                    disagrees with its column -- the last column must end at
+ *                    '\n' or at the end of the text, the others at delim --
+ *                    gets status FP_STATUS_BAD_SHAPE (its value is stored).
+ *   opt->rows_cap  entries per column (columns >= 2)
+ * The JSON and column-major modes run with 8 KiB chunks when the configured
+ * chunk size is 4 or 8 KiB and with 16 KiB chunks otherwise.  Binary32 and
+ * column-major calls use the same per-stream location scratch as
+ * fp_parse_f32.  FP_ERR_ARG for unknown options or columns == 1.
+ */
+#define FP_FORMAT_F64 0
+#define FP_FORMAT_F32 1
+#define FP_GRAMMAR_DECIMAL 0
+#define FP_GRAMMAR_HEX 1
+#define FP_GRAMMAR_JSON 2
+typedef struct {
+  char delim;
+  uint8_t format;
+  uint8_t grammar;
+  uint8_t reserved;
+  uint32_t columns;
+  uint64_t rows_cap;
+} fp_options_t;
+FP_API fp_err_t fp_parse_ex(const char *text, size_t len, const fp_options_t *opt,
+                            void *out_values, uint8_t *out_status, uint64_t *out_count,
+                            struct CUstream_st *stream);
 
 /*
  * fp_parse_f64_batch -- parse many independent buffers in one persistent

@@ -16,7 +16,8 @@ from . import _lib
 from ._lib import (STATUS_INVALID, STATUS_OK, STATUS_OVERFLOW, STATUS_UNDERFLOW, Config,
                    FpError, Stats)
 
-__all__ = ["BatchPlan", "Server", "parse_f32", "parse_f32_into", "parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
+__all__ = ["BatchPlan", "Server", "parse_ex", "parse_ex_into", "parse_f32", "parse_f32_into",
+           "parse_f64", "parse_f64_into", "parse_f64_host", "parse_f64_host_into", "parse_f64_batch",
            "parse_f64_batch_into", "max_fields", "stats", "get_error", "set_config",
            "get_config", "autotune", "timing_enable", "timing_read", "shutdown", "library_path", "FpError", "STATUS_OK",
            "STATUS_INVALID", "STATUS_OVERFLOW", "STATUS_UNDERFLOW"]
@@ -120,6 +121,51 @@ def parse_f32(text: torch.Tensor, delim=b"\n", stream=None):
     if stream is not None:
         stream.synchronize()
     n = int(cnt.item())
+    return out[:n], st[:n]
+
+
+_GRAMMARS = {"decimal": 0, "hex": 1, "json": 2}
+
+
+def parse_ex_into(text: torch.Tensor, out_values: torch.Tensor, out_status: torch.Tensor,
+                  out_count: torch.Tensor, delim=b"\n", grammar: str = "decimal",
+                  columns: int = 0, rows_cap: int = 0, stream=None) -> None:
+    """fp_parse_ex: out_values float64 or float32 picks the format; grammar
+    'decimal', 'hex' or 'json'; columns K >= 2 stores field i at
+    (i mod K) * rows_cap + i div K."""
+    _check_text(text)
+    n = text.numel()
+    if out_values.dtype not in (torch.float64, torch.float32) or out_status.dtype != torch.uint8:
+        raise TypeError("out_values must be float64 or float32 and out_status uint8")
+    need = columns * rows_cap if columns else n
+    if need and (out_values.numel() < need or out_status.numel() < need):
+        raise ValueError("output arrays need %d entries" % need)
+    opt = _lib.Options(_delim_byte(delim), 1 if out_values.dtype == torch.float32 else 0,
+                       _GRAMMARS[grammar], 0, columns, rows_cap)
+    rc = _lib.load().fp_parse_ex(text.data_ptr() if n else None, n, ctypes.byref(opt),
+                                 out_values.data_ptr() if need else None,
+                                 out_status.data_ptr() if need else None, out_count.data_ptr(),
+                                 _stream_handle(stream))
+    _lib.check(rc, "fp_parse_ex")
+
+
+def parse_ex(text: torch.Tensor, delim=b"\n", f32: bool = False, grammar: str = "decimal",
+             columns: int = 0, rows_cap: int = 0, stream=None):
+    """fp_parse_ex on a device buffer.  Field order: (values, status) of the
+    field count; column-major: (values, status) of shape (columns, rows_cap)
+    (entries no field reaches are left as allocated).  Synchronises."""
+    _check_text(text)
+    dev = text.device
+    cap = columns * rows_cap if columns else max(text.numel(), 1)
+    out = torch.empty(cap, dtype=torch.float32 if f32 else torch.float64, device=dev)
+    st = torch.full((cap,), 0xEE, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    parse_ex_into(text, out, st, cnt, delim, grammar, columns, rows_cap, stream)
+    if stream is not None:
+        stream.synchronize()
+    n = int(cnt.item())
+    if columns:
+        return out.view(columns, rows_cap), st.view(columns, rows_cap), n
     return out[:n], st[:n]
 
 

@@ -13,10 +13,12 @@ _lib = None
 
 FP_OK, FP_ERR_ARG, FP_ERR_CAPACITY, FP_ERR_CUDA, FP_ERR_BUDGET, FP_ERR_TIMEOUT, \
     FP_ERR_INTERNAL = range(7)
-STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW = range(4)
+STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW, STATUS_BAD_SHAPE = range(5)
+FORMAT_F64, FORMAT_F32 = 0, 1
+GRAMMAR_DECIMAL, GRAMMAR_HEX, GRAMMAR_JSON = 0, 1, 2
 
 # every symbol include/fpparse.h declares
-EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_f64_batch", "fp_get_stats",
+EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_ex", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
            "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
            "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_server_create", "fp_server_submit",
@@ -62,6 +64,12 @@ class ServerStats(ctypes.Structure):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
+class Options(ctypes.Structure):
+    _fields_ = [("delim", ctypes.c_char), ("format", ctypes.c_uint8), ("grammar", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint8), ("columns", ctypes.c_uint32),
+                ("rows_cap", ctypes.c_uint64)]
+
+
 class FpError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
@@ -92,6 +100,8 @@ def load(build_if_missing: bool = True):
         lib.fp_parse_f64.restype = ctypes.c_int
         lib.fp_parse_f32.argtypes = [vp, sz, ctypes.c_char, vp, u8p, vp, vp]
         lib.fp_parse_f32.restype = ctypes.c_int
+        lib.fp_parse_ex.argtypes = [vp, sz, ctypes.POINTER(Options), vp, u8p, vp, vp]
+        lib.fp_parse_ex.restype = ctypes.c_int
         lib.fp_parse_f64_batch.argtypes = [vp, vp, ctypes.c_uint32, ctypes.c_char, vp, u8p,
                                            vp, vp, vp]
         lib.fp_parse_f64_batch.restype = ctypes.c_int

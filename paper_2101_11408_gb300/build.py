@@ -17,8 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfpparse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["fp_parse_kernel.cu", "fp_fallback_kernel.cu", "fp_api.cu", "fp_noalloc.cu",
-           "fp_server.cu", "fp_copy_kernel.cu"]
+SOURCES = ["fp_parse_kernel.cu", "fp_parse_kernel_ext.cu", "fp_fallback_kernel.cu", "fp_api.cu",
+           "fp_noalloc.cu", "fp_server.cu", "fp_copy_kernel.cu"]
 HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "pow5_table.inc",
            os.path.join(INCLUDE, "fpparse.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

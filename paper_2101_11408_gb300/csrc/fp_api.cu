@@ -59,6 +59,7 @@ struct DeviceInfo {
   int sms = 0;
   std::map<int, int> parse_occ;    // chunk bytes -> resident blocks per SM (binary64)
   std::map<int, int> parse_occ32;  // the same for the binary32 kernels
+  std::map<int, int> parse_occ_ext;  // JSON / column-major kernels (8 and 16 KiB chunks)
   int fb_occ = 0, fb_occ32 = 0;
   char name[256] = {0};
 };
@@ -142,6 +143,11 @@ fp_err_t device_info(int dev, DeviceInfo** out) {
       di.parse_occ[c] = std::max(occ, 1);
       FP_CUDA(fp::parse_occupancy(c, &occ, true));
       di.parse_occ32[c] = std::max(occ, 1);
+    }
+    for (int c : {8192, 16384}) {
+      int occ = 0;
+      FP_CUDA(fp::parse_occupancy_ext(c, &occ));
+      di.parse_occ_ext[c] = std::max(occ, 1);
     }
     FP_CUDA(fp::fallback_occupancy(&di.fb_occ, false));
     di.fb_occ = std::max(di.fb_occ, 1);
@@ -258,7 +264,7 @@ void fill_desc(BufDesc& d, const char* text, size_t len, unsigned long long chun
 // Queue the two kernels of one call (binary32 results when f32).
 fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& p,
              unsigned long long total_chunks, unsigned long long total_bytes, cudaStream_t stream,
-             bool f32 = false) {
+             bool f32 = false, int mode = 0) {
   if (s->epoch >= fp::LB_EPOCH_MAX) {
     FP_CUDA(cudaMemsetAsync(s->chunk_status, 0, s->cap_chunks * sizeof(unsigned long long), stream));
     s->epoch = 1;
@@ -272,7 +278,8 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   p.ovf_cap = s->ovf_cap;
   p.total_chunks = total_chunks;
   if (!p.loc) p.loc = p.out_bits;  // binary64: the location sits in the output slot
-  const int occ = (f32 ? di.parse_occ32 : di.parse_occ).at((int)cfg.chunk_bytes);
+  const int occ = (mode ? di.parse_occ_ext : (f32 ? di.parse_occ32 : di.parse_occ))
+                      .at((int)cfg.chunk_bytes);
   const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
   unsigned long long grid = (unsigned long long)di.sms * per_sm;
   if (grid > total_chunks) grid = total_chunks;
@@ -287,7 +294,8 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
       for (cudaEvent_t& ev : s->ev[slot]) FP_CUDA(cudaEventCreate(&ev));
     FP_CUDA(cudaEventRecord(s->ev[slot][0], stream));
   }
-  FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
+  if (mode) FP_CUDA(fp::launch_parse_ext(p, (int)cfg.chunk_bytes, (int)grid, stream, f32, mode));
+  else FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
   if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
   FP_CUDA(fp::launch_fallback(p, di.sms * (f32 ? di.fb_occ32 : di.fb_occ), stream, f32));
   if (timing) {
@@ -481,6 +489,62 @@ fp_err_t fp_parse_f32(const char* text, size_t len, char delim, float* out_f32,
   p.out_status = out_status;
   p.loc = s->loc;
   return run(s, cfg, *di, p, nch, len, stream, true);
+}
+
+fp_err_t fp_parse_ex(const char* text, size_t len, const fp_options_t* opt, void* out_values,
+                     uint8_t* out_status, uint64_t* out_count, struct CUstream_st* stream_) {
+  if (!opt || !out_count || len >= MAX_LEN) return FP_ERR_ARG;
+  if (opt->format > FP_FORMAT_F32 || opt->grammar > FP_GRAMMAR_JSON || opt->reserved)
+    return FP_ERR_ARG;
+  const uint64_t K = opt->columns;
+  if (K == 1 || K >= (1u << 24)) return FP_ERR_ARG;
+  unsigned long long out_cap = len;
+  if (K) {
+    if (opt->rows_cap == 0 || opt->rows_cap > (~0ull) / K) return FP_ERR_ARG;
+    out_cap = K * opt->rows_cap;
+  }
+  if (len > 0 && (!text || !out_values || !out_status)) return FP_ERR_ARG;
+  const bool f32 = opt->format == FP_FORMAT_F32;
+  const int mode = (opt->grammar == FP_GRAMMAR_JSON ? 1 : 0) | (K ? 2 : 0);  // MODE_* bits
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Config cfg = g_cfg;
+  if (mode) cfg.chunk_bytes = cfg.chunk_bytes <= 8192 ? 8192 : 16384;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
+  const unsigned long long nch = chunks_of(t & 15, len, cfg.chunk_bytes);
+  Scratch* s = nullptr;
+  e = get_scratch(stream, nch, 1, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  const bool side_loc = f32 || K;  // pending locations outside the output slots
+  if (side_loc && len > s->cap_loc) {
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->loc);
+    s->loc = nullptr;
+    s->cap_loc = 0;
+    FP_CUDA(cudaMalloc(&s->loc, len * sizeof(unsigned long long)));
+    s->cap_loc = len;
+  }
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  fill_desc(p.one, text, len, 0, nch, 0, out_cap, out_count);
+  p.descs = nullptr;
+  p.nbuf = 1;
+  p.delim = (unsigned char)opt->delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_values);
+  p.out_status = out_status;
+  p.loc = side_loc ? s->loc : nullptr;
+  p.grammar = opt->grammar;
+  if (K) {
+    p.columns = (unsigned int)K;
+    p.rows_cap = opt->rows_cap;
+    p.col_magic = (unsigned long long)((((unsigned __int128)1 << 64) + K - 1) / K);
+  }
+  return run(s, cfg, *di, p, nch, len, stream, f32, mode);
 }
 
 fp_err_t fp_parse_f64_batch(const char* const* texts, const size_t* lens, uint32_t nbuf,

@@ -26,6 +26,7 @@ enum : uint8_t {
   ST_INVALID = 1,
   ST_OVERFLOW = 2,
   ST_UNDERFLOW = 3,
+  ST_BAD_SHAPE = 4,          // columnar output: the field's terminator disagrees with its column
   ST_PENDING = 0xFF,         // internal result of the short-field parser
   ST_PENDING_QUEUED = 0xFE,  // stored status: pending, listed in the fallback queue
   ST_PENDING_SCAN = 0xFF,    // stored status: pending, found by scanning its chunk
@@ -56,6 +57,10 @@ struct F32 {
   static constexpr int DEC_OVF = 39, DEC_UNF = -46;  // 1e39 > 2^128, 1e-46 < 2^-150
   static constexpr uint64_t INF = 0x7F800000ull, QNAN = 0x7FC00000ull, SIGN = 0x80000000ull;
 };
+
+// Field grammars (the readings of include/fpparse.h): the decimal one, that
+// or a hexadecimal float (Appendix C), or the JSON number grammar.
+enum : uint32_t { GRAMMAR_DECIMAL = 0, GRAMMAR_HEX = 1, GRAMMAR_JSON = 2 };
 
 // Fields longer than this many bytes are handed to the fallback kernel.
 constexpr int LMAX = 64;
@@ -221,6 +226,48 @@ FP_HD uint8_t status_of(uint64_t pos_bits) {
   return ST_OK;
 }
 
+// Nearest positive pattern of F to (m + d) 2^e2, where 0 <= d < 1 and d > 0
+// exactly when `sticky` (hexadecimal floats are dyadic: the digits give the
+// bits, so rounding needs no table and no big numbers).  m != 0.
+template <class F>
+FP_HD uint64_t hex_to_bits(uint64_t m, int64_t e2, bool sticky) {
+  const int l = clz64(m);
+  m <<= l;
+  e2 -= l;  // value in [2^(e2+63), 2^(e2+64))
+  const int64_t E = e2 + 63 + F::BIAS;  // biased exponent if normal
+  if (E >= F::EMAX_FIELD) return F::INF;
+  // bits of m below the last place kept: 63 - MBITS when normal, more when
+  // subnormal (the last place is fixed at 2^(1 - BIAS - MBITS))
+  const int64_t sh = (63 - F::MBITS) + (E < 1 ? 1 - E : 0);
+  if (sh > 64) return 0;  // below half the smallest subnormal
+  uint64_t q, rem, half;
+  if (sh == 64) {
+    q = 0;
+    rem = m;
+    half = 1ull << 63;
+  } else {
+    q = m >> sh;
+    rem = m & ((1ull << sh) - 1);
+    half = 1ull << (sh - 1);
+  }
+  if (rem > half || (rem == half && (sticky || (q & 1)))) q += 1;
+  if (E < 1) return q;  // subnormal (reaching 2^MBITS gives the smallest normal)
+  uint64_t Ef = (uint64_t)E;
+  if (q >> (F::MBITS + 1)) {  // rounding carried into a new bit
+    q >>= 1;
+    Ef += 1;
+    if (Ef >= (uint64_t)F::EMAX_FIELD) return F::INF;
+  }
+  return (Ef << F::MBITS) | (q & ((1ull << F::MBITS) - 1));
+}
+
+FP_HD int hex_digit(uint32_t c) {
+  if (c - '0' < 10u) return (int)(c - '0');
+  const uint32_t l = c | 0x20u;
+  if (l - 'a' < 6u) return (int)(l - 'a' + 10);
+  return -1;
+}
+
 FP_HD bool is_digit(uint32_t c) { return (c - '0') < 10u; }
 FP_HD bool is_ws(uint32_t c) { return c == ' ' || c == '\t' || c == '\r'; }
 
@@ -241,7 +288,8 @@ struct FieldResult {
 // (w 10^q, (w+1) 10^q), and if both ends round to the same double that is
 // the answer (Section 11); otherwise the field is left pending.
 template <class F = F64>
-FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
+FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab,
+                                    uint32_t grammar = GRAMMAR_DECIMAL) {
   FieldResult r;
   r.two_mul = 0;
   r.is_long = 0;
@@ -249,10 +297,69 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
   int i = 0;
   while (i < n && is_ws(s[i])) i++;
   uint64_t sign = 0;
-  if (i < n && (s[i] == '+' || s[i] == '-')) {
+  if (i < n && (s[i] == '-' || (s[i] == '+' && grammar != GRAMMAR_JSON))) {
     sign = (s[i] == '-') ? F::SIGN : 0;
     i++;
   }
+  if (grammar == GRAMMAR_HEX && i + 1 < n && s[i] == '0' && (s[i + 1] | 0x20) == 'x') {
+    // hexadecimal float: up to 16 significant hex digits in m, the rest into
+    // the exponent (integer digits) or the sticky flag
+    i += 2;
+    uint64_t m = 0;
+    int kept = 0, nd = 0;
+    int64_t e2 = 0;
+    bool sticky = false;
+    for (int part = 0; part < 2; part++) {
+      if (part == 1) {
+        if (i < n && s[i] == '.') i++;
+        else break;
+      }
+      int d;
+      while (i < n && (d = hex_digit(s[i])) >= 0) {
+        if (kept < 16) {
+          if (m || d) {
+            m = m * 16 + (uint64_t)d;
+            kept++;
+          }
+          if (part == 1) e2 -= 4;
+        } else {
+          if (part == 0) e2 += 4;
+          sticky |= (d != 0);
+        }
+        i++;
+        nd++;
+      }
+    }
+    bool ok = nd > 0;
+    if (ok && i < n && (s[i] | 0x20) == 'p') {
+      i++;
+      bool eneg = false;
+      if (i < n && (s[i] == '+' || s[i] == '-')) {
+        eneg = (s[i] == '-');
+        i++;
+      }
+      int ne = 0;
+      int64_t ex = 0;
+      while (i < n && is_digit(s[i])) {
+        if (ex < 100000000) ex = ex * 10 + (s[i] - '0');
+        i++;
+        ne++;
+      }
+      ok = ne > 0;
+      e2 += eneg ? -ex : ex;
+    }
+    while (i < n && is_ws(s[i])) i++;
+    if (!ok || i != n) {
+      r.bits = F::QNAN;
+      r.status = ST_INVALID;
+      return r;
+    }
+    const uint64_t b = m ? hex_to_bits<F>(m, e2, sticky) : 0;
+    r.bits = b | sign;
+    r.status = m ? status_of<F>(b) : ST_OK;
+    return r;
+  }
+  const int int_start = i;
   uint64_t w = 0;
   int nsig = 0;        // significant digits kept in w (<= 19)
   int exp_adj = 0;     // + integer digits dropped, - fraction digits kept
@@ -272,8 +379,11 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
     i++;
     ndig++;
   }
+  const int nint = ndig;
+  bool point = false;
   if (i < n && s[i] == '.') {
     i++;
+    point = true;
     while (i < n && is_digit(s[i])) {
       uint32_t d = s[i] - '0';
       if (nsig < 19) {
@@ -290,6 +400,10 @@ FP_HD FieldResult parse_short_field(const uint8_t* s, int n, const Pow5& tab) {
     }
   }
   bool ok = ndig > 0;
+  if (grammar == GRAMMAR_JSON) {
+    // an integer part without leading zeros; digits after a point
+    ok = ok && nint > 0 && !(nint > 1 && s[int_start] == '0') && !(point && ndig == nint);
+  }
   int64_t ex = 0;
   if (ok && i < n && (s[i] | 0x20) == 'e') {
     i++;
@@ -432,6 +546,9 @@ struct FastToken {
   uint64_t w;     // decimal significand (< 10^19)
   int q;          // decimal exponent
   uint64_t sign;
+  // where the significand starts and ends and where its point is (-1: none);
+  // used by the JSON check, dead code otherwise
+  int s1, send, dot;
 };
 
 // Straight-line tokenizer for the common field shape
@@ -534,7 +651,22 @@ FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
   w = w * 10000u + dig4(x[5]);
   t.w = w;
   t.q = ex - (dpos >= 0 ? 23 - dpos : 0);
+  t.s1 = s1;
+  t.send = sig_end;
+  t.dot = dpos >= 0 ? w0 + dpos : -1;
   return true;
+}
+
+// The JSON number grammar on a field parse_fast accepted: no '+', a digit
+// before the point, a digit after it, and no leading zero before another
+// digit.
+FP_HD bool json_ok_fast(const uint8_t* tile, int s, const FastToken& t) {
+  const uint32_t a = tile[t.s1];
+  bool bad = tile[s] == '+';
+  bad |= a == '.';
+  bad |= t.dot >= 0 && t.dot + 1 == t.send;
+  bad |= a == '0' && t.s1 + 1 < t.send && tile[t.s1 + 1] != '.';
+  return !bad;
 }
 
 }  // namespace fp

@@ -138,6 +138,7 @@ struct LongResult {
   uint8_t status;
   uint8_t bignum;
   uint8_t error;
+  uint8_t nl;  // the field ends at '\n' or at the end of the text (not at the delimiter)
 };
 
 __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c == '\n' || c == delim; }
@@ -145,17 +146,85 @@ __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c ==
 // Parse one field starting at f (at most lim bytes remain in the buffer).
 template <class F>
 __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim, uint32_t delim,
-                                       const Pow5& tab, Big D, Big P, Big B) {
+                                       uint32_t grammar, bool need_nl, const Pow5& tab, Big D,
+                                       Big P, Big B) {
   LongResult r;
   r.bignum = 0;
   r.error = 0;
+  r.nl = 1;
+  if (need_nl) {  // the terminator (only the column-major layout looks at it)
+    unsigned long long t = 0;
+    while (t < lim && !is_sep(f[t], delim)) t++;
+    r.nl = t >= lim || f[t] == '\n';
+  }
   // ---- 1. tokenize ---------------------------------------------------------
   unsigned long long i = 0;
   while (i < lim && is_ws(f[i])) i++;
   uint64_t sign = 0;
-  if (i < lim && (f[i] == '+' || f[i] == '-')) {
+  if (i < lim && (f[i] == '-' || (f[i] == '+' && grammar != GRAMMAR_JSON))) {
     sign = f[i] == '-' ? F::SIGN : 0;
     i++;
+  }
+  if (grammar == GRAMMAR_HEX && i + 1 < lim && f[i] == '0' && (f[i + 1] | 0x20) == 'x') {
+    // a long hexadecimal float: 16 significant hex digits, the rest into the
+    // exponent (integer digits) or the sticky flag; exact without big numbers
+    i += 2;
+    uint64_t m = 0;
+    int kept = 0;
+    unsigned long long nd = 0;
+    long long e2 = 0;
+    bool sticky = false;
+    for (int part = 0; part < 2; part++) {
+      if (part == 1) {
+        if (i < lim && f[i] == '.') i++;
+        else break;
+      }
+      int dv;
+      while (i < lim && (dv = hex_digit(f[i])) >= 0) {
+        if (kept < 16) {
+          if (m || dv) {
+            m = m * 16 + (uint64_t)dv;
+            kept++;
+          }
+          if (part == 1) e2 -= 4;
+        } else {
+          if (part == 0 && e2 < EXP_SAT) e2 += 4;
+          sticky |= (dv != 0);
+        }
+        i++;
+        nd++;
+      }
+    }
+    bool ok = nd > 0;
+    if (ok && i < lim && (f[i] | 0x20) == 'p') {
+      i++;
+      bool eneg = false;
+      if (i < lim && (f[i] == '+' || f[i] == '-')) {
+        eneg = f[i] == '-';
+        i++;
+      }
+      unsigned long long ne = 0;
+      long long ex = 0;
+      while (i < lim && is_digit(f[i])) {
+        if (ex < EXP_SAT) ex = ex * 10 + (f[i] - '0');
+        if (ex > EXP_SAT) ex = EXP_SAT;
+        i++;
+        ne++;
+      }
+      ok = ne > 0;
+      e2 += eneg ? -ex : ex;
+    }
+    while (i < lim && is_ws(f[i])) i++;
+    ok = ok && (i == lim || is_sep(f[i], delim));
+    if (!ok) {
+      r.bits = F::QNAN;
+      r.status = ST_INVALID;
+      return r;
+    }
+    const uint64_t b = m ? hex_to_bits<F>(m, e2, sticky) : 0;
+    r.bits = b | sign;
+    r.status = m ? status_of<F>(b) : ST_OK;
+    return r;
   }
   const unsigned long long int_start = i;
   while (i < lim && is_digit(f[i])) i++;
@@ -169,6 +238,11 @@ __device__ LongResult parse_long_field(const uint8_t* f, unsigned long long lim,
   }
   const unsigned long long ndig = n_int + n_frac;
   bool ok = ndig > 0;
+  if (grammar == GRAMMAR_JSON) {
+    // an integer part without leading zeros; digits after a point
+    ok = ok && n_int > 0 && !(n_int > 1 && f[int_start] == '0') &&
+         !(frac_start != int_start + n_int && n_frac == 0);
+  }
   long long ex = 0;
   if (ok && i < lim && (f[i] | 0x20) == 'e') {
     i++;
@@ -345,10 +419,17 @@ __device__ __forceinline__ void resolve(const LaunchParams& p, unsigned long lon
   }
   const uint8_t* f = d.base + d.o + off;
   const uint64_t* t = reinterpret_cast<const uint64_t*>(fp_pow5_table_dev);
-  LongResult r = parse_long_field<F>(f, d.len - off, p.delim & 0xFFu, Pow5{t, 2, t + 1}, D, P, B);
+  LongResult r = parse_long_field<F>(f, d.len - off, p.delim & 0xFFu, p.grammar, p.columns != 0,
+                                     Pow5{t, 2, t + 1}, D, P, B);
   if (r.error) atomicCAS(&p.ctl->error, 0u, DERR_INTERNAL);
-  reinterpret_cast<typename F::word*>(p.out_bits)[oi] = (typename F::word)r.bits;
-  p.out_status[oi] = r.status;
+  unsigned long long dest = oi;
+  if (p.columns) {  // column-major layout: oi is the field's index
+    const unsigned long long row = oi / p.columns, col = oi - row * p.columns;
+    dest = col * p.rows_cap + row;
+    if ((bool)r.nl != (col == p.columns - 1)) r.status = ST_BAD_SHAPE;
+  }
+  reinterpret_cast<typename F::word*>(p.out_bits)[dest] = (typename F::word)r.bits;
+  p.out_status[dest] = r.status;
   n_items++;
   n_big += r.bignum;
 }
@@ -378,7 +459,12 @@ __global__ void __launch_bounds__(FB_NT) fallback_kernel(const LaunchParams p) {
     const unsigned long long n = p.ovf[2 * c] & LOC_OFF_MASK;
     const unsigned long long ob = p.ovf[2 * c + 1];
     for (unsigned long long k = lane; k < n; k += 32) {
-      if (p.out_status[ob + k] == ST_PENDING_SCAN) {
+      unsigned long long sk = ob + k;  // the status slot of field ob + k
+      if (p.columns) {
+        const unsigned long long row = sk / p.columns;
+        sk = (sk - row * p.columns) * p.rows_cap + row;
+      }
+      if (p.out_status[sk] == ST_PENDING_SCAN) {
         resolve<F>(p, ob + k, D, P, B, n_items, n_big);
         n_scan++;
       }

@@ -11,6 +11,12 @@ namespace fp {
 cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream,
                          bool f32 = false);
 int parse_smem_bytes(int chunk_bytes);
+// The JSON / column-major modes (mode: MODE_* bits of fp_parse_kernel.cuh,
+// nonzero), for 8 KiB and 16 KiB chunks; the occupancy of the most
+// demanding of those instances.
+cudaError_t launch_parse_ext(const LaunchParams& p, int chunk_bytes, int grid,
+                             cudaStream_t stream, bool f32, int mode);
+cudaError_t parse_occupancy_ext(int chunk_bytes, int* blocks_per_sm);
 cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm, bool f32 = false);
 
 cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32 = false);

@@ -1,0 +1,63 @@
+// fp_parse_kernel_ext.cu -- the parse kernel's JSON and column-major modes
+// (fp_parse_ex), for 8 KiB and 16 KiB chunks; the kernel itself is in
+// fp_parse_kernel.cuh.
+#include "fp_launch.h"
+#include "fp_parse_kernel.cuh"
+
+namespace fp {
+
+template <int C, class F, int MODE>
+static cudaError_t launch_ext_c(const LaunchParams& p, int grid, cudaStream_t stream) {
+  static bool attr_set = false;  // the attribute is per function; set it once
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(parse_kernel<C, F, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Layout<C>::TOTAL);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  parse_kernel<C, F, MODE><<<grid, NT, Layout<C>::TOTAL, stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int C, class F>
+static cudaError_t launch_ext_f(const LaunchParams& p, int grid, cudaStream_t stream, int mode) {
+  switch (mode) {
+    case MODE_JSON: return launch_ext_c<C, F, MODE_JSON>(p, grid, stream);
+    case MODE_COLUMNS: return launch_ext_c<C, F, MODE_COLUMNS>(p, grid, stream);
+    case MODE_JSON | MODE_COLUMNS: return launch_ext_c<C, F, MODE_JSON | MODE_COLUMNS>(p, grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_parse_ext(const LaunchParams& p, int chunk_bytes, int grid,
+                             cudaStream_t stream, bool f32, int mode) {
+  if (chunk_bytes == 8192)
+    return f32 ? launch_ext_f<8192, F32>(p, grid, stream, mode)
+               : launch_ext_f<8192, F64>(p, grid, stream, mode);
+  if (chunk_bytes == 16384)
+    return f32 ? launch_ext_f<16384, F32>(p, grid, stream, mode)
+               : launch_ext_f<16384, F64>(p, grid, stream, mode);
+  return cudaErrorInvalidValue;
+}
+
+template <int C, class F, int MODE>
+static cudaError_t occupancy_ext_c(int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(parse_kernel<C, F, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Layout<C>::TOTAL);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, parse_kernel<C, F, MODE>,
+                                                       NT, Layout<C>::TOTAL);
+}
+
+cudaError_t parse_occupancy_ext(int chunk_bytes, int* blocks_per_sm) {
+  // the most demanding instance (binary32, both modes) bounds all of them
+  if (chunk_bytes == 8192)
+    return occupancy_ext_c<8192, F32, MODE_JSON | MODE_COLUMNS>(blocks_per_sm);
+  if (chunk_bytes == 16384)
+    return occupancy_ext_c<16384, F32, MODE_JSON | MODE_COLUMNS>(blocks_per_sm);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fp

@@ -52,6 +52,10 @@ struct LaunchParams {
   // decides it, indexed like the outputs: out_bits itself for binary64
   // (the 8-byte slot holds it), a side array for binary32
   unsigned long long* loc;
+  unsigned int grammar;     // GRAMMAR_* (fp_device.cuh); read by the slow paths
+  unsigned int columns;     // K >= 2: column-major results (field i -> column i mod K)
+  unsigned long long rows_cap;   // entries per column
+  unsigned long long col_magic;  // ceil(2^64 / K): i div K = mulhi(i, magic) for i < 2^40
 };
 
 // Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).

@@ -150,3 +150,24 @@ def test_columnar_layout_by_hand():
     dest = lambda i: (i % 3) * 3 + i // 3
     assert flagged == sorted([dest(4), dest(5), dest(7)])
     assert out.view(np.float64)[dest(6)] == 8.0
+
+
+def test_paper_grammar_examples():
+    """The grammar examples printed in Section 4 (tests/golden/grammar_examples.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "grammar_examples.txt")
+    n = 0
+    with open(path) as f:
+        for ln in f:
+            if not ln.strip() or ln.startswith("#"):
+                continue
+            text, grammar, expected, _ = ln.rstrip("\n").split("\t")
+            g = JSON if grammar == "json" else oracle.GRAMMAR_DEFAULT
+            got = oracle.parse_field_ex(text, grammar=g)
+            if expected == "INVALID":
+                assert got == (QNAN64, INVALID), text
+            else:
+                assert got == (bits64(float(expected)), OK), text
+                # and JSON rejects none of the plain spellings it allows
+            n += 1
+    assert n == 10
