@@ -19,7 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["fp_parse_kernel.cu", "fp_parse_kernel_ext.cu", "fp_fallback_kernel.cu", "fp_api.cu",
            "fp_noalloc.cu", "fp_server.cu", "fp_copy_kernel.cu"]
-HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "pow5_table.inc",
+HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "fp_internal.h",
+           "fp_parse_kernel.cuh", "fp_copy.h", "fp_arena.h", "pow5_table.inc", "dec_tables.inc",
            os.path.join(INCLUDE, "fpparse.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -43,8 +44,8 @@ def _stale(target: str, deps: list[str]) -> bool:
 
 def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    gen = os.path.join(CSRC, "gen_pow5_table.py")
-    subprocess.run([sys.executable, gen], check=True)
+    for g in ("gen_pow5_table.py", "gen_dec_tables.py"):
+        subprocess.run([sys.executable, os.path.join(CSRC, g)], check=True)
     headers = [os.path.join(CSRC, h) if not os.path.isabs(h) else h for h in HEADERS]
     objs, procs = [], []
     for src in SOURCES:

@@ -12,22 +12,26 @@
 //      point, exponent; its significant digits go to shared memory;
 //   2. Algorithm 1 on the 19-digit prefix w and on w+1 (one lane); equal
 //      results settle the field;
-//   3. otherwise D = the first 800 significant digits, with one extra digit 1
-//      appended when there are more (the last one is nonzero).  Every
-//      midpoint between adjacent floating-point values has at most 768
-//      significant digits (Section 11), so D 10^E and the exact value lie on
+//   3. otherwise V = D 10^E with D the first 800 significant digits and one
+//      extra digit 1 appended when there are more (the last one is nonzero).
+//      Every midpoint between adjacent floating-point values has at most
+//      768 significant digits (Section 11), so V and the exact value lie on
 //      the same side of every midpoint;
 //   4. candidate x = the rounded truncated product of the prefix (within one
-//      unit of the answer); compare D 10^E exactly with the midpoints above
-//      and below x, as integers scaled by powers of two and five, and step x
-//      until it is the nearest value; a tie picks the even one.
-// The big naturals are limb arrays in shared memory with limb i on lane
-// i mod 32: a multiply-add takes one 32-limb round per lane step, and its
+//      unit of the answer); compare V exactly with the midpoints above and
+//      below x and step x until it is the nearest value; a tie picks the
+//      even one.  A midpoint h = (2M+1) 2^(e-1) is written in base 10^9 --
+//      (2M+1) 2^(e-1), or (2M+1) 5^(1-e) 10^(e-1) -- from a table power, a
+//      small power and the factor 2M+1, and compared with V's digits
+//      regrouped into the same base-10^9 chunks.
+// The big naturals are base-10^9 limb arrays in shared memory with limb i on
+// lane i mod 32: a multiply takes one 32-limb round per lane step, and its
 // carries are resolved for all 32 limbs of a round at once by adding the
 // round's generate and propagate ballots as integers.  Hexadecimal floats
 // (exact from their digits) are decided by one lane.
 #include <cuda_runtime.h>
 
+#include "dec_tables.inc"
 #include "fp_device.cuh"
 #include "fp_sync.cuh"
 #include "fp_types.cuh"
@@ -36,17 +40,24 @@ namespace fp {
 
 namespace {
 
+// Powers of five and two in base 10^9 (gen_dec_tables.py).
+__device__ const uint32_t dec5_off[FP_DEC5_COUNT + 1] = {FP_DEC5_OFF_VALUES};
+__device__ const uint32_t dec5_limbs[FP_DEC5_LIMBS] = {FP_DEC5_VALUES};
+__device__ const uint32_t dec2_off[FP_DEC2_COUNT + 1] = {FP_DEC2_OFF_VALUES};
+__device__ const uint32_t dec2_limbs[FP_DEC2_LIMBS] = {FP_DEC2_VALUES};
+constexpr uint32_t DBASE = FP_DEC_BASE;
+
 constexpr int FB_WARPS = 4;           // warps per block
 constexpr int FB_NT = 32 * FB_WARPS;  // threads per block
-constexpr int LIMBS = 96;             // 32-bit limbs per big number: three rounds of 32
+constexpr int LIMBS = 96;             // base-10^9 limbs per big number: three rounds of 32
 constexpr int KMAX = 800;             // significant digits kept before the sticky digit
 constexpr int DIG_CAP = 832;          // digit bytes per warp (KMAX + 1, rounded up)
 constexpr long long EXP_SAT = 1000000000000000ll;  // explicit exponent saturation
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
-// per warp: four big naturals and the digit buffer
+// per warp: three big naturals and the digit buffer
 struct WarpSmem {
-  uint32_t D[LIMBS], P[LIMBS], B[LIMBS], Q[LIMBS];
+  uint32_t P[LIMBS], B[LIMBS], Q[LIMBS];
   uint8_t dig[DIG_CAP];
 };
 
@@ -57,26 +68,6 @@ struct WBig {
   int n;
 };
 
-__device__ __forceinline__ uint32_t limb_at(const WBig& x, long long i) {
-  return (i >= 0 && i < x.n) ? x.p[i] : 0u;
-}
-
-// Carries of one 32-limb round: this lane's partial limb r, whether its own
-// sum overflowed (g), and cin, the carry into the round's first limb.  The
-// carry into limb i is g(i-1) | (r(i-1) all ones & carry into i-1): with
-// A = G | P and G as 32-bit integers, (A + G + cin) ^ A ^ G has bit i set
-// exactly when a carry enters limb i.  Returns the finished limb; cin
-// becomes the carry out of the round.
-__device__ __forceinline__ uint32_t round_carries(uint32_t r, bool g, uint32_t& cin, int lane) {
-  const uint32_t G = __ballot_sync(FULL, g);
-  const uint32_t Pm = __ballot_sync(FULL, r == 0xFFFFFFFFu);
-  const uint32_t A = G | Pm;
-  const unsigned long long sum = (unsigned long long)A + G + cin;
-  const uint32_t into = (uint32_t)sum ^ A ^ G;
-  cin = (uint32_t)(sum >> 32);
-  return r + ((into >> lane) & 1u);
-}
-
 // Set n from limb n0-1 downwards (limbs >= n0 are zero).
 __device__ __forceinline__ void wb_trim(WBig& x, int n0) {
   int n = n0;
@@ -84,118 +75,105 @@ __device__ __forceinline__ void wb_trim(WBig& x, int n0) {
   x.n = n;
 }
 
-// y = x * m + c (y may be x).  False if the result needs more than LIMBS limbs.
-__device__ bool wb_mul_add(WBig& y, const WBig& x, uint32_t m, uint32_t c, int lane) {
+// ---- base 10^9 --------------------------------------------------------------
+// Carries of one round in base 10^9: s is this lane's sum (< 2 * 10^9).
+__device__ __forceinline__ uint32_t dec_round(uint32_t s, uint32_t& cin, int lane) {
+  const bool g = s >= DBASE;
+  if (g) s -= DBASE;
+  const uint32_t G = __ballot_sync(FULL, g);
+  const uint32_t Pm = __ballot_sync(FULL, s == DBASE - 1);
+  const uint32_t A = G | Pm;
+  const unsigned long long sum = (unsigned long long)A + G + cin;
+  const uint32_t into = (uint32_t)sum ^ A ^ G;
+  cin = (uint32_t)(sum >> 32);
+  s += (into >> lane) & 1u;
+  return s == DBASE ? 0u : s;
+}
+
+// y = x * m (m < 10^9), y != x.
+__device__ __noinline__ bool dec_mul(WBig& y, const WBig& x, uint32_t m, int lane) {
   const int n = x.n;
   if (n + 1 > LIMBS) return false;
-  uint32_t hp_round = c, cin = 0;
-  const int rounds = (n + 1 + 31) >> 5;  // limbs 0..n
+  uint32_t qp_round = 0, cin = 0;
+  const int rounds = (n + 1 + 31) >> 5;
   for (int j = 0; j < rounds; j++) {
     const int i = 32 * j + lane;
-    const uint32_t xi = i < n ? x.p[i] : 0u;
-    const unsigned long long prod = (unsigned long long)xi * m;
-    const uint32_t lo = (uint32_t)prod, hi = (uint32_t)(prod >> 32);
-    uint32_t hp = __shfl_up_sync(FULL, hi, 1);
-    if (lane == 0) hp = hp_round;
-    hp_round = __shfl_sync(FULL, hi, 31);
-    const unsigned long long s = (unsigned long long)lo + hp;
-    const uint32_t r = round_carries((uint32_t)s, (s >> 32) != 0, cin, lane);
-    __syncwarp();
-    if (i <= n) y.p[i] = r;
+    const unsigned long long prod = (unsigned long long)(i < n ? x.p[i] : 0u) * m;
+    const uint32_t q = (uint32_t)(prod / DBASE), r = (uint32_t)(prod - (unsigned long long)q * DBASE);
+    uint32_t qp = __shfl_up_sync(FULL, q, 1);
+    if (lane == 0) qp = qp_round;
+    qp_round = __shfl_sync(FULL, q, 31);
+    const uint32_t v = dec_round(r + qp, cin, lane);
+    if (i <= n) y.p[i] = v;
   }
   __syncwarp();
   wb_trim(y, n + 1);
   return true;
 }
 
-// y = y + x.
-__device__ bool wb_add(WBig& y, const WBig& x, int lane) {
-  const int n = y.n > x.n ? y.n : x.n;
+// y = y + x * 10^9 (x shifted one limb up), y != x.
+__device__ __noinline__ bool dec_add_shifted(WBig& y, const WBig& x, int lane) {
+  const int n = y.n > x.n + 1 ? y.n : x.n + 1;
   if (n + 1 > LIMBS) return false;
   uint32_t cin = 0;
   const int rounds = (n + 1 + 31) >> 5;
   for (int j = 0; j < rounds; j++) {
     const int i = 32 * j + lane;
-    const uint32_t yi = i < y.n ? y.p[i] : 0u, xi = i < x.n ? x.p[i] : 0u;
-    const unsigned long long s = (unsigned long long)yi + xi;
-    const uint32_t r = round_carries((uint32_t)s, (s >> 32) != 0, cin, lane);
+    const uint32_t yi = i < y.n ? y.p[i] : 0u;
+    const uint32_t xi = (i >= 1 && i - 1 < x.n) ? x.p[i - 1] : 0u;
+    const uint32_t v = dec_round(yi + xi, cin, lane);
     __syncwarp();
-    if (i <= n) y.p[i] = r;
+    if (i <= n) y.p[i] = v;
   }
   __syncwarp();
   wb_trim(y, n + 1);
   return true;
 }
 
-// y = y * 2^32 (one limb up).
-__device__ bool wb_shift_limb(WBig& y, int lane) {
-  const int n = y.n;
-  if (n == 0) return true;
-  if (n + 1 > LIMBS) return false;
-  uint32_t v[LIMBS / 32];
-#pragma unroll
-  for (int j = 0; j < LIMBS / 32; j++) {
-    const int i = 32 * j + lane;
-    v[j] = i < n ? y.p[i] : 0u;
-  }
+// y = table entry [off[a], off[a+1]).
+__device__ __noinline__ void dec_load(WBig& y, const uint32_t* limbs, const uint32_t* off, int a,
+                                      int lane) {
+  const int o0 = (int)off[a], n = (int)off[a + 1] - o0;
+  for (int i = lane; i < n; i += 32) y.p[i] = limbs[o0 + i];
   __syncwarp();
-#pragma unroll
-  for (int j = 0; j < LIMBS / 32; j++) {
-    const int i = 32 * j + lane;
-    if (i < n) y.p[i + 1] = v[j];
-  }
-  if (lane == 0) y.p[0] = 0;
-  __syncwarp();
-  y.n = n + 1;
-  return true;
+  y.n = n;
 }
 
-__device__ bool wb_mul_pow5(WBig& x, long long k, int lane) {
-  const uint32_t P13 = 1220703125u;  // 5^13
-  while (k >= 13) {
-    if (!wb_mul_add(x, x, P13, 0, lane)) return false;
-    k -= 13;
-  }
-  uint32_t m = 1;
-  while (k-- > 0) m *= 5;
-  return m == 1 || wb_mul_add(x, x, m, 0, lane);
+__device__ __forceinline__ int dec_digits(uint32_t v) {  // decimal digits of 0 < v < 10^9
+  int d = 1;
+  for (uint32_t p = 10; d < 9 && v >= p; p *= 10) d++;
+  return d;
 }
 
-__device__ __forceinline__ long long wb_bitlen(const WBig& x) {
-  if (x.n == 0) return 0;
-  return 32ll * (x.n - 1) + (32 - __clz(x.p[x.n - 1]));
-}
-
-// Sign of X * 2^s - Y, given bitlen(X) + s == bitlen(Y) and s >= 0: the
-// highest limb where they differ decides.
-__device__ int wb_cmp_shifted(const WBig& X, long long s, const WBig& Y, int lane) {
-  const long long ws = s >> 5;
-  const int bs = (int)(s & 31);
-  for (int j = (Y.n - 1) >> 5; j >= 0; j--) {
-    const int i = 32 * j + lane;
-    uint32_t xi = 0, yi = 0;
-    if (i < Y.n) {
-      xi = limb_at(X, i - ws) << bs;
-      if (bs) xi |= limb_at(X, i - ws - 1) >> (32 - bs);
-      yi = Y.p[i];
+// Sign of V - h, V = dig[0 .. nD) * 10^ED (dig[0] != 0), h = H * 10^Eh (H > 0
+// in base 10^9): the leading digits' exponents, then V's digits regrouped
+// into H's base-10^9 chunks (the first chunk as wide as H's top limb).
+__device__ __noinline__ int dec_compare(const uint8_t* dig, long long nD, long long ED, const WBig& H,
+                           long long Eh, int lane) {
+  const int nl = H.n;
+  const int ltop = dec_digits(H.p[nl - 1]);
+  const long long nH = ltop + 9ll * (nl - 1);
+  const long long Lv = nD - 1 + ED, Lh = nH - 1 + Eh;
+  if (Lv != Lh) return Lv < Lh ? -1 : 1;
+  const long long vch = nD > ltop ? 1 + (nD - ltop + 8) / 9 : 1;
+  const long long nch = vch > nl ? vch : nl;
+  for (long long c0 = 0; c0 < nch; c0 += 32) {
+    const long long c = c0 + lane;
+    uint32_t hv = 0, vv = 0;
+    if (c < nch) {
+      hv = c < nl ? H.p[nl - 1 - c] : 0u;
+      const long long start = c == 0 ? 0 : ltop + 9 * (c - 1);
+      const int len = c == 0 ? ltop : 9;
+      for (int k = 0; k < len; k++) vv = vv * 10 + (start + k < nD ? dig[start + k] : 0u);
     }
-    const uint32_t diff = __ballot_sync(FULL, xi != yi);
+    const uint32_t diff = __ballot_sync(FULL, hv != vv);
     if (diff) {
-      const int top = 31 - __clz(diff);
-      const int lt = __shfl_sync(FULL, (int)(xi < yi), top);
+      const int first = __ffs(diff) - 1;
+      const int lt = __shfl_sync(FULL, (int)(vv < hv), first);
       return lt ? -1 : 1;
     }
   }
   return 0;
-}
-
-// Sign of X * 2^sx - Y * 2^sy for nonzero X, Y.
-__device__ int wb_cmp_scaled(const WBig& X, long long sx, const WBig& Y, long long sy, int lane) {
-  const long long lx = wb_bitlen(X) + sx, ly = wb_bitlen(Y) + sy;
-  if (lx != ly) return lx < ly ? -1 : 1;
-  const long long d = sx - sy;
-  if (d >= 0) return wb_cmp_shifted(X, d, Y, lane);
-  return -wb_cmp_shifted(Y, -d, X, lane);
 }
 
 // M, e with value = M 2^e for a finite non-negative bit pattern of F.
@@ -212,6 +190,45 @@ __device__ __forceinline__ void float_parts(uint64_t x, uint64_t& M, int& e) {
 }
 
 __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c == '\n' || c == delim; }
+
+// Sign of V - h into c, V = dig[0 .. nD) 10^ED and h the midpoint between
+// the positive patterns lowbits and lowbits + 1 of F; false on a size error.
+template <class F>
+__device__ __noinline__ bool cmp_midpoint(uint64_t lowbits, WarpSmem& sm, long long nD,
+                                          long long ED, int& c, int lane) {
+  WBig X{sm.P, 0}, A{sm.B, 0}, Y{sm.Q, 0};
+  uint64_t M;
+  int e;
+  float_parts<F>(lowbits, M, e);
+  const uint64_t T = 2 * M + 1;  // < 2^55 < 10^18
+  long long Eh;
+  uint32_t m;  // the small power after the table's
+  if (e >= 1) {  // h = T 2^(e-1)
+    const int k = e - 1;
+    dec_load(X, dec2_limbs, dec2_off, k / FP_DEC2_STEP, lane);
+    m = 1u << (k % FP_DEC2_STEP);
+    Eh = 0;
+  } else {  // h = T 5^(1-e) 10^(e-1)
+    const int j = 1 - e;
+    dec_load(X, dec5_limbs, dec5_off, j / FP_DEC5_STEP, lane);
+    m = 1;
+    for (int b = j % FP_DEC5_STEP; b > 0; b--) m *= 5;
+    Eh = e - 1;
+  }
+  if (m != 1) {
+    if (!dec_mul(Y, X, m, lane)) return false;
+    const WBig t = X;  // swap the roles of X and Y
+    X = Y;
+    Y = t;
+  }
+  const uint32_t t0 = (uint32_t)(T % DBASE), t1 = (uint32_t)(T / DBASE);
+  if (!dec_mul(A, X, t0, lane)) return false;
+  if (t1) {
+    if (!dec_mul(Y, X, t1, lane) || !dec_add_shifted(A, Y, lane)) return false;
+  }
+  c = dec_compare(sm.dig, nD, ED, A, Eh, lane);
+  return true;
+}
 
 struct LongResult {
   uint64_t bits;
@@ -289,11 +306,12 @@ __device__ LongResult hex_field(const uint8_t* f, unsigned long long i, unsigned
 // One field starting at f (lim >= 1 bytes remain in the buffer), by the
 // whole warp.  *nl: the field ends at '\n' or at the end of the text.
 template <class F>
-__device__ LongResult warp_field(const uint8_t* f, unsigned long long lim, uint32_t delim,
+__device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint32_t delim,
                                  uint32_t grammar, WarpSmem& sm, bool* nl, int lane) {
   LongResult r;
   r.bignum = 0;
   r.error = 0;
+  const uint8_t* f = fg;
   const uint32_t lt_mask = (1u << lane) - 1;
   auto invalid = [&]() {
     r.bits = F::QNAN;
@@ -466,72 +484,23 @@ __device__ LongResult warp_field(const uint8_t* f, unsigned long long lim, uint3
     r.status = status_of<F>(abits);
     return r;
   }
-  // ---- exact big-number comparison --------------------------------------------
+  // ---- exact comparison with midpoints, in decimal --------------------------
   r.bignum = 1;
-  const long long nK = nsig < KMAX ? nsig : KMAX;
-  long long ED = E + (nsig - nK);
-  WBig D{sm.D, 0}, P{sm.P, 0}, B{sm.B, 0}, Q{sm.Q, 0};
   {
-    // D from the digits, nine at a time: the chunks' values in parallel
-    // (into Q), then one multiply-add per chunk
-    const int nch = (int)((nK + 8) / 9);
-    for (int c = lane; c < nch; c += 32) {
-      uint32_t v = 0;
-      const int k1 = 9 * c + 9 < nK ? 9 * c + 9 : (int)nK;
-      for (int k = 9 * c; k < k1; k++) v = v * 10 + sm.dig[k];
-      Q.p[c] = v;
-    }
-    __syncwarp();
-    for (int c = 0; c < nch; c++) {
-      const int len = 9 * c + 9 < nK ? 9 : (int)(nK - 9 * c);
-      uint32_t p10 = 1;
-      for (int k = 0; k < len; k++) p10 *= 10;
-      if (!wb_mul_add(D, D, p10, Q.p[c], lane)) goto fail;
-    }
+    long long nD = nsig < KMAX ? nsig : KMAX;
+    long long ED = E + (nsig - nD);
     if (nsig > KMAX) {  // the sticky digit
-      if (!wb_mul_add(D, D, 10, 1, lane)) goto fail;
-      ED -= 1;
-    }
-  }
-  {
-    // V = D * 10^ED.  With ED >= 0 compare D 5^ED 2^ED against midpoints;
-    // with ED < 0 compare D 2^ED against (2M+1) 5^-ED 2^(e-1).
-    if (ED >= 0) {
-      if (!wb_mul_pow5(D, ED, lane)) goto fail;
-    } else {
-      if (lane == 0) P.p[0] = 1;
+      if (lane == 0) sm.dig[nD] = 1;
       __syncwarp();
-      P.n = 1;
-      if (!wb_mul_pow5(P, -ED, lane)) goto fail;
+      nD += 1;
+      ED -= 1;
     }
     // the candidate
     uint64_t x = 0;
     if (lane == 0) x = convert_wq<F>(w, q19, tab, false).bits;
     x = __shfl_sync(FULL, x, 0);
-    // sign of V - midpoint(lowbits, lowbits + 1); false on a size error
     auto cmp_mid = [&](uint64_t lowbits, int& c) -> bool {
-      uint64_t M;
-      int e;
-      float_parts<F>(lowbits, M, e);
-      const uint64_t T = 2 * M + 1;  // < 2^55
-      if (ED >= 0) {
-        if (lane == 0) {
-          B.p[0] = (uint32_t)T;
-          B.p[1] = (uint32_t)(T >> 32);
-        }
-        __syncwarp();
-        B.n = (T >> 32) ? 2 : 1;
-      } else {
-        const uint32_t th = (uint32_t)(T >> 32), tl = (uint32_t)T;
-        if (th) {
-          if (!wb_mul_add(B, P, th, 0, lane) || !wb_shift_limb(B, lane)) return false;
-          if (!wb_mul_add(Q, P, tl, 0, lane) || !wb_add(B, Q, lane)) return false;
-        } else {
-          if (!wb_mul_add(B, P, tl, 0, lane)) return false;
-        }
-      }
-      c = wb_cmp_scaled(D, ED, B, (long long)e - 1, lane);
-      return true;
+      return cmp_midpoint<F>(lowbits, sm, nD, ED, c, lane);
     };
     for (int iter = 0; iter < 8; iter++) {
       int c;
