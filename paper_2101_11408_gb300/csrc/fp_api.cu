@@ -98,6 +98,14 @@ struct Scratch {
   // binary32 calls: pending fields' locations, indexed like the outputs
   unsigned long long* loc = nullptr;
   unsigned long long cap_loc = 0;
+  // the pipelined host parse: copy-in and copy-out streams, per-segment
+  // events, segment counts
+  static constexpr int PIPE_SEGS = 64;
+  cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
+  cudaEvent_t pipe_ev_in[PIPE_SEGS] = {}, pipe_ev_parsed[PIPE_SEGS] = {};
+  cudaEvent_t pipe_ev_start = nullptr, pipe_ev_done = nullptr;
+  unsigned long long* pipe_dev = nullptr;   // segment counts (device)
+  unsigned long long* pipe_host = nullptr;  // segment counts (pinned)
 };
 bool g_timing = false;
 
@@ -178,6 +186,22 @@ void free_scratch(Scratch* s) {
   cudaFree(s->stage_status);
   cudaFree(s->stage_count);
   cudaFree(s->loc);
+  if (s->pipe_in) {
+    cudaStreamSynchronize(s->pipe_in);
+    cudaStreamDestroy(s->pipe_in);
+  }
+  if (s->pipe_out) {
+    cudaStreamSynchronize(s->pipe_out);
+    cudaStreamDestroy(s->pipe_out);
+  }
+  for (int i = 0; i < Scratch::PIPE_SEGS; i++) {
+    if (s->pipe_ev_in[i]) cudaEventDestroy(s->pipe_ev_in[i]);
+    if (s->pipe_ev_parsed[i]) cudaEventDestroy(s->pipe_ev_parsed[i]);
+  }
+  if (s->pipe_ev_start) cudaEventDestroy(s->pipe_ev_start);
+  if (s->pipe_ev_done) cudaEventDestroy(s->pipe_ev_done);
+  cudaFree(s->pipe_dev);
+  cudaFreeHost(s->pipe_host);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
 }
@@ -418,6 +442,167 @@ fp_err_t stream_error_word(cudaStream_t stream, unsigned int** word) {
 }  // namespace fp
 
 namespace {
+// ---------------------------------------------------------------------------
+// host-buffer parse
+// ---------------------------------------------------------------------------
+constexpr size_t PIPE_MIN_BYTES = 32u << 20;  // smaller texts take the simple path
+constexpr size_t PIPE_SEG_BYTES = 16u << 20;  // segment size of the pipelined path (each parse
+                                              // launch has a fixed cost of about 25 us)
+
+// The address the device uses for host memory p, or null when p is not
+// pinned (page-locked) memory.
+const void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+  return a.devicePointer;
+}
+void* device_view(void* p) { return const_cast<void*>(device_view(static_cast<const void*>(p))); }
+
+// Staging of (stream) for texts of len bytes.  Call with g_mu held.
+fp_err_t stage_for(cudaStream_t stream, size_t len, Scratch** out) {
+  Scratch* s = nullptr;
+  fp_err_t e = get_scratch(stream, 1, 1, g_cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  if (!s->stage_count) FP_CUDA(cudaMalloc(&s->stage_count, sizeof(unsigned long long)));
+  if (len > s->stage_cap) {
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->stage_text);
+    cudaFree(s->stage_out);
+    cudaFree(s->stage_status);
+    s->stage_text = nullptr;
+    s->stage_out = nullptr;
+    s->stage_status = nullptr;
+    s->stage_cap = 0;
+    FP_CUDA(cudaMalloc(&s->stage_text, len));
+    FP_CUDA(cudaMalloc(&s->stage_out, len * sizeof(double)));
+    FP_CUDA(cudaMalloc(&s->stage_status, len));
+    s->stage_cap = len;
+  }
+  *out = s;
+  return FP_OK;
+}
+
+// One copy in, one parse, the count, then exactly that many results back.
+fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host_f64,
+                     uint8_t* host_status, uint64_t* host_count, cudaStream_t stream) {
+  Scratch* s = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    fp_err_t e = stage_for(stream, len, &s);
+    if (e != FP_OK) return e;
+  }
+  if (len) FP_CUDA(cudaMemcpyAsync(s->stage_text, host_text, len, cudaMemcpyHostToDevice, stream));
+  fp_err_t e = fp_parse_f64(len ? (const char*)s->stage_text : nullptr, len, delim, s->stage_out,
+                            s->stage_status, (uint64_t*)s->stage_count,
+                            reinterpret_cast<struct CUstream_st*>(stream));
+  if (e != FP_OK) return e;
+  unsigned long long n = 0;
+  FP_CUDA(cudaMemcpyAsync(&n, s->stage_count, sizeof(n), cudaMemcpyDeviceToHost, stream));
+  FP_CUDA(cudaStreamSynchronize(stream));
+  if (n > len) return FP_ERR_INTERNAL;
+  if (n) {
+    FP_CUDA(cudaMemcpyAsync(host_f64, s->stage_out, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream));
+    FP_CUDA(cudaMemcpyAsync(host_status, s->stage_status, n, cudaMemcpyDeviceToHost, stream));
+  }
+  FP_CUDA(cudaStreamSynchronize(stream));
+  *host_count = n;
+  return FP_OK;
+}
+
+// Pinned host memory: the text is cut at separators into segments of about
+// PIPE_SEG_BYTES (each ends with its separator, so its fields are exactly
+// the buffer's fields in that range).  All segments are copied in on
+// pipe_in, back to back; segment i is parsed on the caller's stream once it
+// has landed, and its field count comes back on pipe_out; this thread waits
+// for each count in turn and queues the copies of exactly that many results
+// (copy engine, pipe_out) at the running total.  Copies in, parses and
+// copies out of different segments overlap, and the SMs only parse.
+fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* host_f64,
+                        uint8_t* host_status, uint64_t* host_count, cudaStream_t stream) {
+  // segment starts: after a separator near each multiple of the segment size
+  size_t cuts[Scratch::PIPE_SEGS + 1];
+  int K = 0;
+  cuts[K++] = 0;
+  const size_t want = (len + PIPE_SEG_BYTES - 1) / PIPE_SEG_BYTES;
+  const size_t nseg = want < (size_t)Scratch::PIPE_SEGS ? want : (size_t)Scratch::PIPE_SEGS;
+  const unsigned char d = (unsigned char)delim;
+  for (size_t i = 1; i < nseg; i++) {
+    size_t c = i * (len / nseg);
+    if (c <= cuts[K - 1]) continue;
+    const size_t stop = c + (1u << 20) < len ? c + (1u << 20) : len;
+    while (c < stop && host_text[c - 1] != '\n' && (unsigned char)host_text[c - 1] != d) c++;
+    if (c < stop && c < len) cuts[K++] = c;  // else: no separator near, no cut here
+  }
+  cuts[K] = len;
+  Scratch* s = nullptr;
+  Config cfg;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    cfg = g_cfg;
+    fp_err_t e = stage_for(stream, len, &s);
+    if (e != FP_OK) return e;
+    size_t maxseg = 0;
+    for (int i = 0; i < K; i++) maxseg = std::max(maxseg, cuts[i + 1] - cuts[i]);
+    e = get_scratch(stream, chunks_of(15, maxseg, cfg.chunk_bytes), 1, cfg.fallback_queue, &s);
+    if (e != FP_OK) return e;
+    if (!s->pipe_in) {
+      FP_CUDA(cudaStreamCreateWithFlags(&s->pipe_in, cudaStreamNonBlocking));
+      FP_CUDA(cudaStreamCreateWithFlags(&s->pipe_out, cudaStreamNonBlocking));
+      for (int i = 0; i < Scratch::PIPE_SEGS; i++) {
+        FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_in[i], cudaEventDisableTiming));
+        FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_parsed[i], cudaEventDisableTiming));
+      }
+      FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_start, cudaEventDisableTiming));
+      FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_done, cudaEventDisableTiming));
+      FP_CUDA(cudaMalloc(&s->pipe_dev, Scratch::PIPE_SEGS * sizeof(unsigned long long)));
+      FP_CUDA(cudaMallocHost(&s->pipe_host, Scratch::PIPE_SEGS * sizeof(unsigned long long)));
+    }
+  }
+  unsigned long long* counts = s->pipe_dev;
+  volatile unsigned long long* hcounts = s->pipe_host;
+  // everything queued before on the caller's stream comes first
+  FP_CUDA(cudaEventRecord(s->pipe_ev_start, stream));
+  FP_CUDA(cudaStreamWaitEvent(s->pipe_in, s->pipe_ev_start, 0));
+  FP_CUDA(cudaStreamWaitEvent(s->pipe_out, s->pipe_ev_start, 0));
+  for (int i = 0; i < K; i++) {  // all copies in, back to back
+    FP_CUDA(cudaMemcpyAsync(s->stage_text + cuts[i], host_text + cuts[i], cuts[i + 1] - cuts[i],
+                            cudaMemcpyHostToDevice, s->pipe_in));
+    FP_CUDA(cudaEventRecord(s->pipe_ev_in[i], s->pipe_in));
+  }
+  for (int i = 0; i < K; i++) {  // the parses, each once its bytes have landed
+    const size_t c = cuts[i];
+    FP_CUDA(cudaStreamWaitEvent(stream, s->pipe_ev_in[i], 0));
+    fp_err_t e = fp_parse_f64((const char*)s->stage_text + c, cuts[i + 1] - c, delim,
+                              s->stage_out + c, s->stage_status + c, (uint64_t*)(counts + i),
+                              reinterpret_cast<struct CUstream_st*>(stream));
+    if (e != FP_OK) return e;
+    FP_CUDA(cudaMemcpyAsync((void*)(hcounts + i), counts + i, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, stream));
+    FP_CUDA(cudaEventRecord(s->pipe_ev_parsed[i], stream));
+  }
+  unsigned long long total = 0;
+  for (int i = 0; i < K; i++) {  // results out, segment by segment
+    FP_CUDA(cudaEventSynchronize(s->pipe_ev_parsed[i]));
+    const unsigned long long n = hcounts[i];
+    if (n > cuts[i + 1] - cuts[i]) return FP_ERR_INTERNAL;
+    if (n) {
+      FP_CUDA(cudaMemcpyAsync(host_f64 + total, s->stage_out + cuts[i], n * sizeof(double),
+                              cudaMemcpyDeviceToHost, s->pipe_out));
+      FP_CUDA(cudaMemcpyAsync(host_status + total, s->stage_status + cuts[i], n,
+                              cudaMemcpyDeviceToHost, s->pipe_out));
+    }
+    total += n;
+  }
+  FP_CUDA(cudaStreamSynchronize(s->pipe_out));
+  *host_count = total;
+  return FP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -670,43 +855,14 @@ fp_err_t fp_parse_f64_host(const char* host_text, size_t len, char delim, double
   if (len >= MAX_LEN || !host_count) return FP_ERR_ARG;
   if (len > 0 && (!host_text || !host_f64 || !host_status)) return FP_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  Scratch* s = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    fp_err_t e = get_scratch(stream, 1, 1, g_cfg.fallback_queue, &s);
-    if (e != FP_OK) return e;
-    if (!s->stage_count) FP_CUDA(cudaMalloc(&s->stage_count, sizeof(unsigned long long)));
-    if (len > s->stage_cap) {
-      FP_CUDA(cudaStreamSynchronize(stream));
-      cudaFree(s->stage_text);
-      cudaFree(s->stage_out);
-      cudaFree(s->stage_status);
-      s->stage_text = nullptr;
-      s->stage_out = nullptr;
-      s->stage_status = nullptr;
-      s->stage_cap = 0;
-      FP_CUDA(cudaMalloc(&s->stage_text, len));
-      FP_CUDA(cudaMalloc(&s->stage_out, len * sizeof(double)));
-      FP_CUDA(cudaMalloc(&s->stage_status, len));
-      s->stage_cap = len;
-    }
+  if (len >= PIPE_MIN_BYTES) {
+    const void* dv_text = device_view(host_text);
+    void* dv_f64 = device_view(host_f64);
+    void* dv_st = device_view(host_status);
+    if (dv_text && dv_f64 && dv_st)
+      return host_pipelined(host_text, len, delim, host_f64, host_status, host_count, stream);
   }
-  if (len) FP_CUDA(cudaMemcpyAsync(s->stage_text, host_text, len, cudaMemcpyHostToDevice, stream));
-  fp_err_t e = fp_parse_f64(len ? (const char*)s->stage_text : nullptr, len, delim, s->stage_out,
-                            s->stage_status, (uint64_t*)s->stage_count, stream_);
-  if (e != FP_OK) return e;
-  unsigned long long n = 0;
-  FP_CUDA(cudaMemcpyAsync(&n, s->stage_count, sizeof(n), cudaMemcpyDeviceToHost, stream));
-  FP_CUDA(cudaStreamSynchronize(stream));
-  if (n > len) return FP_ERR_INTERNAL;
-  if (n) {
-    FP_CUDA(cudaMemcpyAsync(host_f64, s->stage_out, n * sizeof(double), cudaMemcpyDeviceToHost,
-                            stream));
-    FP_CUDA(cudaMemcpyAsync(host_status, s->stage_status, n, cudaMemcpyDeviceToHost, stream));
-  }
-  FP_CUDA(cudaStreamSynchronize(stream));
-  *host_count = n;
-  return FP_OK;
+  return host_simple(host_text, len, delim, host_f64, host_status, host_count, stream);
 }
 
 fp_err_t fp_shutdown(void) {

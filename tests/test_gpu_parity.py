@@ -341,3 +341,31 @@ def test_autotune_picks_a_valid_config(tmp_path):
         assert_parity(workloads.bulk_mixed_text(50000, 82))
     finally:
         fp.set_config(**before)
+
+
+@pytest.mark.parametrize("delim", [b"\n", b","])
+def test_host_entry_point_pipelined(delim):
+    """Texts of 32 MB and more in pinned memory take the pipelined path
+    (segments cut at separators, results written to the host arrays on the
+    device); they must equal the oracle, and pageable copies of the same
+    arrays (the one-copy path)."""
+    parts = [workloads.bulk_mixed_text(1_500_000, 91), workloads.hard_case_text(20_000, 92),
+             b"7" * (3 << 20),  # a field of 3 MB: no separator near some cuts
+             workloads.bulk_mixed_text(800_000, 93)]
+    text = b"\n".join(parts)
+    if delim == b",":
+        text = text.replace(b"\n", b",", 200_000)
+    n = len(text)
+    rb, rs = oracle.parse_buffer(text, delim)
+    for pinned in (True, False):
+        h_text = torch.frombuffer(bytearray(text), dtype=torch.uint8)
+        h_out = torch.full((n,), -1.0, dtype=torch.float64)
+        h_st = torch.full((n,), 0xEE, dtype=torch.uint8)
+        if pinned:
+            h_text, h_out, h_st = h_text.pin_memory(), h_out.pin_memory(), h_st.pin_memory()
+        k = fp.parse_f64_host_into(h_text, h_out, h_st, delim)
+        assert k == rb.size
+        assert np.array_equal(h_out[:k].numpy().view(np.uint64), rb)
+        assert np.array_equal(h_st[:k].numpy(), rs)
+        assert (h_st[k:k + 1000].numpy() == 0xEE).all()  # nothing written past the count
+    assert fp.get_error() == 0
