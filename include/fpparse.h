@@ -387,9 +387,12 @@ FP_API fp_err_t fp_timing_read(struct CUstream_st *stream, double *parse_ms,
  *   host_status  host array of at least fp_max_fields(len) bytes
  *   host_count   host pointer: the number of fields
  * Copies the text to a per-stream device staging buffer, parses it there,
- * reads the field count and copies back exactly that many results.
- * Synchronous: returns after the results are in host memory.  The staging
- * buffers are allocated with cudaMalloc on first use and grown as needed.
+ * reads the field count and copies back exactly that many results.  When
+ * all three host arrays are pinned and len >= 32 MB, the text is cut at
+ * separators into segments of about 16 MB whose copies in, parses and
+ * copies out overlap (results identical).  Synchronous: returns after the
+ * results are in host memory.  The staging buffers are allocated with
+ * cudaMalloc on first use and grown as needed.
  */
 FP_API fp_err_t fp_parse_f64_host(const char *host_text, size_t len, char delim,
                                   double *host_f64, uint8_t *host_status, uint64_t *host_count,
