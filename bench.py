@@ -677,7 +677,8 @@ def run_serve(args, world, rank, dist) -> None:
         rank, R, lens.sum() / 1e6, mean_bytes / 1e6, lens.max() / 1e6, time.perf_counter() - t))
 
     srv = fp.Server(device_budget=args.serve_budget, max_batch=args.serve_batch,
-                    max_inflight=args.serve_inflight, delim=b",")
+                    max_inflight=args.serve_inflight, delim=b",",
+                    launch_bytes=args.serve_launch_mb << 20)
     stream = torch.cuda.current_stream()
     cnt = ctypes.c_uint64()
 
@@ -797,6 +798,7 @@ def run_serve(args, world, rank, dist) -> None:
         "config": {"workload": SERVE_WORKLOAD, "bodies": R, "mean_request_bytes": mean_bytes,
                    "max_request_bytes": int(lens.max()), "device_budget": args.serve_budget,
                    "max_batch": args.serve_batch, "max_inflight": args.serve_inflight,
+                   "launch_mb": args.serve_launch_mb or 32,
                    "checked_fields": checked,
                    "l2": "requests stream from host memory; no L2 reuse between requests",
                    "parallelism": "replicas: one independent server per GPU"},
@@ -840,7 +842,8 @@ def main() -> None:
     ap.add_argument("--serve-max-requests", type=int, default=60000)
     ap.add_argument("--serve-budget", type=int, default=40_000_000_000)
     ap.add_argument("--serve-batch", type=int, default=1024)
-    ap.add_argument("--serve-inflight", type=int, default=3)
+    ap.add_argument("--serve-inflight", type=int, default=4)
+    ap.add_argument("--serve-launch-mb", type=int, default=0, help="serve: MB per launch (0: 32)")
     ap.add_argument("--format", choices=["f64", "f32"], default="f64",
                     help="bulk/uniform/hard: binary64 (fp_parse_f64) or binary32 (fp_parse_f32)")
     ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")

@@ -255,15 +255,17 @@ FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
  * `len` bytes holds len + 16 units, rounded up to 256, from admission to
  * completion.  Requests are admitted first-come first-served as arena space
  * frees up (a request that does not fit waits, and so do those behind it).
- * Whenever one of `max_inflight` launch slots is free, every admitted
- * request not yet launched (at most `max_batch`) goes into one launch
+ * Whenever one of `max_inflight` launch slots is free, the admitted
+ * requests not yet launched, in order, up to `launch_bytes` of text (at
+ * least one, at most `max_batch`) go into one launch
  * sequence on that slot's stream: a gather kernel copies the texts from
  * host memory into the arena, the persistent batched parse and its
  * fallback run, and a scatter kernel writes each request's first
  * min(fields, out_cap) values and statuses straight into the caller's
  * host arrays; then the request's units are released.  The kernels reach
- * host memory directly when it is pinned (page-locked); texts and arrays in
- * pageable memory are moved by copy calls instead (slower).  Different
+ * host memory directly when it is pinned (page-locked); requests of 1 MB
+ * or more, and texts and arrays in pageable memory, are moved by copy
+ * calls instead (results after their counts are back).  Different
  * slots' sequences overlap on the device.  Results equal those of
  * fp_parse_f64 on the same text, alone or in any mix.
  * Besides the arena, each slot's stream holds the parse scratch of up to
@@ -276,6 +278,8 @@ FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
  *   max_batch      most requests in one launch, 1..65536
  *   max_inflight   launches in flight at once, 1..8
  *   delim          field separator besides '\n'
+ *   launch_bytes   text bytes one launch takes at most (at least one
+ *                  request); 0 means 32 MB
  * fp_server_submit -- queue one request and return at once.
  *   host_text    len bytes of host memory (pinned copies fastest)
  *   host_f64     host array of out_cap doubles
@@ -300,6 +304,7 @@ typedef struct {
   uint32_t max_batch;
   uint32_t max_inflight;
   char delim;
+  uint64_t launch_bytes; /* text bytes per launch at most (0: 32 MB) */
 } fp_server_config_t;
 typedef struct {
   uint64_t count;      /* fields in the text (min(count, out_cap) written) */

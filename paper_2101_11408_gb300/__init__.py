@@ -288,8 +288,9 @@ class Server:
     references to the tensors until they are waited for."""
 
     def __init__(self, device_budget: int = 40_000_000_000, max_batch: int = 1024,
-                 max_inflight: int = 3, delim=b"\n"):
-        cfg = _lib.ServerConfig(device_budget, max_batch, max_inflight, _delim_byte(delim))
+                 max_inflight: int = 4, delim=b"\n", launch_bytes: int = 0):
+        cfg = _lib.ServerConfig(device_budget, max_batch, max_inflight, _delim_byte(delim),
+                                launch_bytes)
         self._h = ctypes.c_void_p()
         _lib.check(_lib.load().fp_server_create(ctypes.byref(cfg), ctypes.byref(self._h)),
                    "fp_server_create")

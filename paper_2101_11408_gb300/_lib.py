@@ -42,7 +42,8 @@ class Config(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("device_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
-                ("max_inflight", ctypes.c_uint32), ("delim", ctypes.c_char)]
+                ("max_inflight", ctypes.c_uint32), ("delim", ctypes.c_char),
+                ("launch_bytes", ctypes.c_uint64)]
 
 
 class RequestInfo(ctypes.Structure):

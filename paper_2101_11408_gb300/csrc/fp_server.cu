@@ -8,12 +8,15 @@
 //   take    new submissions move to the pending queue (FIFO);
 //   admit   pending requests get arena units in arrival order while they
 //           fit;
-//   launch  each free slot takes every admitted request not yet launched
-//           (at most max_batch) and queues on its own stream: one gather
-//           kernel (texts, pinned host -> arena), the persistent batched
-//           parse and its fallback, one scatter kernel (each request's
-//           first min(count, cap) results, arena -> the caller's pinned
-//           arrays) and the copy of the counts.
+//   launch  each free slot takes the admitted requests not yet launched, in
+//           order, up to launch_bytes of text (at least one request, at most
+//           max_batch) and queues on its own stream: the texts in
+//           (one gather kernel for the small requests, a copy call for each
+//           request of 1 MB or more), the persistent batched parse and its
+//           fallback, one scatter kernel for the small requests' results
+//           (first min(count, cap), arena -> the caller's pinned arrays) and
+//           the copy of the counts; large requests' results follow by copy
+//           calls of exactly their counts once those are back.
 // The slots' streams overlap on the device: one batch's texts come in
 // while another is parsed and a third one's results go out.
 #include <cuda_runtime.h>
@@ -37,6 +40,14 @@
 namespace {
 
 constexpr uint64_t UNIT_ROUND = 256;       // units of a request are rounded up to this
+// Requests of at least this many bytes move by copy engines (one copy call
+// each way costs little next to their bytes, and copy engines leave the SMs
+// to the parse); smaller ones by the gather / scatter kernels.
+constexpr uint64_t ENGINE_BYTES = 1u << 20;
+// By default a launch takes admitted requests up to this many text bytes (at
+// least one request), so that under load consecutive launches on different
+// slots overlap their copies in, parses and copies out.
+constexpr uint64_t LAUNCH_BYTES = 32u << 20;
 constexpr uint64_t MIN_BUDGET = 4096;
 constexpr uint32_t MAX_SLOTS = 8;
 constexpr uint32_t MAX_BATCH = 65536;
@@ -222,7 +233,11 @@ bool retire(fp_server* S, Slot& sl) {
 
 // Launch step for one free slot.
 void launch(fp_server* S, Slot& sl) {
-  const size_t k = std::min<size_t>(S->admitted.size(), S->cfg.max_batch);
+  const size_t kmax = std::min<size_t>(S->admitted.size(), S->cfg.max_batch);
+  size_t k = 1;
+  uint64_t bytes = S->admitted[0]->len;
+  const uint64_t cap = S->cfg.launch_bytes ? S->cfg.launch_bytes : LAUNCH_BYTES;
+  while (k < kmax && bytes + S->admitted[k]->len <= cap) bytes += S->admitted[k++]->len;
   sl.reqs.assign(S->admitted.begin(), S->admitted.begin() + k);
   S->admitted.erase(S->admitted.begin(), S->admitted.begin() + k);
   sl.texts.resize(k);
@@ -240,7 +255,8 @@ void launch(fp_server* S, Slot& sl) {
     sl.base[i] = r->off;
     sl.cap[i] = r->len;  // fp_max_fields(len)
     // text in: by the gather kernel, else by a copy call
-    if (r->len && r->dv_text) {
+    const bool engine = r->len >= ENGINE_BYTES;
+    if (r->len && r->dv_text && !engine) {
       for (uint64_t p = 0; p < r->len; p += fp::GATHER_PIECE) {
         if (ng >= sl.cap_gpieces) {
           e = FP_ERR_INTERNAL;
@@ -255,7 +271,7 @@ void launch(fp_server* S, Slot& sl) {
     }
     // results out: by the scatter kernel, else by copy calls after the counts
     const uint64_t cap = std::min<uint64_t>(r->out_cap, r->len);
-    if (r->dv_f64 && r->dv_status) {
+    if (r->dv_f64 && r->dv_status && !engine) {
       sl.sitems[i] = fp::ScatterItem{reinterpret_cast<const unsigned long long*>(S->d_f64) + r->off,
                                      S->d_status + r->off, r->dv_f64, r->dv_status,
                                      reinterpret_cast<const unsigned long long*>(sl.d_counts) + i,
