@@ -12,14 +12,15 @@
 //               SWAR zero-byte tests; a block scan ranks the field starts,
 //               whose positions are scattered in order; the chunk's field
 //               count is published at once for the decoupled look-back;
-//   3. parse  : one thread per field: the SWAR tokenizer for the common
-//               shape (eight digits per step), else the general tokenizer of
-//               Section 4; quick exits and Algorithm 1 against the table
-//               held in shared memory; the w / w+1 check of Section 11;
-//               results are staged in shared memory;
-//   4. prefix : look back over the preceding chunks for this chunk's first
-//               field index (after parsing, when the predecessors have mostly
-//               finished);
+//   3. parse  : one thread per field, warps taking groups of 32 fields from a
+//               shared counter: the straight-line tokenizer for the common
+//               shape, else the general tokenizer of Section 4; quick exits
+//               and Algorithm 1 against the table held in shared memory; the
+//               w / w+1 check of Section 11; results are staged in shared
+//               memory;
+//   4. prefix : one warp looks back over the preceding chunks for this
+//               chunk's first field index while the others parse, then joins
+//               them;
 //   5. store  : coalesced stores of the doubles and status bytes; fields that
 //               cannot be settled here are queued for the fallback kernel.
 #pragma once
@@ -66,6 +67,7 @@ struct Layout {
   static_assert(C % (16 * NT) == 0, "whole granules per thread");
   static_assert(TILE < 65536, "u16 positions");
   static_assert(S_CAP == STAGE, "one window of fields is staged at a time");
+  static_assert(S_CAP <= 32 * 32, "a window's groups of 32 fields fit a 32-bit mask");
 };
 
 // Miscellaneous shared state of a block.
@@ -79,6 +81,7 @@ struct Misc {
   unsigned long long lb_part[NT / 32];
   int last_start[NSTAGE];  // tile offset of the last field start of each staged chunk
   unsigned long long cnt[CNT_NUM];
+  unsigned int group;  // next group of 32 fields of the window to parse
 };
 static_assert(sizeof(Misc) <= 1024, "misc");
 
@@ -223,7 +226,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   const Pow5 pow5{table, 1, reinterpret_cast<const uint64_t*>(fp_pow5_table_dev) + 1};
   __syncthreads();
 
-  // path counters of the current chunk (flushed to shared memory per chunk)
+  // path counters of this thread's fields (added up once, at the end)
   uint32_t c_el = 0, c_two = 0, c_long = 0, c_long_ok = 0, c_slow = 0;
   auto flush_counters = [&]() {
     uint32_t v[5] = {c_el, c_two, c_long, c_long_ok, c_slow};
@@ -509,6 +512,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
           m &= m - 1;
         }
       }
+      if (tid == 0) ms->group = 0;
       if (hi == n && n > lo && warp == 0) {
         // the last field ends at the first separator after its start, at the
         // end of the text, or (if neither is staged) it is long
@@ -538,15 +542,33 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
           if (lc + 1 == (long long)d.nchunks && d.out_count) *d.out_count = b + n;
         }
       }
-      // each warp takes a contiguous, equal share of this window's fields
+      // Warps take groups of 32 fields until none is left, so that the warp
+      // that ran the look-back, or one that met general fields, does less.
+      // The general tokenizer then runs on the fields of the warp's own
+      // groups that need it, in a second pass (the hot loop stays free of
+      // its rare branches).
       const uint32_t cntw = hi - lo;
+      const uint32_t ngroups = (cntw + 31) / 32;  // at most S_CAP / 32 = 32
+      uint32_t mine = 0;                          // the groups this warp took
+      for (;;) {
+        uint32_t gi = 0;
+        if (lane == 0) gi = atomicAdd(&ms->group, 1u);
+        gi = __shfl_sync(0xFFFFFFFFu, gi, 0);
+        if (gi >= ngroups) break;
+        mine |= 1u << gi;
+        const uint32_t k = 32 * gi + lane;
+        if (k < cntw) parse_hot(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
+      }
+      while (mine) {
+        const uint32_t k = 32 * (__ffs(mine) - 1) + lane;
+        mine &= mine - 1;
+        if (k < cntw && stage_st[k] == ST_GENERAL)
+          parse_general(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
+      }
+      // stores: each warp a contiguous, equal share of the window
       const uint32_t share = (cntw + NT / 32 - 1) / (NT / 32);
       const uint32_t k_end = min(warp * share + share, cntw);
-      for (uint32_t k = warp * share + lane; k < k_end; k += 32)
-        parse_hot(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
-      for (uint32_t k = warp * share + lane; k < k_end; k += 32)
-        if (stage_st[k] == ST_GENERAL) parse_general(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
-      __syncthreads();  // the prefix is in shared memory
+      __syncthreads();  // the prefix and the results are in shared memory
       if (lo == 0) {
         base = ms->lb_part[0];
         cap = d.out_cap > base ? d.out_cap - base : 0;
@@ -559,7 +581,6 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       __syncthreads();  // S and the staged results are rewritten for the next window
     }
     if (tid == 0) ms->cnt[CNT_FIELDS] += n;
-    flush_counters();
     __syncthreads();
     if (tid == 0 && ms->overflowed) {
       // The fallback kernel will scan this chunk's outputs for pending fields.
