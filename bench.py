@@ -18,6 +18,7 @@ scaling, no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -643,6 +644,9 @@ def _percentile_ms(lat_ns, q):
     return float(np.percentile(np.asarray(lat_ns, dtype=np.float64), q)) / 1e6
 
 
+SERVE_RING_BYTES = 1 << 31  # pinned result space of the serving bench's client
+
+
 def run_serve(args, world, rank, dist) -> None:
     """The request server against the plain per-request path, both fed the
     same Poisson arrival traces of host-memory requests."""
@@ -690,30 +694,78 @@ def run_serve(args, world, rank, dist) -> None:
             raise SystemExit("bench: plain path failed (%d, %d fields of %d)" % (rc, cnt.value,
                                                                                 fields))
 
-    def run_server(order, arr_ns):
+    # Results of the timed requests go to one pinned ring, taken in arrival
+    # order: the client waits for an earlier request only when the ring comes
+    # round to space that request still holds (more than the ring's bytes of
+    # results in flight), never because a body is used again.
+    ring = torch.empty(SERVE_RING_BYTES, dtype=torch.uint8).pin_memory()
+
+    def ring_views(a, fields):
+        return (ring[a:a + 8 * fields].view(torch.float64), ring[a + 8 * fields:a + 9 * fields])
+
+    def run_server(order, arr_ns, parts=None, check_last=64):
+        """Submit request i at t0 + arr_ns[i]; latency = done - that arrival.
+        parts collects the latency's pieces: client lag (arrival -> submit),
+        queue (submit -> launch) and service (launch -> done).  The last
+        check_last requests' results, still in the ring at the end, are
+        compared with the body's reference results."""
         n = len(order)
         t0 = time.monotonic_ns() + 2_000_000
         infos = [None] * n
         rids = [0] * n
-        last = {}
+        held = collections.deque()  # (start, end, request), oldest first
+        head = 0                    # the end of the newest region
+        where = [0] * n
+
+        def reserve(need):
+            """Start of `need` free bytes after the newest region (or at the
+            ring's start), waiting for the oldest requests until they fit."""
+            nonlocal head
+            while held:
+                tail = held[0][0]
+                if held[-1][0] >= tail:  # held: [tail, head)
+                    if head + need <= SERVE_RING_BYTES:
+                        return head
+                    if need <= tail:
+                        return 0
+                elif head + need <= tail:  # held: [tail, end) and [0, head)
+                    return head
+                _, _, p = held.popleft()
+                if infos[p] is None:
+                    infos[p] = srv.wait(rids[p])
+            return 0
+
         for i in range(n):
             j = int(order[i])
-            p = last.get(j)
-            if p is not None and infos[p] is None:  # the body's arrays are about to be reused
-                infos[p] = srv.wait(rids[p])
+            fields = bodies[j][3]
+            need = (9 * fields + 63) // 64 * 64
+            a = reserve(need)
             ta = t0 + int(arr_ns[i])
             while time.monotonic_ns() < ta:
                 pass
-            h, v, s_, _ = bodies[j]
-            rids[i] = srv.submit(h, v, s_)
-            last[j] = i
+            v, s_ = ring_views(a, fields)
+            rids[i] = srv.submit(bodies[j][0], v, s_)
+            held.append((a, a + need, i))
+            where[i] = a
+            head = a + need
         for i in range(n):
             if infos[i] is None:
                 infos[i] = srv.wait(rids[i])
         for i, inf in enumerate(infos):
             if inf["error"] or inf["count"] != bodies[int(order[i])][3]:
                 raise SystemExit("bench: server request %d failed: %r" % (i, inf))
-        lat = [inf["done_ns"] - (t0 + int(arr_ns[i])) for i, inf in enumerate(infos)]
+        for i in range(max(0, n - check_last), n):
+            j = int(order[i])
+            v, _ = ring_views(where[i], bodies[j][3])
+            if not np.array_equal(v.numpy().view(np.uint64), ref_bits[j]):
+                raise SystemExit("bench: server request %d (body %d) has wrong results" % (i, j))
+        arrival = [t0 + int(arr_ns[i]) for i in range(n)]
+        lat = [inf["done_ns"] - arrival[i] for i, inf in enumerate(infos)]
+        if parts is not None:
+            for name, a, b in (("client_lag", None, "submit_ns"), ("queue", "submit_ns", "launch_ns"),
+                               ("service", "launch_ns", "done_ns")):
+                d = [inf[b] - (arrival[i] if a is None else inf[a]) for i, inf in enumerate(infos)]
+                parts[name] = {"p50_ms": _percentile_ms(d, 50), "p99_ms": _percentile_ms(d, 99)}
         span = max(inf["done_ns"] for inf in infos) - t0
         return lat, span, [inf["batch_size"] for inf in infos]
 
@@ -735,8 +787,11 @@ def run_serve(args, world, rank, dist) -> None:
 
     # correctness: every body once through the server and once alone, against
     # each other, and a sample of bodies against the oracle
-    order0 = np.arange(R)
-    run_server(order0, np.zeros(R))
+    rids0 = [srv.submit(*bodies[j][:3]) for j in range(R)]
+    for j in range(R):
+        inf = srv.wait(rids0[j])
+        if inf["error"] or inf["count"] != bodies[j][3]:
+            raise SystemExit("bench: server request for body %d failed: %r" % (j, inf))
     ref_bits = [b[1].numpy().view(np.uint64).copy() for b in bodies]
     for j in range(R):
         plain_one(j)
@@ -773,13 +828,15 @@ def run_serve(args, world, rank, dist) -> None:
         arr -= arr[0]
         order = perm_order(n, 200 + k)
         nbytes = float(lens[order].sum())
-        lat_s, span_s, batch = run_server(order, arr)
+        parts = {}
+        lat_s, span_s, batch = run_server(order, arr, parts)
         lat_p, span_p = run_plain(order, arr)
         levels.append({
             "load": load, "offered_GBps": load * peak_server, "requests": n,
             "seconds": float(arr[-1]) / 1e9,
             "server": {"GBps": nbytes / (span_s / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_s, 50),
-                       "p99_ms": _percentile_ms(lat_s, 99), "mean_batch": float(np.mean(batch))},
+                       "p99_ms": _percentile_ms(lat_s, 99), "mean_batch": float(np.mean(batch)),
+                       "latency_parts": parts},
             "plain": {"GBps": nbytes / (span_p / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_p, 50),
                       "p99_ms": _percentile_ms(lat_p, 99)},
         })
