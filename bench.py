@@ -216,11 +216,27 @@ def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0, f32: bo
     for _ in range(passes):
         oracle_time(sample, cores, f32)
     dt = time.perf_counter() - t
-    return {"value": passes * len(sample) / dt / 1e9, "unit": UNIT, "cores": cores,
+    base = {"value": passes * len(sample) / dt / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "first %d bytes (%.2f MB, cut at a line break) of the %s workload, %d "
                       "pass(es), %d threads, %.2f s" % (len(sample), len(sample) / 1e6, kind,
                                                       passes, cores, dt)}
+    if not f32:
+        base["context"] = {"glibc_strtod": strtod_context(sample, cores)}
+    return base
+
+
+def strtod_context(sample: bytes, cores: int, seconds: float = 1.0) -> dict:
+    """The C library's strtod on the same sample and threads (context beside
+    the oracle: the paper's comparison point; correctly rounded in glibc)."""
+    from oracle import context
+    n, sec = context.strtod_buffer(sample, b"\n", cores)
+    passes = max(1, int(seconds / max(sec, 1e-6)))
+    total = 0.0
+    for _ in range(passes):
+        total += context.strtod_buffer(sample, b"\n", cores)[1]
+    return {"value": passes * len(sample) / total / 1e9, "unit": UNIT, "threads": cores,
+            "mfloats_per_s": passes * n / total / 1e6, "passes": passes}
 
 
 def run_reference(args, world, rank) -> None:
