@@ -537,6 +537,23 @@ FP_HD int clz32(uint32_t x) {
 #endif
 }
 
+// Sum of the four unsigned byte products of a and b, plus c.
+FP_HD uint32_t dp4a_u(uint32_t a, uint32_t b, uint32_t c) {
+#ifdef __CUDA_ARCH__
+  return __dp4a(a, b, c);
+#else
+  for (int i = 0; i < 4; i++) c += ((a >> (8 * i)) & 0xFF) * ((b >> (8 * i)) & 0xFF);
+  return c;
+#endif
+}
+
+// Two words of flag bytes (each 0x80 or 0) to 128 times an 8-bit mask: bit
+// b for byte b of w0, bit 4 + b for byte b of w1 (a byte dot product weighs
+// each flag by 2^b or 2^(4+b)).
+FP_HD uint32_t flag_pair(uint32_t w0, uint32_t w1) {
+  return dp4a_u(w1, 0x80402010u, dp4a_u(w0, 0x08040201u, 0u));
+}
+
 // 0x80 in every byte of t that is zero, exactly.
 FP_HD uint32_t zero_bytes(uint32_t t) {
   return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
@@ -619,10 +636,14 @@ FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
   // a word is exact); anything else that is not a digit, or a second point,
   // is still there after the point is removed and fails the check below
   int dpos = -1;
+  {
+    uint32_t f[6];
 #pragma unroll
-  for (int j = 5; j >= 0; j--) {
-    const uint32_t f = nondigit_flags(x[j]);
-    if (f) dpos = 4 * j + (ctz32(f) >> 3);
+    for (int j = 0; j < 6; j++) f[j] = nondigit_flags(x[j]);
+    // bit i: byte i of the window flagged (the lowest set bit is exact)
+    const uint32_t M = (flag_pair(f[0], f[1]) >> 7) | (flag_pair(f[2], f[3]) << 1) |
+                       (flag_pair(f[4], f[5]) << 9);
+    if (M) dpos = ctz32(M);
   }
   if (dpos >= 0 && tile[w0 + dpos] != '.') return false;  // (dpos >= tsig: text byte)
   // the bytes up to the point move one place toward the end, over it (a '0'

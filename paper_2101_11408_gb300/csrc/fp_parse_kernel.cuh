@@ -296,14 +296,12 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       const int j = tid * L::SEG_PER_THREAD + k;  // granule within the chunk
       const uint4 v = *reinterpret_cast<const uint4*>(tile + PAD + 16 * j);
       const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-      uint32_t m16 = 0;
+      uint32_t z[4];
 #pragma unroll
-      for (int i = 0; i < 4; i++) {
-        const uint32_t z = one_sep ? zero_bytes(w4[i] ^ NLW)
-                                   : (zero_bytes(w4[i] ^ NLW) | zero_bytes(w4[i] ^ DLW));
-        // the high bit of each byte -> one bit per byte position
-        m16 |= ((((z >> 7) * 0x00204081u) >> 21) & 0xFu) << (4 * i);
-      }
+      for (int i = 0; i < 4; i++)
+        z[i] = one_sep ? zero_bytes(w4[i] ^ NLW) : (zero_bytes(w4[i] ^ NLW) | zero_bytes(w4[i] ^ DLW));
+      // one bit per byte position
+      uint32_t m16 = (flag_pair(z[0], z[1]) >> 7) | (flag_pair(z[2], z[3]) << 1);
       const long long x0 = c0 + 16 * j;
       // boundaries in this granule are field starts iff o <= b < endx-1,
       // plus the virtual boundary o-1; the chunk's last byte c1-1 is not ours
@@ -499,17 +497,26 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       // list the starts of fields lo..hi (hi included: it ends field hi-1)
       {
         uint32_t rank = cur.rank0;
-        if (cur.pad_bit) {
-          if (rank >= lo && rank <= hi) S[rank - lo] = PAD;
-          rank++;
-        }
         const int base_off = PAD + 16 * tid * L::SEG_PER_THREAD + 1;
         MaskT m = cur.mask;
-        while (m) {
-          const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
-          if (rank >= lo && rank <= hi) S[rank - lo] = (uint16_t)(base_off + bpos);
-          rank++;
-          m &= m - 1;
+        if (n <= (uint32_t)L::S_CAP) {  // one window: every start is listed
+          if (cur.pad_bit) S[rank++] = PAD;
+          while (m) {
+            const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
+            S[rank++] = (uint16_t)(base_off + bpos);
+            m &= m - 1;
+          }
+        } else {
+          if (cur.pad_bit) {
+            if (rank >= lo && rank <= hi) S[rank - lo] = PAD;
+            rank++;
+          }
+          while (m) {
+            const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
+            if (rank >= lo && rank <= hi) S[rank - lo] = (uint16_t)(base_off + bpos);
+            rank++;
+            m &= m - 1;
+          }
         }
       }
       if (tid == 0) ms->group = 0;
@@ -549,19 +556,25 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       // its rare branches).
       const uint32_t cntw = hi - lo;
       const uint32_t ngroups = (cntw + 31) / 32;  // at most S_CAP / 32 = 32
-      uint32_t mine = 0;                          // the groups this warp took
+      uint32_t general = 0;  // this warp's groups with a field for the general tokenizer
       for (;;) {
         uint32_t gi = 0;
         if (lane == 0) gi = atomicAdd(&ms->group, 1u);
         gi = __shfl_sync(0xFFFFFFFFu, gi, 0);
         if (gi >= ngroups) break;
-        mine |= 1u << gi;
         const uint32_t k = 32 * gi + lane;
-        if (k < cntw) parse_hot(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
+        uint8_t status = ST_OK;
+        if (k < cntw) {
+          unsigned long long bits;
+          parse_hot(S[k], S[k + 1] - 1, bits, status);
+          stage_bits[k] = bits;
+          stage_st[k] = status;
+        }
+        if (__any_sync(0xFFFFFFFFu, status == ST_GENERAL)) general |= 1u << gi;
       }
-      while (mine) {
-        const uint32_t k = 32 * (__ffs(mine) - 1) + lane;
-        mine &= mine - 1;
+      while (general) {
+        const uint32_t k = 32 * (__ffs(general) - 1) + lane;
+        general &= general - 1;
         if (k < cntw && stage_st[k] == ST_GENERAL)
           parse_general(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
       }
