@@ -391,11 +391,15 @@ FP_API fp_err_t fp_timing_read(struct CUstream_st *stream, double *parse_ms,
  *   host_f64     host array of at least fp_max_fields(len) doubles
  *   host_status  host array of at least fp_max_fields(len) bytes
  *   host_count   host pointer: the number of fields
- * Copies the text to a per-stream device staging buffer, parses it there,
- * reads the field count and copies back exactly that many results.  When
- * all three host arrays are pinned and len >= 32 MB, the text is cut at
- * separators into segments of about 16 MB whose copies in, parses and
- * copies out overlap (results identical).  Synchronous: returns after the
+ * Copies the text to a per-stream device staging buffer and parses it
+ * there.  When host_f64 and host_status are pinned and len < 8 MB, the
+ * parse kernel writes the results (and the count) straight into them
+ * through their device addresses; otherwise the library reads the field
+ * count and copies back exactly that many results.  When all three host
+ * arrays are pinned and len >= 32 MB, the text is cut at separators into
+ * segments of about 16 MB whose copies in, parses and copies out overlap,
+ * each segment's count written by its parse kernel into pinned host memory
+ * (results identical).  Synchronous: returns after the
  * results are in host memory.  The staging buffers are allocated with
  * cudaMalloc on first use and grown as needed.
  */

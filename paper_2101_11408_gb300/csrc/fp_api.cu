@@ -94,7 +94,8 @@ struct Scratch {
   double* stage_out = nullptr;
   uint8_t* stage_status = nullptr;
   unsigned long long* stage_count = nullptr;
-  size_t stage_cap = 0;
+  size_t stage_cap = 0;      // bytes of stage_text
+  size_t stage_out_cap = 0;  // entries of stage_out and stage_status
   // binary32 calls: pending fields' locations, indexed like the outputs
   unsigned long long* loc = nullptr;
   unsigned long long cap_loc = 0;
@@ -104,8 +105,10 @@ struct Scratch {
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev_in[PIPE_SEGS] = {}, pipe_ev_parsed[PIPE_SEGS] = {};
   cudaEvent_t pipe_ev_start = nullptr, pipe_ev_done = nullptr;
-  unsigned long long* pipe_dev = nullptr;   // segment counts (device)
-  unsigned long long* pipe_host = nullptr;  // segment counts (pinned)
+  unsigned long long* pipe_counts = nullptr;     // segment counts (pinned) ...
+  unsigned long long* pipe_counts_dv = nullptr;  // ... and the address the parse kernel writes them at
+  unsigned long long* pipe_host = nullptr;       // one count (pinned) ...
+  unsigned long long* pipe_host_dv = nullptr;    // ... and the address the parse kernel writes it at
 };
 bool g_timing = false;
 
@@ -200,7 +203,7 @@ void free_scratch(Scratch* s) {
   }
   if (s->pipe_ev_start) cudaEventDestroy(s->pipe_ev_start);
   if (s->pipe_ev_done) cudaEventDestroy(s->pipe_ev_done);
-  cudaFree(s->pipe_dev);
+  cudaFreeHost(s->pipe_counts);
   cudaFreeHost(s->pipe_host);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
@@ -446,8 +449,12 @@ namespace {
 // host-buffer parse
 // ---------------------------------------------------------------------------
 constexpr size_t PIPE_MIN_BYTES = 32u << 20;  // smaller texts take the simple path
-constexpr size_t PIPE_SEG_BYTES = 16u << 20;  // segment size of the pipelined path (each parse
-                                              // launch has a fixed cost of about 25 us)
+// Below this many bytes the simple path lets the parse kernel write the
+// results into pinned host arrays directly (no count round trip, no copy
+// calls); larger result sets move faster by copy engine.
+constexpr size_t DIRECT_MAX_BYTES = 8u << 20;
+constexpr size_t PIPE_SEG_BYTES = 16u << 20;  // segment size of the pipelined path (each copy
+                                              // in and each parse call has a fixed cost)
 
 // The address the device uses for host memory p, or null when p is not
 // pinned (page-locked) memory.
@@ -462,8 +469,9 @@ const void* device_view(const void* p) {
 }
 void* device_view(void* p) { return const_cast<void*>(device_view(static_cast<const void*>(p))); }
 
-// Staging of (stream) for texts of len bytes.  Call with g_mu held.
-fp_err_t stage_for(cudaStream_t stream, size_t len, Scratch** out) {
+// Staging of (stream) for texts of len bytes, and for their results when
+// `results` (room for len of them).  Call with g_mu held.
+fp_err_t stage_for(cudaStream_t stream, size_t len, bool results, Scratch** out) {
   Scratch* s = nullptr;
   fp_err_t e = get_scratch(stream, 1, 1, g_cfg.fallback_queue, &s);
   if (e != FP_OK) return e;
@@ -471,34 +479,107 @@ fp_err_t stage_for(cudaStream_t stream, size_t len, Scratch** out) {
   if (len > s->stage_cap) {
     FP_CUDA(cudaStreamSynchronize(stream));
     cudaFree(s->stage_text);
-    cudaFree(s->stage_out);
-    cudaFree(s->stage_status);
     s->stage_text = nullptr;
-    s->stage_out = nullptr;
-    s->stage_status = nullptr;
     s->stage_cap = 0;
     FP_CUDA(cudaMalloc(&s->stage_text, len));
+    s->stage_cap = len;
+  }
+  if (results && len > s->stage_out_cap) {
+    FP_CUDA(cudaStreamSynchronize(stream));
+    cudaFree(s->stage_out);
+    cudaFree(s->stage_status);
+    s->stage_out = nullptr;
+    s->stage_status = nullptr;
+    s->stage_out_cap = 0;
     FP_CUDA(cudaMalloc(&s->stage_out, len * sizeof(double)));
     FP_CUDA(cudaMalloc(&s->stage_status, len));
-    s->stage_cap = len;
+    s->stage_out_cap = len;
   }
   *out = s;
   return FP_OK;
 }
 
+// One-buffer binary64 parse of device text into out_f64 / out_status (room
+// for out_cap results; device memory, or pinned host memory through its
+// device address).  base_in / base_out: see LaunchParams (null: the results
+// start at out_f64[0]).  out_count may be null.
+fp_err_t parse_one(const char* text, size_t len, char delim, double* out_f64, uint8_t* out_status,
+                   size_t out_cap, uint64_t* out_count, const unsigned long long* base_in,
+                   unsigned long long* base_out, cudaStream_t stream) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  const Config cfg = g_cfg;
+  int dev = 0;
+  FP_CUDA(cudaGetDevice(&dev));
+  DeviceInfo* di = nullptr;
+  fp_err_t e = device_info(dev, &di);
+  if (e != FP_OK) return e;
+  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
+  const unsigned long long nch = chunks_of(t & 15, len, cfg.chunk_bytes);
+  Scratch* s = nullptr;
+  e = get_scratch(stream, nch, 1, cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  LaunchParams p;
+  memset(&p, 0, sizeof(p));
+  fill_desc(p.one, text, len, 0, nch, 0, out_cap, out_count);
+  p.descs = nullptr;
+  p.nbuf = 1;
+  p.delim = (unsigned char)delim;
+  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
+  p.out_status = out_status;
+  p.base_in = base_in;
+  p.base_out = base_out;
+  return run(s, cfg, *di, p, nch, len, stream);
+}
+
+// The mapped count word of (stream)'s scratch (pinned; `dv` is its device
+// address).  Call with g_mu held.
+fp_err_t count_word(Scratch* s, volatile unsigned long long** host,
+                    unsigned long long** dv) {
+  if (!s->pipe_host) {
+    FP_CUDA(cudaMallocHost(&s->pipe_host, sizeof(unsigned long long)));
+    FP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->pipe_host_dv), s->pipe_host, 0));
+  }
+  *host = s->pipe_host;
+  *dv = s->pipe_host_dv;
+  return FP_OK;
+}
+
 // One copy in, one parse, the count, then exactly that many results back.
+// When both result arrays are pinned and the text is below DIRECT_MAX_BYTES
+// the parse kernel writes them (and the count) in host memory directly, so
+// nothing is copied back.
 fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host_f64,
                      uint8_t* host_status, uint64_t* host_count, cudaStream_t stream) {
+  double* dv_f64 = static_cast<double*>(device_view(host_f64));
+  uint8_t* dv_st = static_cast<uint8_t*>(device_view(host_status));
+  const bool direct = dv_f64 && dv_st && len < DIRECT_MAX_BYTES;
   Scratch* s = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
-    fp_err_t e = stage_for(stream, len, &s);
+    fp_err_t e = stage_for(stream, len, !direct, &s);
     if (e != FP_OK) return e;
   }
   if (len) FP_CUDA(cudaMemcpyAsync(s->stage_text, host_text, len, cudaMemcpyHostToDevice, stream));
-  fp_err_t e = fp_parse_f64(len ? (const char*)s->stage_text : nullptr, len, delim, s->stage_out,
-                            s->stage_status, (uint64_t*)s->stage_count,
-                            reinterpret_cast<struct CUstream_st*>(stream));
+  const char* text = len ? (const char*)s->stage_text : nullptr;
+  if (direct) {  // results straight into the caller's pinned arrays
+    volatile unsigned long long* hc = nullptr;
+    unsigned long long* dc = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      fp_err_t e = count_word(s, &hc, &dc);
+      if (e != FP_OK) return e;
+    }
+    fp_err_t e = parse_one(text, len, delim, dv_f64, dv_st, len, (uint64_t*)dc, nullptr, nullptr,
+                           stream);
+    if (e != FP_OK) return e;
+    FP_CUDA(cudaStreamSynchronize(stream));
+    const unsigned long long n = *hc;
+    if (n > len) return FP_ERR_INTERNAL;
+    *host_count = n;
+    return FP_OK;
+  }
+  fp_err_t e = parse_one(text, len, delim, s->stage_out, s->stage_status, len,
+                         (uint64_t*)s->stage_count, nullptr, nullptr, stream);
   if (e != FP_OK) return e;
   unsigned long long n = 0;
   FP_CUDA(cudaMemcpyAsync(&n, s->stage_count, sizeof(n), cudaMemcpyDeviceToHost, stream));
@@ -518,9 +599,13 @@ fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host
 // PIPE_SEG_BYTES (each ends with its separator, so its fields are exactly
 // the buffer's fields in that range).  All segments are copied in on
 // pipe_in, back to back; segment i is parsed on the caller's stream once it
-// has landed, and its field count comes back on pipe_out; this thread waits
-// for each count in turn and queues the copies of exactly that many results
-// (copy engine, pipe_out) at the running total.  Copies in, parses and
+// has landed, and the parse kernel writes its field count straight into
+// pinned host memory (no copy call queues behind the result copies); this
+// thread waits for each parse in turn and queues the copies of exactly that
+// many results (copy engine, pipe_out) at the running total.  (Results
+// written by the parse kernels into the caller's pinned arrays directly
+// were slower here: the kernels' writes share the link less well than the
+// copy engine's.)  Copies in, parses and
 // copies out of different segments overlap, and the SMs only parse.
 fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* host_f64,
                         uint8_t* host_status, uint64_t* host_count, cudaStream_t stream) {
@@ -544,7 +629,7 @@ fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* h
   {
     std::lock_guard<std::mutex> lk(g_mu);
     cfg = g_cfg;
-    fp_err_t e = stage_for(stream, len, &s);
+    fp_err_t e = stage_for(stream, len, true, &s);
     if (e != FP_OK) return e;
     size_t maxseg = 0;
     for (int i = 0; i < K; i++) maxseg = std::max(maxseg, cuts[i + 1] - cuts[i]);
@@ -559,12 +644,13 @@ fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* h
       }
       FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_start, cudaEventDisableTiming));
       FP_CUDA(cudaEventCreateWithFlags(&s->pipe_ev_done, cudaEventDisableTiming));
-      FP_CUDA(cudaMalloc(&s->pipe_dev, Scratch::PIPE_SEGS * sizeof(unsigned long long)));
-      FP_CUDA(cudaMallocHost(&s->pipe_host, Scratch::PIPE_SEGS * sizeof(unsigned long long)));
+      FP_CUDA(cudaMallocHost(&s->pipe_counts, Scratch::PIPE_SEGS * sizeof(unsigned long long)));
+      FP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->pipe_counts_dv), s->pipe_counts,
+                                       0));
     }
   }
-  unsigned long long* counts = s->pipe_dev;
-  volatile unsigned long long* hcounts = s->pipe_host;
+  unsigned long long* counts = s->pipe_counts_dv;  // written by the parse kernels
+  volatile unsigned long long* hcounts = s->pipe_counts;
   // everything queued before on the caller's stream comes first
   FP_CUDA(cudaEventRecord(s->pipe_ev_start, stream));
   FP_CUDA(cudaStreamWaitEvent(s->pipe_in, s->pipe_ev_start, 0));
@@ -581,8 +667,6 @@ fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* h
                               s->stage_out + c, s->stage_status + c, (uint64_t*)(counts + i),
                               reinterpret_cast<struct CUstream_st*>(stream));
     if (e != FP_OK) return e;
-    FP_CUDA(cudaMemcpyAsync((void*)(hcounts + i), counts + i, sizeof(unsigned long long),
-                            cudaMemcpyDeviceToHost, stream));
     FP_CUDA(cudaEventRecord(s->pipe_ev_parsed[i], stream));
   }
   unsigned long long total = 0;
@@ -614,28 +698,8 @@ fp_err_t fp_parse_f64(const char* text, size_t len, char delim, double* out_f64,
   if (len >= MAX_LEN) return FP_ERR_ARG;
   if (!out_count) return FP_ERR_ARG;
   if (len > 0 && (!text || !out_f64 || !out_status)) return FP_ERR_ARG;
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  std::lock_guard<std::mutex> lk(g_mu);
-  const Config cfg = g_cfg;
-  int dev = 0;
-  FP_CUDA(cudaGetDevice(&dev));
-  DeviceInfo* di = nullptr;
-  fp_err_t e = device_info(dev, &di);
-  if (e != FP_OK) return e;
-  const uintptr_t t = reinterpret_cast<uintptr_t>(text);
-  const unsigned long long nch = chunks_of(t & 15, len, cfg.chunk_bytes);
-  Scratch* s = nullptr;
-  e = get_scratch(stream, nch, 1, cfg.fallback_queue, &s);
-  if (e != FP_OK) return e;
-  LaunchParams p;
-  memset(&p, 0, sizeof(p));
-  fill_desc(p.one, text, len, 0, nch, 0, len, out_count);
-  p.descs = nullptr;
-  p.nbuf = 1;
-  p.delim = (unsigned char)delim;
-  p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
-  p.out_status = out_status;
-  return run(s, cfg, *di, p, nch, len, stream);
+  return parse_one(text, len, delim, out_f64, out_status, len, out_count, nullptr, nullptr,
+                   reinterpret_cast<cudaStream_t>(stream_));
 }
 
 fp_err_t fp_parse_f32(const char* text, size_t len, char delim, float* out_f32,

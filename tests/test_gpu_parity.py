@@ -327,6 +327,32 @@ def test_host_entry_point():
     assert np.array_equal(vals.view(np.uint64), rb) and np.array_equal(st, rs)
 
 
+def test_host_entry_point_direct():
+    """Below 8 MB with pinned result arrays the parse kernel writes the
+    results and the count into host memory itself: equal to the oracle,
+    hard cases included (the fallback kernel then reads the pending fields'
+    locations from, and writes their values to, the pinned arrays), nothing
+    written past the count, for pinned and pageable text."""
+    texts = [workloads.bulk_mixed_text(100_000, 94), workloads.hard_case_text(5_000, 95), b"",
+             b"1", b"\n\n", b"1e-400\n-0\nx\n" + b"9" * 900 + b"e-1000"]
+    for text in texts:
+        rb, rs = oracle.parse_buffer(text)
+        n = len(text) + 64
+        for pin_text in (True, False):
+            h_text = (torch.frombuffer(bytearray(text), dtype=torch.uint8) if text
+                      else torch.empty(0, dtype=torch.uint8))
+            if pin_text:
+                h_text = h_text.pin_memory()
+            h_out = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+            h_st = torch.full((n,), 0xEE, dtype=torch.uint8).pin_memory()
+            k = fp.parse_f64_host_into(h_text, h_out, h_st)
+            assert k == rb.size, (text[:30], pin_text)
+            assert np.array_equal(h_out[:k].numpy().view(np.uint64), rb)
+            assert np.array_equal(h_st[:k].numpy(), rs)
+            assert (h_st[k:].numpy() == 0xEE).all() and (h_out[k:].numpy() == -1.0).all()
+    assert fp.get_error() == 0
+
+
 def test_autotune_picks_a_valid_config(tmp_path):
     before = fp.get_config()
     try:
