@@ -501,11 +501,9 @@ fp_err_t stage_for(cudaStream_t stream, size_t len, bool results, Scratch** out)
 
 // One-buffer binary64 parse of device text into out_f64 / out_status (room
 // for out_cap results; device memory, or pinned host memory through its
-// device address).  base_in / base_out: see LaunchParams (null: the results
-// start at out_f64[0]).  out_count may be null.
+// device address).  out_count may be null.
 fp_err_t parse_one(const char* text, size_t len, char delim, double* out_f64, uint8_t* out_status,
-                   size_t out_cap, uint64_t* out_count, const unsigned long long* base_in,
-                   unsigned long long* base_out, cudaStream_t stream) {
+                   size_t out_cap, uint64_t* out_count, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(g_mu);
   const Config cfg = g_cfg;
   int dev = 0;
@@ -526,8 +524,6 @@ fp_err_t parse_one(const char* text, size_t len, char delim, double* out_f64, ui
   p.delim = (unsigned char)delim;
   p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
   p.out_status = out_status;
-  p.base_in = base_in;
-  p.base_out = base_out;
   return run(s, cfg, *di, p, nch, len, stream);
 }
 
@@ -569,8 +565,7 @@ fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host
       fp_err_t e = count_word(s, &hc, &dc);
       if (e != FP_OK) return e;
     }
-    fp_err_t e = parse_one(text, len, delim, dv_f64, dv_st, len, (uint64_t*)dc, nullptr, nullptr,
-                           stream);
+    fp_err_t e = parse_one(text, len, delim, dv_f64, dv_st, len, (uint64_t*)dc, stream);
     if (e != FP_OK) return e;
     FP_CUDA(cudaStreamSynchronize(stream));
     const unsigned long long n = *hc;
@@ -579,7 +574,7 @@ fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host
     return FP_OK;
   }
   fp_err_t e = parse_one(text, len, delim, s->stage_out, s->stage_status, len,
-                         (uint64_t*)s->stage_count, nullptr, nullptr, stream);
+                         (uint64_t*)s->stage_count, stream);
   if (e != FP_OK) return e;
   unsigned long long n = 0;
   FP_CUDA(cudaMemcpyAsync(&n, s->stage_count, sizeof(n), cudaMemcpyDeviceToHost, stream));
@@ -698,7 +693,7 @@ fp_err_t fp_parse_f64(const char* text, size_t len, char delim, double* out_f64,
   if (len >= MAX_LEN) return FP_ERR_ARG;
   if (!out_count) return FP_ERR_ARG;
   if (len > 0 && (!text || !out_f64 || !out_status)) return FP_ERR_ARG;
-  return parse_one(text, len, delim, out_f64, out_status, len, out_count, nullptr, nullptr,
+  return parse_one(text, len, delim, out_f64, out_status, len, out_count,
                    reinterpret_cast<cudaStream_t>(stream_));
 }
 

@@ -355,10 +355,6 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     // (warp_sum is next written after at least one more barrier)
   };
 
-  // output index of the first field of a one-buffer launch that appends to
-  // an earlier launch's results (written by that launch)
-  const unsigned long long dyn_base = p.base_in ? *p.base_in : 0ull;
-
   Counted cur, nxt;
   int buf = 0;
   // this block's previous chunk and the inclusive prefix after it
@@ -399,7 +395,6 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
 
     const BufDesc d = ms->desc[buf];
     const unsigned int dix = ms->desc_index[buf];
-    const unsigned long long out_base = d.out_base + dyn_base;  // output index of the buffer's field 0
     const long long lc = (long long)(g - d.chunk0);
     const long long c0 = lc * C;
     const long long t0 = c0 - PAD;
@@ -465,7 +460,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       typename F::word* vo = ob + k;
       uint8_t* so = os + k;
       if constexpr ((MODE & MODE_COLUMNS) != 0) {
-        const unsigned long long i = out_base + base + k;
+        const unsigned long long i = d.out_base + base + k;
         const unsigned long long row = __umul64hi(i, p.col_magic);
         const unsigned long long col = i - row * p.columns;
         // the last column ends at '\n' (or the end of the text), the others
@@ -480,13 +475,13 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       if constexpr (in_slot) {
         *vo = bits;  // a pending field's location stays in its own slot
       } else {
-        if (status == ST_PENDING) p.loc[out_base + base + k] = bits;
+        if (status == ST_PENDING) p.loc[d.out_base + base + k] = bits;
         else *vo = (typename F::word)bits;
       }
       if (status == ST_PENDING) {
         const unsigned long long slot = atomicAdd(&ctl->qcount, 1ull);
         if (slot < p.qcap) {
-          p.queue[slot] = out_base + base + k;
+          p.queue[slot] = d.out_base + base + k;
           *so = ST_PENDING_QUEUED;
         } else {
           *so = ST_PENDING_SCAN;
@@ -551,10 +546,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         if (lane == 0) {
           ms->lb_part[0] = b;
           if (lc != 0) st_relaxed_u64(&p.chunk_status[g], lb_word(p.epoch, LB_FLAG_INC, b + n));
-          if (lc + 1 == (long long)d.nchunks) {
-            if (d.out_count) *d.out_count = b + n;
-            if (p.base_out) *p.base_out = dyn_base + b + n;
-          }
+          if (lc + 1 == (long long)d.nchunks && d.out_count) *d.out_count = b + n;
         }
       }
       // Warps take groups of 32 fields until none is left, so that the warp
@@ -593,8 +585,8 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       if (lo == 0) {
         base = ms->lb_part[0];
         cap = d.out_cap > base ? d.out_cap - base : 0;
-        ob = reinterpret_cast<typename F::word*>(p.out_bits) + out_base + base;
-        os = p.out_status + out_base + base;
+        ob = reinterpret_cast<typename F::word*>(p.out_bits) + d.out_base + base;
+        os = p.out_status + d.out_base + base;
       }
       for (uint32_t k = warp * share + lane; k < k_end; k += 32)
         store_one(lo + k, stage_bits[k], stage_st[k], (int)S[k + 1] - 1);
@@ -610,7 +602,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         // (descriptor << 40 | fields of the chunk that were stored, first output index)
         const unsigned long long stored = n < cap ? n : cap;
         p.ovf[2 * slot] = ((unsigned long long)dix << LOC_OFF_BITS) | stored;
-        p.ovf[2 * slot + 1] = out_base + base;
+        p.ovf[2 * slot + 1] = d.out_base + base;
       } else {
         set_error(ctl, DERR_INTERNAL);
       }

@@ -56,13 +56,6 @@ struct LaunchParams {
   unsigned int columns;     // K >= 2: column-major results (field i -> column i mod K)
   unsigned long long rows_cap;   // entries per column
   unsigned long long col_magic;  // ceil(2^64 / K): i div K = mulhi(i, magic) for i < 2^40
-  // Optional, one-buffer launches only (null otherwise): the buffer's first
-  // output index is *base_in plus its descriptor's out_base, and the launch
-  // writes that index plus the buffer's field count to *base_out.  A launch
-  // on the same stream whose base_in is an earlier launch's base_out
-  // appends its results to that one's without the host knowing the counts.
-  const unsigned long long* base_in;
-  unsigned long long* base_out;
 };
 
 // Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).
