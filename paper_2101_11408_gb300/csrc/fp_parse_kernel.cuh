@@ -132,52 +132,73 @@ __device__ __forceinline__ void issue_stage(uint8_t* tile, uint64_t* bar, const 
 // a chunk whose inclusive prefix `known` this block already has (its own
 // previous chunk).  Chunks publish their counts (aggregates) as soon as they
 // are counted, one iteration before they are parsed, and their inclusive
-// prefixes once known; the warp reads up to 32*LB_PER_LANE entries per
-// round, newest first, and stops at the nearest inclusive prefix.  Each wait
-// is bounded.  Every lane returns the prefix.
+// prefixes once known; the warp reads PER entries per lane per round, newest
+// first, and stops at the nearest inclusive prefix.  Each wait is bounded.
+// One round: returns the sum of the entries up to and including the nearest
+// inclusive one (or of all PER*32 when there is none) to every lane, and
+// whether one was found.
+template <int PER>
+__device__ __forceinline__ unsigned long long lookback_round(const LaunchParams& p, long long top,
+                                                             long long first, int lane,
+                                                             bool& found) {
+  unsigned long long wv[PER];
+#pragma unroll
+  for (int u = 0; u < PER; u++) {
+    const long long idx = top - (PER * lane + u);
+    wv[u] = idx >= first ? ld_relaxed_u64(&p.chunk_status[idx]) : lb_word(p.epoch, LB_FLAG_AGG, 0);
+  }
+  unsigned int nearest = 0xFFFFFFFFu;  // distance of this lane's nearest inclusive entry
+  unsigned long long part = 0;
+#pragma unroll
+  for (int u = 0; u < PER; u++) {
+    const long long idx = top - (PER * lane + u);
+    if ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0) {
+      const uint64_t ts = globaltimer_ns();
+      do {
+        __nanosleep(64);
+        wv[u] = ld_relaxed_u64(&p.chunk_status[idx]);
+        if (globaltimer_ns() - ts > 2000000000ull) {
+          set_error(p.ctl, DERR_TIMEOUT);
+          wv[u] = lb_word(p.epoch, LB_FLAG_INC, 0);
+          break;
+        }
+      } while ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0);
+    }
+    const bool inc = ((wv[u] >> LB_VALUE_BITS) & 3) == LB_FLAG_INC;
+    if (nearest == 0xFFFFFFFFu) {
+      part += wv[u] & LB_VALUE_MASK;
+      if (inc) nearest = PER * lane + u;
+    }
+  }
+  const unsigned int stop = __reduce_min_sync(0xFFFFFFFFu, nearest);
+  // lanes wholly beyond the nearest inclusive entry contribute nothing
+  if ((unsigned int)(PER * lane) > stop) part = 0;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
+  found = stop != 0xFFFFFFFFu;
+  return part;
+}
+
+// The 32 nearest entries first (one load per lane: most look-backs stop
+// there), then the next 128, then rounds of 32*LB_PER_LANE.  Every lane
+// returns the prefix.
 constexpr int LB_PER_LANE = 16;
 __device__ __forceinline__ unsigned long long warp_lookback(const LaunchParams& p, long long g,
                                                             long long first,
                                                             unsigned long long known, int lane) {
-  unsigned long long prefix = 0;
   long long top = g - 1;
+  if (top < first) return known;
+  bool found = false;
+  unsigned long long prefix = lookback_round<1>(p, top, first, lane, found);
+  if (found) return prefix;
+  top -= 32;
+  if (top < first) return prefix + known;
+  prefix += lookback_round<4>(p, top, first, lane, found);
+  if (found) return prefix;
+  top -= 128;
   while (top >= first) {
-    unsigned long long wv[LB_PER_LANE];
-#pragma unroll
-    for (int u = 0; u < LB_PER_LANE; u++) {
-      const long long idx = top - (LB_PER_LANE * lane + u);
-      wv[u] = idx >= first ? ld_relaxed_u64(&p.chunk_status[idx]) : lb_word(p.epoch, LB_FLAG_AGG, 0);
-    }
-    unsigned int nearest = 0xFFFFFFFFu;  // distance of this lane's nearest inclusive entry
-    unsigned long long part = 0;
-#pragma unroll
-    for (int u = 0; u < LB_PER_LANE; u++) {
-      const long long idx = top - (LB_PER_LANE * lane + u);
-      if ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0) {
-        const uint64_t ts = globaltimer_ns();
-        do {
-          __nanosleep(64);
-          wv[u] = ld_relaxed_u64(&p.chunk_status[idx]);
-          if (globaltimer_ns() - ts > 2000000000ull) {
-            set_error(p.ctl, DERR_TIMEOUT);
-            wv[u] = lb_word(p.epoch, LB_FLAG_INC, 0);
-            break;
-          }
-        } while ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0);
-      }
-      const bool inc = ((wv[u] >> LB_VALUE_BITS) & 3) == LB_FLAG_INC;
-      if (nearest == 0xFFFFFFFFu) {
-        part += wv[u] & LB_VALUE_MASK;
-        if (inc) nearest = LB_PER_LANE * lane + u;
-      }
-    }
-    const unsigned int stop = __reduce_min_sync(0xFFFFFFFFu, nearest);
-    // lanes wholly beyond the nearest inclusive entry contribute nothing
-    if ((unsigned int)(LB_PER_LANE * lane) > stop) part = 0;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
-    prefix += part;
-    if (stop != 0xFFFFFFFFu) return prefix;
+    prefix += lookback_round<LB_PER_LANE>(p, top, first, lane, found);
+    if (found) return prefix;
     top -= 32 * LB_PER_LANE;
   }
   return prefix + known;
