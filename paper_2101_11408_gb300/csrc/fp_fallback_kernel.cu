@@ -191,36 +191,53 @@ __device__ __forceinline__ void float_parts(uint64_t x, uint64_t& M, int& e) {
 
 __device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c == '\n' || c == delim; }
 
+// The power part of a midpoint, 2^(e-1) or 5^(1-e) (times 10^Eh), for the
+// exponent e of the last call: the midpoints on both sides of a candidate
+// share it (unless they straddle a power of two), so it is formed once.
+struct MidPower {
+  bool valid;
+  int e;
+  long long Eh;
+  WBig X;  // in sm.P or sm.Q
+};
+
 // Sign of V - h into c, V = dig[0 .. nD) 10^ED and h the midpoint between
 // the positive patterns lowbits and lowbits + 1 of F; false on a size error.
 template <class F>
 __device__ __noinline__ bool cmp_midpoint(uint64_t lowbits, WarpSmem& sm, long long nD,
-                                          long long ED, int& c, int lane) {
-  WBig X{sm.P, 0}, A{sm.B, 0}, Y{sm.Q, 0};
+                                          long long ED, int& c, int lane, MidPower& mp) {
   uint64_t M;
   int e;
   float_parts<F>(lowbits, M, e);
   const uint64_t T = 2 * M + 1;  // < 2^55 < 10^18
-  long long Eh;
-  uint32_t m;  // the small power after the table's
-  if (e >= 1) {  // h = T 2^(e-1)
-    const int k = e - 1;
-    dec_load(X, dec2_limbs, dec2_off, k / FP_DEC2_STEP, lane);
-    m = 1u << (k % FP_DEC2_STEP);
-    Eh = 0;
-  } else {  // h = T 5^(1-e) 10^(e-1)
-    const int j = 1 - e;
-    dec_load(X, dec5_limbs, dec5_off, j / FP_DEC5_STEP, lane);
-    m = 1;
-    for (int b = j % FP_DEC5_STEP; b > 0; b--) m *= 5;
-    Eh = e - 1;
+  if (!mp.valid || mp.e != e) {
+    WBig X{sm.P, 0}, Y{sm.Q, 0};
+    long long Eh;
+    uint32_t m;  // the small power after the table's
+    if (e >= 1) {  // h = T 2^(e-1)
+      const int k = e - 1;
+      dec_load(X, dec2_limbs, dec2_off, k / FP_DEC2_STEP, lane);
+      m = 1u << (k % FP_DEC2_STEP);
+      Eh = 0;
+    } else {  // h = T 5^(1-e) 10^(e-1)
+      const int j = 1 - e;
+      dec_load(X, dec5_limbs, dec5_off, j / FP_DEC5_STEP, lane);
+      m = 1;
+      for (int b = j % FP_DEC5_STEP; b > 0; b--) m *= 5;
+      Eh = e - 1;
+    }
+    if (m != 1) {
+      if (!dec_mul(Y, X, m, lane)) return false;
+      X = Y;  // the power now sits in sm.Q
+    }
+    mp.valid = true;
+    mp.e = e;
+    mp.Eh = Eh;
+    mp.X = X;
   }
-  if (m != 1) {
-    if (!dec_mul(Y, X, m, lane)) return false;
-    const WBig t = X;  // swap the roles of X and Y
-    X = Y;
-    Y = t;
-  }
+  const WBig X = mp.X;
+  const long long Eh = mp.Eh;
+  WBig A{sm.B, 0}, Y{X.p == sm.P ? sm.Q : sm.P, 0};  // the two buffers X does not use
   const uint32_t t0 = (uint32_t)(T % DBASE), t1 = (uint32_t)(T / DBASE);
   if (!dec_mul(A, X, t0, lane)) return false;
   if (t1) {
@@ -319,22 +336,64 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     return r;
   };
   // ---- the field's end, first and last non-blank byte ---------------------
+  // 512 bytes per round: lane L tests the aligned 16-byte granule L of the
+  // round with word-wide zero-byte tests.  A granule is read only if it
+  // holds a byte of the text (x0 < lim), so no read leaves the 16-byte
+  // granules of the buffer; bytes before the field are ignored and bytes at
+  // or after lim act as separators.
+  const uint8_t* fa = reinterpret_cast<const uint8_t*>(reinterpret_cast<uintptr_t>(f) & ~(uintptr_t)15);
+  const long long head = f - fa;
   long long fe = (long long)lim;
   long long p0 = -1, p1 = 0;
-  for (long long base = 0; base < (long long)lim; base += 32) {
-    const long long i = base + lane;
-    const uint32_t c = i < (long long)lim ? f[i] : '\n';
-    const uint32_t S = __ballot_sync(FULL, is_sep(c, delim));
-    const uint32_t valid = S ? ((S & (0u - S)) - 1) : FULL;  // lanes before the first separator
-    const uint32_t nb = __ballot_sync(FULL, !is_ws(c)) & valid;
-    if (nb) {
-      if (p0 < 0) p0 = base + __ffs(nb) - 1;
-      p1 = base + 32 - __clz(nb);
+  for (long long r0 = 0;; r0 += 512) {
+    const long long x0 = r0 + 16 * lane - head;  // field offset of this lane's first byte
+    uint32_t sepm = 0xFFFFu, nbm = 0;           // bit b: byte x0 + b
+    if (x0 < (long long)lim) {
+      const uint4 v = *reinterpret_cast<const uint4*>(fa + r0 + 16 * lane);
+      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
+      uint32_t sz[4], wz[4];
+      const uint32_t DLW = delim * 0x01010101u;
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        sz[i] = zero_bytes(w4[i] ^ 0x0A0A0A0Au) | zero_bytes(w4[i] ^ DLW);
+        wz[i] = zero_bytes(w4[i] ^ 0x20202020u) | zero_bytes(w4[i] ^ 0x09090909u) |
+                zero_bytes(w4[i] ^ 0x0D0D0D0Du);
+      }
+      sepm = (flag_pair(sz[0], sz[1]) >> 7) | (flag_pair(sz[2], sz[3]) << 1);
+      nbm = ~((flag_pair(wz[0], wz[1]) >> 7) | (flag_pair(wz[2], wz[3]) << 1)) & 0xFFFFu;
+      if (x0 + 16 > (long long)lim) {  // bytes at or after lim: separators
+        const uint32_t past = 0xFFFFu << (int)((long long)lim - x0);
+        sepm |= past & 0xFFFFu;
+        nbm &= ~past;
+      }
+      if (x0 < 0) {  // bytes before the field
+        const uint32_t keep = 0xFFFFu << (int)(-x0);
+        sepm &= keep;
+        nbm &= keep;
+      }
     }
+    const uint32_t S = __ballot_sync(FULL, sepm != 0);
+    int Ls = 32, bs = 0;
     if (S) {
-      fe = base + __ffs(S) - 1;
-      break;
+      Ls = __ffs(S) - 1;
+      bs = __ffs(__shfl_sync(FULL, sepm, Ls)) - 1;
+      fe = r0 + 16 * Ls - head + bs;
     }
+    // non-blank bytes before the first separator
+    if (lane > Ls) nbm = 0;
+    else if (lane == Ls) nbm &= (1u << bs) - 1u;
+    const uint32_t NB = __ballot_sync(FULL, nbm != 0);
+    if (NB) {
+      const int L1 = 31 - __clz(NB);
+      const uint32_t m1 = __shfl_sync(FULL, nbm, L1);
+      if (p0 < 0) {
+        const int L0 = __ffs(NB) - 1;
+        const uint32_t m0 = __shfl_sync(FULL, nbm, L0);
+        p0 = r0 + 16 * L0 - head + __ffs(m0) - 1;
+      }
+      p1 = r0 + 16 * L1 - head + (32 - __clz(m1));
+    }
+    if (S) break;
   }
   *nl = fe >= (long long)lim || f[fe] == '\n';
   if (p0 < 0) return invalid();  // blank or empty
@@ -499,8 +558,13 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     uint64_t x = 0;
     if (lane == 0) x = convert_wq<F>(w, q19, tab, false).bits;
     x = __shfl_sync(FULL, x, 0);
+    MidPower mp;
+    mp.valid = false;
+    mp.e = 0;
+    mp.Eh = 0;
+    mp.X = WBig{sm.P, 0};
     auto cmp_mid = [&](uint64_t lowbits, int& c) -> bool {
-      return cmp_midpoint<F>(lowbits, sm, nD, ED, c, lane);
+      return cmp_midpoint<F>(lowbits, sm, nD, ED, c, lane, mp);
     };
     for (int iter = 0; iter < 8; iter++) {
       int c;
@@ -577,7 +641,7 @@ __device__ void resolve(const LaunchParams& p, unsigned long long oi, WarpSmem& 
 }
 
 template <class F>
-__global__ void __launch_bounds__(FB_NT, 4) fallback_kernel(const LaunchParams p) {
+__global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p) {
   __shared__ WarpSmem smem[FB_WARPS];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   WarpSmem& sm = smem[wib];
