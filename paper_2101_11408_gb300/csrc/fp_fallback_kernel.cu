@@ -526,23 +526,28 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
   const long long q19 = E + (nsig - n19);
   const uint64_t* t = reinterpret_cast<const uint64_t*>(fp_pow5_table_dev);
   const Pow5 tab{t, 2, t + 1};
-  uint64_t abits = 0;
+  uint64_t abits = 0, bbits = EL_ABORT;
   int settled = 0;
   if (lane == 0) {
     const ElResult a = convert_wq<F>(w, q19, tab, true);
     abits = a.bits;
     if (a.bits != EL_ABORT) {
-      if (nsig <= 19) settled = 1;
-      else settled = convert_wq<F>(w + 1, q19, tab, true).bits == a.bits;
+      if (nsig <= 19) {
+        settled = 1;
+      } else {
+        bbits = convert_wq<F>(w + 1, q19, tab, true).bits;
+        settled = bbits == a.bits;
+      }
     }
   }
   settled = __shfl_sync(FULL, settled, 0);
+  abits = __shfl_sync(FULL, abits, 0);
   if (settled) {
-    abits = __shfl_sync(FULL, abits, 0);
     r.bits = abits | sign;
     r.status = status_of<F>(abits);
     return r;
   }
+  bbits = __shfl_sync(FULL, bbits, 0);
   // ---- exact comparison with midpoints, in decimal --------------------------
   r.bignum = 1;
   {
@@ -554,10 +559,6 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
       nD += 1;
       ED -= 1;
     }
-    // the candidate
-    uint64_t x = 0;
-    if (lane == 0) x = convert_wq<F>(w, q19, tab, false).bits;
-    x = __shfl_sync(FULL, x, 0);
     MidPower mp;
     mp.valid = false;
     mp.e = 0;
@@ -566,6 +567,21 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     auto cmp_mid = [&](uint64_t lowbits, int& c) -> bool {
       return cmp_midpoint<F>(lowbits, sm, nD, ED, c, lane, mp);
     };
+    uint64_t x = 0;
+    if (abits != EL_ABORT && bbits != EL_ABORT && bbits == abits + 1) {
+      // V lies in [w, w+1) 10^q19, whose products round to abits and
+      // abits + 1 (Algorithm 1 is exact on them): that interval, of relative
+      // width at most 10^-18, holds one midpoint, the one above abits, and
+      // one comparison with it decides
+      int c;
+      if (!cmp_mid(abits, c)) goto fail;
+      x = c > 0 ? abits + 1 : (c < 0 ? abits : ((abits & 1) ? abits + 1 : abits));
+      goto done;
+    }
+    // the candidate (Algorithm 1 gave up on w or w + 1): the rounded
+    // truncated product, within one unit of the answer, stepped below
+    if (lane == 0) x = convert_wq<F>(w, q19, tab, false).bits;
+    x = __shfl_sync(FULL, x, 0);
     for (int iter = 0; iter < 8; iter++) {
       int c;
       if (x < F::INF) {
