@@ -7,9 +7,11 @@
 // when its 19-digit truncation w and w+1 round differently (Section 11).
 //
 // One warp per field, all lanes on the same field:
-//   1. tokenize the whole field with 32-byte coalesced reads and ballots
-//      (Section 4 grammar, or the JSON one): its end, sign, significand,
-//      point, exponent; its significant digits go to shared memory;
+//   1. tokenize the whole field (Section 4 grammar, or the JSON one): its end
+//      from aligned 16-byte reads, 512 bytes per round; then one pass of
+//      byte ballots, 32 bytes per round, for the sign, point, digits and
+//      exponent marker, which also writes the significant digits to shared
+//      memory;
 //   2. Algorithm 1 on the 19-digit prefix w and on w+1 (one lane); equal
 //      results settle the field;
 //   3. otherwise V = D 10^E with D the first 800 significant digits and one
@@ -17,10 +19,13 @@
 //      Every midpoint between adjacent floating-point values has at most
 //      768 significant digits (Section 11), so V and the exact value lie on
 //      the same side of every midpoint;
-//   4. candidate x = the rounded truncated product of the prefix (within one
-//      unit of the answer); compare V exactly with the midpoints above and
-//      below x and step x until it is the nearest value; a tie picks the
-//      even one.  A midpoint h = (2M+1) 2^(e-1) is written in base 10^9 --
+//   4. when the two results of step 2 are adjacent values, V lies between
+//      the two products and so on one side of the one midpoint between
+//      them: one exact comparison decides (a tie picks the even one).  When
+//      Algorithm 1 gave up, the candidate x = the rounded truncated product
+//      of the prefix (within one unit of the answer) is stepped by exact
+//      comparisons with the midpoints above and below it until it is the
+//      nearest value.  A midpoint h = (2M+1) 2^(e-1) is written in base 10^9 --
 //      (2M+1) 2^(e-1), or (2M+1) 5^(1-e) 10^(e-1) -- from a table power, a
 //      small power and the factor 2M+1, and compared with V's digits
 //      regrouped into the same base-10^9 chunks.
@@ -417,10 +422,16 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     return h;
   }
   // ---- structure: the exponent marker, the point, the digits ---------------
+  // One pass over [s, the marker): the digits from the first nonzero one on
+  // go to shared memory in order (the point skipped), ranked by ballots;
+  // the last nonzero digit's rank gives the significant digits, the digits
+  // stored after it are the trailing zeros, and the digits after the point
+  // are counted on the way.
   long long ep = p1;  // first 'e' / 'E' in [s, p1)
   long long dp = -1;  // the point
   long long ndot = 0, nbad = 0, ndig = 0;
-  long long fz = -1, lz = -1;  // first and last nonzero digit of the significand
+  long long fz = -1;                       // first nonzero digit of the significand
+  long long nst = 0, nsig = 0, n_frac = 0;  // digits stored; up to the last nonzero one; after the point
   for (long long base = s; base < p1; base += 32) {
     const long long i = base + lane;
     const bool in = i < p1;
@@ -437,9 +448,18 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
       ndot += __popc(dots);
       if (dp < 0) dp = base + __ffs(dots) - 1;
     }
-    if (nz) {
-      if (fz < 0) fz = base + __ffs(nz) - 1;
-      lz = base + 31 - __clz(nz);
+    if (dp >= 0) {  // digits after the point (it may lie in this round)
+      const long long k = dp - base;  // the point's lane, or below 0
+      n_frac += __popc(k < 0 ? digs : (k >= 31 ? 0u : digs & (FULL << (k + 1))));
+    }
+    if (fz < 0 && nz) fz = base + __ffs(nz) - 1;
+    if (fz >= 0) {
+      const long long k = fz - base;  // lanes from fz on
+      const uint32_t st = k <= 0 ? digs : digs & (FULL << k);
+      const long long rank = nst + __popc(st & lt_mask);
+      if (((st >> lane) & 1u) && rank < KMAX) sm.dig[rank] = (uint8_t)(c - '0');
+      if (nz) nsig = nst + __popc(st & (FULL >> __clz(nz)));  // through the last nonzero digit
+      nst += __popc(st);
     }
     if (E) {
       ep = base + __ffs(E) - 1;
@@ -489,23 +509,8 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     r.status = ST_OK;
     return r;
   }
-  // ---- significant digits to shared memory; the decimal exponent E ---------
-  // the digits of [fz, lz] (the point skipped) in order; n_frac: digits after
-  // the point; tz: the (zero) digits after lz
-  long long nsig = 0, n_frac = 0, tz = 0;
-  for (long long base = fz; base < ep; base += 32) {
-    const long long i = base + lane;
-    const uint32_t c = i < ep ? f[i] : '.';
-    const bool dg = is_digit(c);
-    const uint32_t sigm = __ballot_sync(FULL, dg && i <= lz);
-    const long long rank = nsig + __popc(sigm & lt_mask);
-    if (dg && i <= lz && rank < KMAX) sm.dig[rank] = (uint8_t)(c - '0');
-    nsig += __popc(sigm);
-    tz += __popc(__ballot_sync(FULL, dg && i > lz));
-    if (dp >= 0) n_frac += __popc(__ballot_sync(FULL, dg && i > dp));
-  }
-  // zeros between the point and fz are fraction digits too
-  if (dp >= 0 && dp < fz) n_frac += fz - dp - 1;
+  // ---- the decimal exponent E ----------------------------------------------
+  const long long tz = nst - nsig;  // the zero digits after the last nonzero one
   __syncwarp();
   const long long E = ex - n_frac + tz;  // value = (digits fz..lz) * 10^E
   // ---- quick exits: 10^(nsig-1+E) <= V < 10^(nsig+E) ----------------------
