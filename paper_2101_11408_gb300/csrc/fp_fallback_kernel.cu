@@ -51,6 +51,12 @@ __device__ const uint32_t dec5_limbs[FP_DEC5_LIMBS] = {FP_DEC5_VALUES};
 __device__ const uint32_t dec2_off[FP_DEC2_COUNT + 1] = {FP_DEC2_OFF_VALUES};
 __device__ const uint32_t dec2_limbs[FP_DEC2_LIMBS] = {FP_DEC2_VALUES};
 constexpr uint32_t DBASE = FP_DEC_BASE;
+// 10^k, k < 19
+__device__ const unsigned long long kPow10[19] = {
+    1ull, 10ull, 100ull, 1000ull, 10000ull, 100000ull, 1000000ull, 10000000ull, 100000000ull,
+    1000000000ull, 10000000000ull, 100000000000ull, 1000000000000ull, 10000000000000ull,
+    100000000000000ull, 1000000000000000ull, 10000000000000000ull, 100000000000000000ull,
+    1000000000000000000ull};
 
 constexpr int FB_WARPS = 4;           // warps per block
 constexpr int FB_NT = 32 * FB_WARPS;  // threads per block
@@ -526,33 +532,25 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
   }
   // ---- 19-digit prefix: Algorithm 1, then the w / w+1 check (one lane) ----
   const int n19 = nsig < 19 ? (int)nsig : 19;
-  uint64_t w = 0;
-  for (int k = 0; k < n19; k++) w = w * 10 + sm.dig[k];
+  // w = the first n19 digits: lane k < n19 weighs digit k by 10^(n19-1-k),
+  // and a butterfly adds the terms
+  uint64_t w = lane < n19 ? (uint64_t)sm.dig[lane] * kPow10[n19 - 1 - lane] : 0ull;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(FULL, w, off);
   const long long q19 = E + (nsig - n19);
   const uint64_t* t = reinterpret_cast<const uint64_t*>(fp_pow5_table_dev);
   const Pow5 tab{t, 2, t + 1};
-  uint64_t abits = 0, bbits = EL_ABORT;
-  int settled = 0;
-  if (lane == 0) {
-    const ElResult a = convert_wq<F>(w, q19, tab, true);
-    abits = a.bits;
-    if (a.bits != EL_ABORT) {
-      if (nsig <= 19) {
-        settled = 1;
-      } else {
-        bbits = convert_wq<F>(w + 1, q19, tab, true).bits;
-        settled = bbits == a.bits;
-      }
-    }
-  }
-  settled = __shfl_sync(FULL, settled, 0);
-  abits = __shfl_sync(FULL, abits, 0);
+  // Algorithm 1 on w (lane 0) and, for more than 19 digits, on w + 1 (lane 1)
+  uint64_t mine = EL_ABORT;
+  if (lane == 0 || (lane == 1 && nsig > 19)) mine = convert_wq<F>(w + lane, q19, tab, true).bits;
+  const uint64_t abits = __shfl_sync(FULL, mine, 0);
+  const uint64_t bbits = __shfl_sync(FULL, mine, 1);
+  const bool settled = abits != EL_ABORT && (nsig <= 19 || bbits == abits);
   if (settled) {
     r.bits = abits | sign;
     r.status = status_of<F>(abits);
     return r;
   }
-  bbits = __shfl_sync(FULL, bbits, 0);
   // ---- exact comparison with midpoints, in decimal --------------------------
   r.bignum = 1;
   {
