@@ -501,10 +501,15 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     }
     if (nondig) return invalid();
     if (nonzero0 >= 0) {
-      if (p1 - nonzero0 > 16) {
+      const long long ne = p1 - nonzero0;  // digits from the first nonzero one
+      if (ne > 16) {
         ex = EXP_SAT;  // at least 10^16
       } else {
-        for (long long i = nonzero0; i < p1; i++) ex = ex * 10 + (f[i] - '0');
+        // lane k < ne weighs digit k by 10^(ne-1-k); a butterfly adds them
+        uint64_t term = lane < ne ? (uint64_t)(f[nonzero0 + lane] - '0') * kPow10[ne - 1 - lane] : 0ull;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) term += __shfl_xor_sync(FULL, term, off);
+        ex = (long long)term;
         if (ex > EXP_SAT) ex = EXP_SAT;
       }
     }
