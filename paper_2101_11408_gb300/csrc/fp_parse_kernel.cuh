@@ -58,8 +58,9 @@ struct Layout {
   static constexpr int OFF_TABLE = 0;
   static constexpr int OFF_TILE = (TABLE_BYTES + 127) / 128 * 128;
   static constexpr int OFF_S = OFF_TILE + NSTAGE * TILE_ALLOC;
-  static constexpr int S_BYTES = ((S_CAP + 2) * 2 + 15) / 16 * 16;
-  static constexpr int OFF_STAGE_BITS = OFF_S + S_BYTES;
+  static constexpr int S_BYTES = ((S_CAP + 2) * 2 + 15) / 16 * 16;  // one list of field starts
+  static constexpr int S_STRIDE = S_BYTES / 2;                       // in uint16 entries
+  static constexpr int OFF_STAGE_BITS = OFF_S + 2 * S_BYTES;         // two lists
   static constexpr int OFF_STAGE_ST = OFF_STAGE_BITS + STAGE * 8;
   static constexpr int OFF_MISC = OFF_STAGE_ST + STAGE;
   static constexpr int MISC_BYTES = 1024;
@@ -81,7 +82,7 @@ struct Misc {
   unsigned long long lb_part[NT / 32];
   int last_start[NSTAGE];  // tile offset of the last field start of each staged chunk
   unsigned long long cnt[CNT_NUM];
-  unsigned int group;  // next group of 32 fields of the window to parse
+  unsigned int group[2];  // next group of 32 fields to parse, per list of field starts
 };
 static_assert(sizeof(Misc) <= 1024, "misc");
 
@@ -292,7 +293,11 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     MaskT mask;  // bit i: a field starts at byte i+1 of this thread's granules
     uint32_t pad_bit, rank0, n;
   };
-  auto count_chunk = [&](int b, Counted& cn) {
+  // When the chunk fits one window, the field starts are listed into Sx
+  // right away (and Sx[n] = one past the last field's terminator), and
+  // group counter gs is reset: the chunk's parse, an iteration later, then
+  // needs no barrier of its own.
+  auto count_chunk = [&](int b, Counted& cn, uint16_t* Sx, int gs) {
     const uint8_t* tile = tiles + b * L::TILE_ALLOC;
     const BufDesc& d = ms->desc[b];
     const unsigned long long g = ms->chunk[b];
@@ -367,23 +372,57 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       st_relaxed_u64(&p.chunk_status[g], lb_word(p.epoch, lc == 0 ? LB_FLAG_INC : LB_FLAG_AGG, n));
     // the thread holding the chunk's last field start records it, for the
     // scan that finds where that field ends
+    int last = -1;
     if (cnt && wpre + incl == n) {
       const int hb = mask ? (int)(8 * sizeof(MaskT)) - 1 -
                                 ((sizeof(MaskT) == 8) ? __clzll((long long)mask) : __clz((uint32_t)mask))
                           : -1;
-      ms->last_start[b] = hb >= 0 ? PAD + 16 * tid * L::SEG_PER_THREAD + hb + 1 : PAD;
+      last = hb >= 0 ? PAD + 16 * tid * L::SEG_PER_THREAD + hb + 1 : PAD;
+      ms->last_start[b] = last;
+    }
+    if (n <= (uint32_t)L::S_CAP) {
+      uint32_t rank = cn.rank0;
+      if (cn.pad_bit) Sx[rank++] = PAD;
+      const int base_off = PAD + 16 * tid * L::SEG_PER_THREAD + 1;
+      MaskT m = mask;
+      while (m) {
+        const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
+        Sx[rank++] = (uint16_t)(base_off + bpos);
+        m &= m - 1;
+      }
+      if (last >= 0) {
+        // the last field ends at the first separator after its start, at the
+        // end of the text, or (if neither is staged) it is long
+        const long long vend = endx - (c0 - PAD);
+        const int lim = vend < L::TILE ? (int)vend : L::TILE;
+        int term = last + 128;
+        const int w0 = last & ~3;
+        for (int wb = w0; wb < w0 + 128; wb += 4) {
+          const uint32_t wv = *reinterpret_cast<const uint32_t*>(tile + wb);
+          uint32_t f = one_sep ? zero_bytes(wv ^ NLW) : (zero_bytes(wv ^ NLW) | zero_bytes(wv ^ DLW));
+          if (wb == w0) f &= 0xFFFFFFFFu << (8 * (last & 3));
+          if (f) {
+            term = wb + (ctz32(f) >> 3);
+            break;
+          }
+        }
+        if (term > lim) term = lim;
+        Sx[n] = (uint16_t)(term + 1);
+      }
+      if (tid == 0) ms->group[gs] = 0;
     }
     // (warp_sum is next written after at least one more barrier)
   };
 
   Counted cur, nxt;
   int buf = 0;
+  int sset = 0;  // list of field starts of the current chunk
   // this block's previous chunk and the inclusive prefix after it
   long long prev_g = -1;
   unsigned long long prev_inc = 0;
   if (ms->chunk[0] < p.total_chunks) {
     wait_buf(0);
-    count_chunk(0, cur);
+    count_chunk(0, cur, S, 0);
   }
   __syncthreads();
 
@@ -400,7 +439,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     // field count is public long before any later chunk looks back at it.
     if (ms->chunk[b1] < p.total_chunks) {
       wait_buf(b1);
-      count_chunk(b1, nxt);
+      count_chunk(b1, nxt, S + (sset ^ 1) * L::S_STRIDE, sset ^ 1);
     }
     if (tid == 0) {
       // stage the ticketed chunk into the buffer that the previous iteration
@@ -513,53 +552,49 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       }
     };
 
+    // The chunk's list of field starts: listed when the chunk was counted if
+    // it fits one window (visible since the barrier that ended the previous
+    // iteration), else window by window below.
+    uint16_t* Sw = S + sset * L::S_STRIDE;
+    const bool one_window = n <= (uint32_t)L::S_CAP;
     for (uint32_t lo = 0;; lo += L::S_CAP) {
       const uint32_t hi = min(lo + (uint32_t)L::S_CAP, n);
-      // list the starts of fields lo..hi (hi included: it ends field hi-1)
-      {
+      if (!one_window) {
+        // list the starts of fields lo..hi (hi included: it ends field hi-1)
         uint32_t rank = cur.rank0;
         const int base_off = PAD + 16 * tid * L::SEG_PER_THREAD + 1;
         MaskT m = cur.mask;
-        if (n <= (uint32_t)L::S_CAP) {  // one window: every start is listed
-          if (cur.pad_bit) S[rank++] = PAD;
-          while (m) {
-            const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
-            S[rank++] = (uint16_t)(base_off + bpos);
-            m &= m - 1;
-          }
-        } else {
-          if (cur.pad_bit) {
-            if (rank >= lo && rank <= hi) S[rank - lo] = PAD;
-            rank++;
-          }
-          while (m) {
-            const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
-            if (rank >= lo && rank <= hi) S[rank - lo] = (uint16_t)(base_off + bpos);
-            rank++;
-            m &= m - 1;
-          }
+        if (cur.pad_bit) {
+          if (rank >= lo && rank <= hi) Sw[rank - lo] = PAD;
+          rank++;
         }
-      }
-      if (tid == 0) ms->group = 0;
-      if (hi == n && n > lo && warp == 0) {
-        // the last field ends at the first separator after its start, at the
-        // end of the text, or (if neither is staged) it is long
-        const int st = ms->last_start[buf];
-        const int wb = (st & ~3) + 4 * lane;
-        const uint32_t wv = *reinterpret_cast<const uint32_t*>(tile + wb);
-        uint32_t f = one_sep ? zero_bytes(wv ^ NLW) : (zero_bytes(wv ^ NLW) | zero_bytes(wv ^ DLW));
-        if (lane == 0) f &= 0xFFFFFFFFu << (8 * (st & 3));
-        const unsigned int hit = __ballot_sync(0xFFFFFFFFu, f != 0);
-        int term = st + 128;
-        if (hit) {
-          const int l = __ffs(hit) - 1;
-          const uint32_t fl = __shfl_sync(0xFFFFFFFFu, f, l);
-          term = (st & ~3) + 4 * l + (ctz32(fl) >> 3);
+        while (m) {
+          const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
+          if (rank >= lo && rank <= hi) Sw[rank - lo] = (uint16_t)(base_off + bpos);
+          rank++;
+          m &= m - 1;
         }
-        if (term > limit) term = limit;
-        if (lane == 0) S[n - lo] = (uint16_t)(term + 1);
+        if (tid == 0) ms->group[sset] = 0;
+        if (hi == n && n > lo && warp == 0) {
+          // the last field ends at the first separator after its start, at the
+          // end of the text, or (if neither is staged) it is long
+          const int st = ms->last_start[buf];
+          const int wb = (st & ~3) + 4 * lane;
+          const uint32_t wv = *reinterpret_cast<const uint32_t*>(tile + wb);
+          uint32_t f = one_sep ? zero_bytes(wv ^ NLW) : (zero_bytes(wv ^ NLW) | zero_bytes(wv ^ DLW));
+          if (lane == 0) f &= 0xFFFFFFFFu << (8 * (st & 3));
+          const unsigned int hit = __ballot_sync(0xFFFFFFFFu, f != 0);
+          int term = st + 128;
+          if (hit) {
+            const int l = __ffs(hit) - 1;
+            const uint32_t fl = __shfl_sync(0xFFFFFFFFu, f, l);
+            term = (st & ~3) + 4 * l + (ctz32(fl) >> 3);
+          }
+          if (term > limit) term = limit;
+          if (lane == 0) Sw[n - lo] = (uint16_t)(term + 1);
+        }
+        __syncthreads();  // S ready
       }
-      __syncthreads();  // S ready
       if (lo == 0 && warp == 0) {
         // the prefix, while the other warps parse; published at once
         const unsigned long long b =
@@ -580,14 +615,14 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       uint32_t general = 0;  // this warp's groups with a field for the general tokenizer
       for (;;) {
         uint32_t gi = 0;
-        if (lane == 0) gi = atomicAdd(&ms->group, 1u);
+        if (lane == 0) gi = atomicAdd(&ms->group[sset], 1u);
         gi = __shfl_sync(0xFFFFFFFFu, gi, 0);
         if (gi >= ngroups) break;
         const uint32_t k = 32 * gi + lane;
         uint8_t status = ST_OK;
         if (k < cntw) {
           unsigned long long bits;
-          parse_hot(S[k], S[k + 1] - 1, bits, status);
+          parse_hot(Sw[k], Sw[k + 1] - 1, bits, status);
           stage_bits[k] = bits;
           stage_st[k] = status;
         }
@@ -597,7 +632,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         const uint32_t k = 32 * (__ffs(general) - 1) + lane;
         general &= general - 1;
         if (k < cntw && stage_st[k] == ST_GENERAL)
-          parse_general(S[k], S[k + 1] - 1, stage_bits[k], stage_st[k]);
+          parse_general(Sw[k], Sw[k + 1] - 1, stage_bits[k], stage_st[k]);
       }
       // stores: each warp a contiguous, equal share of the window
       const uint32_t share = (cntw + NT / 32 - 1) / (NT / 32);
@@ -610,7 +645,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         os = p.out_status + d.out_base + base;
       }
       for (uint32_t k = warp * share + lane; k < k_end; k += 32)
-        store_one(lo + k, stage_bits[k], stage_st[k], (int)S[k + 1] - 1);
+        store_one(lo + k, stage_bits[k], stage_st[k], (int)Sw[k + 1] - 1);
       if (hi >= n) break;
       __syncthreads();  // S and the staged results are rewritten for the next window
     }
@@ -633,6 +668,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     prev_inc = base + n;
     cur = nxt;
     buf = b1;
+    sset ^= 1;
   }
 
   // ---- counters and end-of-launch reset ---------------------------------
