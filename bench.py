@@ -784,6 +784,14 @@ def run_serve(args, world, rank, dist) -> None:
                                ("service", "launch_ns", "done_ns")):
                 d = [inf[b] - (arrival[i] if a is None else inf[a]) for i, inf in enumerate(infos)]
                 parts[name] = {"p50_ms": _percentile_ms(d, 50), "p99_ms": _percentile_ms(d, 99)}
+            # latency by request size: below 1 MB and from 1 MB on
+            for name, pick in (("below_1MB", lambda j: lens[j] < (1 << 20)),
+                               ("from_1MB", lambda j: lens[j] >= (1 << 20))):
+                d = [lat_i for lat_i, j in zip((inf["done_ns"] - arrival[i]
+                                               for i, inf in enumerate(infos)), order) if pick(int(j))]
+                if d:
+                    parts[name] = {"requests": len(d), "p50_ms": _percentile_ms(d, 50),
+                                   "p99_ms": _percentile_ms(d, 99)}
         span = max(inf["done_ns"] for inf in infos) - t0
         return lat, span, [inf["batch_size"] for inf in infos]
 
