@@ -729,8 +729,6 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
 
 }  // namespace
 
-int fallback_smem_bytes() { return 0; }  // static shared memory only
-
 template <class F>
 static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream) {
   fallback_kernel<F><<<grid, FB_NT, 0, stream>>>(p);

@@ -10,7 +10,6 @@ namespace fp {
 // else binary64 (8-byte values; p.loc == p.out_bits).
 cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream,
                          bool f32 = false);
-int parse_smem_bytes(int chunk_bytes);
 // The JSON / column-major modes (mode: MODE_* bits of fp_parse_kernel.cuh,
 // nonzero), for 8 KiB and 16 KiB chunks; the occupancy of the most
 // demanding of those instances.
@@ -20,7 +19,6 @@ cudaError_t parse_occupancy_ext(int chunk_bytes, int* blocks_per_sm);
 cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm, bool f32 = false);
 
 cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32 = false);
-int fallback_smem_bytes();
 cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32 = false);
 
 }  // namespace fp

@@ -39,16 +39,6 @@ cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaS
              : launch_parse_f<F64>(p, chunk_bytes, grid, stream);
 }
 
-int parse_smem_bytes(int chunk_bytes) {
-  switch (chunk_bytes) {
-    case 4096: return Layout<4096>::TOTAL;
-    case 8192: return Layout<8192>::TOTAL;
-    case 12288: return Layout<12288>::TOTAL;
-    case 16384: return Layout<16384>::TOTAL;
-    default: return -1;
-  }
-}
-
 template <int C, class F>
 static cudaError_t occupancy_c(int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(parse_kernel<C, F, 0>,
