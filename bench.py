@@ -581,40 +581,46 @@ def run_batch(args, world, rank, dist) -> None:
     ms_per = _time_steps(torch, stream, per_buffer, few, 3)
     wall_per = (time.perf_counter() - t0) / (few + 3) * 1e3
 
-    # end to end: packed host text -> device, graph replay, counts and exact
-    # results per buffer -> host, every step
+    # end to end: packed host text -> device, graph replay, the results
+    # packed in buffer order on the device (fp_batch_plan_gather), their
+    # total and then exactly that many results -> host, every step
     e2e = None
     if not args.skip_e2e:
         h_out = torch.empty(N, dtype=torch.float64).pin_memory()
         h_st = torch.empty(N, dtype=torch.uint8).pin_memory()
-        h_cnt = torch.empty(len(texts), dtype=torch.int64).pin_memory()
-        dst = [0]
-        for c in counts:
-            dst.append(dst[-1] + c)
+        d_pv = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
+        d_ps = torch.empty(max(N, 1), dtype=torch.uint8, device=dev)
+        d_tot = torch.empty(1, dtype=torch.int64, device=dev)
+        h_tot = torch.empty(1, dtype=torch.int64).pin_memory()
 
         def e2e_step():
             d_packed.copy_(h_packed, non_blocking=True)
             plan_g.launch(stream)
-            h_cnt.copy_(cnt, non_blocking=True)
+            plan_g.gather(d_pv, d_ps, d_tot, stream)
+            h_tot.copy_(d_tot, non_blocking=True)
             stream.synchronize()
-            cs = h_cnt.tolist()
-            for b in range(len(texts)):
-                if cs[b]:
-                    h_out[dst[b]:dst[b] + cs[b]].copy_(out[offs[b]:offs[b] + cs[b]], non_blocking=True)
-                    h_st[dst[b]:dst[b] + cs[b]].copy_(st[offs[b]:offs[b] + cs[b]], non_blocking=True)
+            n = int(h_tot[0])
+            h_out[:n].copy_(d_pv[:n], non_blocking=True)
+            h_st[:n].copy_(d_ps[:n], non_blocking=True)
             stream.synchronize()
+            return n
 
         for _ in range(3):
             e2e_step()
         steps = min(args.steps, args.e2e_steps)
         t0 = time.perf_counter()
         for _ in range(steps):
-            e2e_step()
+            n_e2e = e2e_step()
         dt = (time.perf_counter() - t0) / steps
+        # the packed results are the buffers' results one after the other
+        packed_ref = torch.cat([out[offs[b]:offs[b] + counts[b]] for b in range(len(texts))])
+        if n_e2e != N or not torch.equal(d_pv[:N].view(torch.int64), packed_ref.view(torch.int64)):
+            raise SystemExit("bench: packed batch results differ from the per-buffer ones")
         e2e = {"value": world * B / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(packed.size),
-               "d2h_bytes_per_step": 9 * N + 8 * len(texts), "steps": steps,
+               "d2h_bytes_per_step": 9 * N + 8, "steps": steps,
                "api": "one host->device copy of the packed buffers, fp_batch_plan_launch (graph), "
-                      "one copy of the counts, then exact per-buffer result copies"}
+                      "fp_batch_plan_gather (results packed in buffer order on the device), then "
+                      "one copy of the total and two of exactly that many results"}
     if rank != 0:
         return
     peak, peak_kind = measured_hbm_peak()

@@ -268,6 +268,20 @@ class BatchPlan:
         _lib.check(_lib.load().fp_batch_plan_launch(self._h, _stream_handle(stream)),
                    "fp_batch_plan_launch")
 
+    def gather(self, dst_f64: torch.Tensor, dst_status: torch.Tensor, dst_total: torch.Tensor,
+               stream=None) -> None:
+        """Pack the last launch's results in buffer order into dst_f64 /
+        dst_status (float64 / uint8 device tensors) and their number into
+        dst_total (one int64 device element), on the stream, without
+        synchronising (fp_batch_plan_gather)."""
+        for t, dt in ((dst_f64, torch.float64), (dst_status, torch.uint8), (dst_total, torch.int64)):
+            if t.device.type != "cuda" or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("gather targets are contiguous device tensors")
+        _lib.check(_lib.load().fp_batch_plan_gather(self._h, dst_f64.data_ptr(),
+                                                    dst_status.data_ptr(), dst_total.data_ptr(),
+                                                    _stream_handle(stream)),
+                   "fp_batch_plan_gather")
+
     def close(self) -> None:
         if self._h:
             _lib.load().fp_batch_plan_destroy(self._h)

@@ -21,7 +21,8 @@ GRAMMAR_DECIMAL, GRAMMAR_HEX, GRAMMAR_JSON = 0, 1, 2
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_ex", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
            "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
-           "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_server_create", "fp_server_submit",
+           "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_batch_plan_gather",
+           "fp_server_create", "fp_server_submit",
            "fp_server_wait", "fp_server_get_stats", "fp_server_destroy", "fp_shutdown",
            "fp_strerror"]
 
@@ -135,6 +136,8 @@ def load(build_if_missing: bool = True):
         lib.fp_batch_plan_launch.restype = ctypes.c_int
         lib.fp_batch_plan_destroy.argtypes = [vp]
         lib.fp_batch_plan_destroy.restype = ctypes.c_int
+        lib.fp_batch_plan_gather.argtypes = [vp, vp, u8p, vp, vp]
+        lib.fp_batch_plan_gather.restype = ctypes.c_int
         lib.fp_server_create.argtypes = [ctypes.POINTER(ServerConfig),
                                          ctypes.POINTER(ctypes.c_void_p)]
         lib.fp_server_create.restype = ctypes.c_int

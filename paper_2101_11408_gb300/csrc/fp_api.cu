@@ -15,6 +15,7 @@
 #include "../../include/fpparse.h"
 #include "fp_device.cuh"
 #include "fp_internal.h"
+#include "fp_copy.h"
 #include "fp_launch.h"
 #include "fp_types.cuh"
 
@@ -1086,6 +1087,14 @@ struct fp_batch_plan {
   size_t scratch_bytes;            // bytes cleared before each launch (ctl + look-back words)
   int grid_parse, grid_fallback;
   cudaGraphExec_t graph;           // the captured launch sequence, or null
+  // packing of the results (fp_batch_plan_gather)
+  const unsigned long long* counts;  // the caller's out_counts (device)
+  void* pack;                      // one allocation: bases[nbuf], starts[nbuf + 1], pieces
+  const unsigned long long* bases;
+  unsigned long long* starts;
+  const unsigned long long* pieces;
+  unsigned long long npieces;
+  int grid_pack;
 };
 
 namespace {
@@ -1202,9 +1211,40 @@ extern "C" fp_err_t fp_batch_plan_create(const char* const* texts, const size_t*
   pl->grid_parse = (int)(grid > c ? c : grid);
   pl->grid_fallback = di->sms * di->fb_occ;
   pl->graph = nullptr;
+  // the packing pieces: each buffer's output range cut into PACK_PIECE fields
+  {
+    std::vector<unsigned long long> pk;
+    for (uint32_t b = 0; b < nbuf; b++)
+      for (unsigned long long f0 = 0; f0 < out_offsets[b + 1] - out_offsets[b]; f0 += fp::PACK_PIECE)
+        pk.push_back(((unsigned long long)b << 40) | f0);
+    pl->npieces = pk.size();
+    const size_t n_words = (size_t)nbuf + (nbuf + 1) + pk.size();
+    if (cudaMalloc(&pl->pack, n_words * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaFree(pl->dmem);
+      delete pl;
+      return FP_ERR_CUDA;
+    }
+    unsigned long long* w = static_cast<unsigned long long*>(pl->pack);
+    pl->bases = w;
+    pl->starts = w + nbuf;
+    pl->pieces = w + nbuf + nbuf + 1;
+    std::vector<unsigned long long> bs(out_offsets, out_offsets + nbuf);
+    if (cudaMemcpy(w, bs.data(), nbuf * sizeof(unsigned long long), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        (!pk.empty() && cudaMemcpy(w + 2 * nbuf + 1, pk.data(), pk.size() * sizeof(unsigned long long),
+                                   cudaMemcpyHostToDevice) != cudaSuccess)) {
+      cudaFree(pl->pack);
+      cudaFree(pl->dmem);
+      delete pl;
+      return FP_ERR_CUDA;
+    }
+    pl->counts = reinterpret_cast<const unsigned long long*>(out_counts);
+    pl->grid_pack = di->sms * 8;
+  }
   if (flags & FP_PLAN_GRAPH) {
     fp_err_t e = plan_capture(pl);
     if (e != FP_OK) {
+      cudaFree(pl->pack);
       cudaFree(pl->dmem);
       delete pl;
       return e;
@@ -1224,6 +1264,20 @@ extern "C" fp_err_t fp_batch_plan_launch(fp_batch_plan* pl, struct CUstream_st* 
   return plan_enqueue(pl, stream);
 }
 
+extern "C" fp_err_t fp_batch_plan_gather(fp_batch_plan* pl, double* dst_f64, uint8_t* dst_status,
+                                         uint64_t* dst_total, struct CUstream_st* stream_) {
+  if (!pl) return FP_ERR_ARG;
+  if (pl->npieces && (!dst_f64 || !dst_status)) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  FP_CUDA(fp::launch_pack_scan(pl->counts, pl->p.nbuf, pl->starts,
+                               reinterpret_cast<unsigned long long*>(dst_total), stream));
+  FP_CUDA(fp::launch_pack_copy(pl->pieces, pl->npieces, pl->counts, pl->bases, pl->starts,
+                               pl->p.out_bits, pl->p.out_status,
+                               reinterpret_cast<unsigned long long*>(dst_f64), dst_status,
+                               pl->grid_pack, stream));
+  return FP_OK;
+}
+
 extern "C" fp_err_t fp_batch_plan_destroy(fp_batch_plan* pl) {
   if (!pl) return FP_OK;
   int prev = -1;
@@ -1231,6 +1285,7 @@ extern "C" fp_err_t fp_batch_plan_destroy(fp_batch_plan* pl) {
   cudaSetDevice(pl->device);
   cudaDeviceSynchronize();
   if (pl->graph) cudaGraphExecDestroy(pl->graph);
+  cudaFree(pl->pack);
   cudaFree(pl->dmem);
   if (prev >= 0) cudaSetDevice(prev);
   delete pl;

@@ -1,4 +1,5 @@
-// fp_copy.h -- the request server's copy kernels (fp_copy_kernel.cu).
+// fp_copy.h -- copy kernels (fp_copy_kernel.cu): the request server's
+// gather and scatter, and the packing of a batch's results.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -33,6 +34,22 @@ struct ScatterPiece {
   unsigned long long first;
 };
 constexpr uint32_t SCATTER_PIECE = 32768;  // fields per piece at most
+
+// Packing of a batch's results: buffer b's count_b results, at output index
+// base_b, go to dst at the sum of the earlier buffers' counts.  A piece is
+// (b << 40) | f0: fields [f0, f0 + PACK_PIECE) of buffer b's capacity.
+constexpr uint32_t PACK_PIECE = 8192;  // fields per piece at most
+// starts[b] = sum of counts[b'] for b' < b (b <= nbuf; starts[nbuf] is the
+// total, also written to *total when total is not null); one block.
+cudaError_t launch_pack_scan(const unsigned long long* counts, uint32_t nbuf,
+                             unsigned long long* starts, unsigned long long* total,
+                             cudaStream_t stream);
+cudaError_t launch_pack_copy(const unsigned long long* pieces, unsigned long long npieces,
+                             const unsigned long long* counts,
+                             const unsigned long long* bases, const unsigned long long* starts,
+                             const unsigned long long* src_vals, const uint8_t* src_status,
+                             unsigned long long* dst_vals, uint8_t* dst_status, int grid,
+                             cudaStream_t stream);
 
 cudaError_t launch_gather(const CopyPiece* pieces, uint32_t npieces, int grid, cudaStream_t stream);
 cudaError_t launch_scatter(const ScatterItem* items, const ScatterPiece* pieces, uint32_t npieces,

@@ -10,6 +10,10 @@
 //                   statuses, arena -> host, reading count on the device, in
 //                   pieces of at most SCATTER_PIECE fields.
 // Piece tables live in pinned host memory and are read by the kernels.
+//   pack_scan_kernel / pack_copy_kernel  a batch's results packed in buffer
+//                   order (device to device): an exclusive scan of the
+//                   per-buffer counts, then fixed-size pieces of each
+//                   buffer's output range copied to their packed place.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -67,7 +71,85 @@ __global__ void __launch_bounds__(COPY_NT) scatter_kernel(const ScatterItem* ite
   }
 }
 
+constexpr int SCAN_NT = 1024;
+
+__global__ void __launch_bounds__(SCAN_NT) pack_scan_kernel(const unsigned long long* counts,
+                                                            uint32_t nbuf,
+                                                            unsigned long long* starts,
+                                                            unsigned long long* total) {
+  __shared__ unsigned long long wsum[SCAN_NT / 32];
+  const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  // thread t sums buffers [t * per, (t + 1) * per)
+  const uint32_t per = (nbuf + SCAN_NT - 1) / SCAN_NT;
+  const uint32_t b0 = t * per, b1 = min(b0 + per, nbuf);
+  unsigned long long mine = 0;
+  for (uint32_t b = b0; b < b1; b++) mine += counts[b];
+  unsigned long long incl = mine;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  unsigned long long before = 0, all = 0;
+  for (int w = 0; w < SCAN_NT / 32; w++) {
+    before += w < (int)warp ? wsum[w] : 0ull;
+    all += wsum[w];
+  }
+  unsigned long long run = before + incl - mine;  // exclusive prefix of this thread's first buffer
+  for (uint32_t b = b0; b < b1; b++) {
+    starts[b] = run;
+    run += counts[b];
+  }
+  if (t == 0) {
+    starts[nbuf] = all;
+    if (total) *total = all;
+  }
+}
+
+__global__ void __launch_bounds__(COPY_NT) pack_copy_kernel(
+    const unsigned long long* pieces, unsigned long long npieces,
+    const unsigned long long* counts, const unsigned long long* bases,
+    const unsigned long long* starts, const unsigned long long* src_vals,
+    const uint8_t* src_status, unsigned long long* dst_vals, uint8_t* dst_status) {
+  for (unsigned long long k = blockIdx.x; k < npieces; k += gridDim.x) {
+    const unsigned long long pc = pieces[k];
+    const uint32_t b = (uint32_t)(pc >> 40);
+    const unsigned long long f0 = pc & ((1ull << 40) - 1);
+    const unsigned long long count = counts[b];
+    if (f0 >= count) continue;
+    const unsigned long long m0 = count - f0;
+    const uint32_t m = m0 < PACK_PIECE ? (uint32_t)m0 : PACK_PIECE;
+    const unsigned long long* sv = src_vals + bases[b] + f0;
+    const uint8_t* ss = src_status + bases[b] + f0;
+    unsigned long long* dv = dst_vals + starts[b] + f0;
+    uint8_t* ds = dst_status + starts[b] + f0;
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) dv[i] = sv[i];
+    for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ds[i] = ss[i];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pack_scan(const unsigned long long* counts, uint32_t nbuf,
+                             unsigned long long* starts, unsigned long long* total,
+                             cudaStream_t stream) {
+  pack_scan_kernel<<<1, SCAN_NT, 0, stream>>>(counts, nbuf, starts, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_copy(const unsigned long long* pieces, unsigned long long npieces,
+                             const unsigned long long* counts,
+                             const unsigned long long* bases, const unsigned long long* starts,
+                             const unsigned long long* src_vals, const uint8_t* src_status,
+                             unsigned long long* dst_vals, uint8_t* dst_status, int grid,
+                             cudaStream_t stream) {
+  if (npieces == 0) return cudaSuccess;
+  pack_copy_kernel<<<grid, COPY_NT, 0, stream>>>(pieces, npieces, counts, bases, starts, src_vals,
+                                                 src_status, dst_vals, dst_status);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gather(const CopyPiece* pieces, uint32_t npieces, int grid,
                           cudaStream_t stream) {

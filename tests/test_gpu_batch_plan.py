@@ -157,3 +157,39 @@ def test_plan_on_the_batched_workload_sample():
     torch.cuda.synchronize()
     check_against_oracle(texts, offs, out, st, cnt)
     plan.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_gather_packs_the_results_in_buffer_order(graph):
+    """fp_batch_plan_gather: every buffer's results, exactly its count of
+    them, in buffer order and nothing after the total -- equal to the
+    oracle's results of the buffers one after the other; empty buffers and
+    buffers larger than one packing piece (8192 fields) included."""
+    texts = mixed_texts(60, 21) + [workloads.uniform_text(20000, 22), b"",
+                                   workloads.bulk_mixed_text(30000, 23)]
+    _, views = pack_to_device(texts)
+    offs, out, st, cnt = outputs(texts)
+    plan = fp.BatchPlan(views, out, st, offs, cnt, graph=graph)
+    try:
+        cap = max(offs[-1], 1)
+        dst = torch.full((cap + 16,), -7.0, dtype=torch.float64, device="cuda")
+        dst_st = torch.full((cap + 16,), 0xAB, dtype=torch.uint8, device="cuda")
+        tot = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        want_v, want_s = [], []
+        for t in texts:
+            rb, rs = oracle.parse_buffer(t)
+            want_v.append(rb)
+            want_s.append(rs)
+        want_v = np.concatenate(want_v)
+        want_s = np.concatenate(want_s)
+        for _ in range(2):
+            plan.launch()
+            plan.gather(dst, dst_st, tot)
+            torch.cuda.synchronize()
+            n = int(tot.item())
+            assert n == want_v.size
+            assert np.array_equal(dst[:n].cpu().numpy().view(np.uint64), want_v)
+            assert np.array_equal(dst_st[:n].cpu().numpy(), want_s)
+            assert (dst[n:].cpu().numpy() == -7.0).all() and (dst_st[n:].cpu().numpy() == 0xAB).all()
+    finally:
+        plan.close()
