@@ -289,6 +289,17 @@ void fill_desc(BufDesc& d, const char* text, size_t len, unsigned long long chun
   d.out_count = reinterpret_cast<unsigned long long*>(out_count);
 }
 
+// Texts below this many bytes are parsed in 4 KiB chunks when the configured
+// chunk size is the default 16 KiB (more blocks share a small text), and
+// their fallback launch is one block per SM (its blocks only look at the
+// queue when nothing is pending).
+constexpr size_t SMALL_TEXT_BYTES = 4u << 20;
+constexpr uint32_t DEFAULT_CHUNK = 16384;
+Config text_config(Config cfg, size_t len) {
+  if (len < SMALL_TEXT_BYTES && cfg.chunk_bytes == DEFAULT_CHUNK) cfg.chunk_bytes = 4096;
+  return cfg;
+}
+
 // Queue the two kernels of one call (binary32 results when f32).
 fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& p,
              unsigned long long total_chunks, unsigned long long total_bytes, cudaStream_t stream,
@@ -325,7 +336,9 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   if (mode) FP_CUDA(fp::launch_parse_ext(p, (int)cfg.chunk_bytes, (int)grid, stream, f32, mode));
   else FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
   if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
-  FP_CUDA(fp::launch_fallback(p, di.sms * (f32 ? di.fb_occ32 : di.fb_occ), stream, f32));
+  const int fb_grid =
+      total_bytes < SMALL_TEXT_BYTES ? di.sms : di.sms * (f32 ? di.fb_occ32 : di.fb_occ);
+  FP_CUDA(fp::launch_fallback(p, fb_grid, stream, f32));
   if (timing) {
     FP_CUDA(cudaEventRecord(s->ev[slot][2], stream));
     s->ev_used[slot] = true;
@@ -506,7 +519,7 @@ fp_err_t stage_for(cudaStream_t stream, size_t len, bool results, Scratch** out)
 fp_err_t parse_one(const char* text, size_t len, char delim, double* out_f64, uint8_t* out_status,
                    size_t out_cap, uint64_t* out_count, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(g_mu);
-  const Config cfg = g_cfg;
+  const Config cfg = text_config(g_cfg, len);
   int dev = 0;
   FP_CUDA(cudaGetDevice(&dev));
   DeviceInfo* di = nullptr;
@@ -705,7 +718,7 @@ fp_err_t fp_parse_f32(const char* text, size_t len, char delim, float* out_f32,
   if (len > 0 && (!text || !out_f32 || !out_status)) return FP_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   std::lock_guard<std::mutex> lk(g_mu);
-  const Config cfg = g_cfg;
+  const Config cfg = text_config(g_cfg, len);
   int dev = 0;
   FP_CUDA(cudaGetDevice(&dev));
   DeviceInfo* di = nullptr;
