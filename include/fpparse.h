@@ -360,9 +360,11 @@ FP_API fp_err_t fp_get_error(struct CUstream_st *stream);
 /*
  * fp_set_config / fp_get_config -- launch parameters used by later calls
  * (all streams).  chunk_bytes: text bytes per work tile (4096, 8192, 12288
- * or 16384); ctas_per_sm: resident blocks per SM for the persistent grid
- * (1..8); fallback_queue: entries of the per-stream fallback queue
- * (>= 1024).  Returns FP_ERR_ARG for values outside those sets.
+ * or 16384; at the default 16384, fp_parse_f64 / fp_parse_f32 calls on
+ * texts below 4 MB use 4096, so that more blocks share a small text);
+ * ctas_per_sm: resident blocks per SM for the persistent grid (1..8);
+ * fallback_queue: entries of the per-stream fallback queue (>= 1024).
+ * Returns FP_ERR_ARG for values outside those sets.
  */
 typedef struct {
     uint32_t chunk_bytes;
