@@ -668,7 +668,7 @@ def _percentile_ms(lat_ns, q):
     return float(np.percentile(np.asarray(lat_ns, dtype=np.float64), q)) / 1e6
 
 
-SERVE_RING_BYTES = 1 << 31  # pinned result space of the serving bench's client
+SERVE_RING_BYTES = 1 << 32  # pinned result space of the serving bench's client
 
 
 def run_serve(args, world, rank, dist) -> None:
