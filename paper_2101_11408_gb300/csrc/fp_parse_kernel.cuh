@@ -7,11 +7,15 @@
 //
 //   1. stage  : the chunk's text plus a 16-byte pad before it and a 64-byte
 //               margin after it is copied into shared memory by the bulk-copy
-//               (TMA) engine, double buffered with the previous chunk's work;
-//   2. index  : separators are found four bytes per 32-bit word with exact
-//               SWAR zero-byte tests; a block scan ranks the field starts,
-//               whose positions are scattered in order; the chunk's field
-//               count is published at once for the decoupled look-back;
+//               (TMA) engine, two chunks ahead of the one being parsed (three
+//               buffers);
+//   2. index  : one iteration ahead of its parse, separators are found four
+//               bytes per 32-bit word with exact SWAR zero-byte tests; a
+//               block scan ranks the field starts, whose positions are
+//               scattered in order into one of two lists (a chunk of more
+//               than 1024 fields is listed window by window at its parse);
+//               the chunk's field count is published at once for the
+//               decoupled look-back;
 //   3. parse  : one thread per field, warps taking groups of 32 fields from a
 //               shared counter: the straight-line tokenizer for the common
 //               shape, else the general tokenizer of Section 4; quick exits
@@ -19,8 +23,8 @@
 //               w / w+1 check of Section 11; results are staged in shared
 //               memory;
 //   4. prefix : one warp looks back over the preceding chunks for this
-//               chunk's first field index while the others parse, then joins
-//               them;
+//               chunk's first field index (the 32 nearest first, then wider
+//               rounds) while the others parse, then joins them;
 //   5. store  : coalesced stores of the doubles and status bytes; fields that
 //               cannot be settled here are queued for the fallback kernel.
 #pragma once
