@@ -701,6 +701,24 @@ fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* h
   return FP_OK;
 }
 
+// A host call that failed part-way may still have copies queued that read or
+// write the caller's host arrays: wait for them, so that the arrays are the
+// caller's again when the call returns (its documented synchronous contract
+// holds on errors too).  The error itself was already returned.
+void drain_host_call(cudaStream_t stream) {
+  cudaStreamSynchronize(stream);
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_scratch.find({dev, stream});
+    if (it != g_scratch.end() && it->second) {
+      if (it->second->pipe_in) cudaStreamSynchronize(it->second->pipe_in);
+      if (it->second->pipe_out) cudaStreamSynchronize(it->second->pipe_out);
+    }
+  }
+  cudaGetLastError();  // the failure is reported by the call's return value
+}
+
 }  // namespace
 
 extern "C" {
@@ -937,10 +955,16 @@ fp_err_t fp_parse_f64_host(const char* host_text, size_t len, char delim, double
     const void* dv_text = device_view(host_text);
     void* dv_f64 = device_view(host_f64);
     void* dv_st = device_view(host_status);
-    if (dv_text && dv_f64 && dv_st)
-      return host_pipelined(host_text, len, delim, host_f64, host_status, host_count, stream);
+    if (dv_text && dv_f64 && dv_st) {
+      const fp_err_t e =
+          host_pipelined(host_text, len, delim, host_f64, host_status, host_count, stream);
+      if (e != FP_OK) drain_host_call(stream);
+      return e;
+    }
   }
-  return host_simple(host_text, len, delim, host_f64, host_status, host_count, stream);
+  const fp_err_t e = host_simple(host_text, len, delim, host_f64, host_status, host_count, stream);
+  if (e != FP_OK) drain_host_call(stream);
+  return e;
 }
 
 fp_err_t fp_shutdown(void) {
