@@ -164,6 +164,11 @@ void finish(fp_server* S, Request* r, fp_err_t err) {
 }
 
 void fail_slot(fp_server* S, Slot& sl, fp_err_t err) {
+  // Whatever the slot had queued before the failure (copies from or to the
+  // callers' host arrays, kernels writing arena units) ends before the
+  // requests complete and their units return to the arena.
+  cudaStreamSynchronize(sl.stream);
+  cudaGetLastError();  // the failure is reported through the requests
   for (Request* r : sl.reqs) finish(S, r, err);
   sl.reqs.clear();
   sl.phase = Phase::FREE;
