@@ -247,15 +247,16 @@ FP_API fp_err_t fp_batch_plan_destroy(fp_batch_plan *plan);
 
 /*
  * fp_batch_plan_gather -- pack the results of the plan's last launch in
- *   buffer order, for one copy back: buffer b's out_counts[b] values and
- *   statuses go to dst_f64 / dst_status from the sum of the earlier buffers'
- *   counts on, and that sum over all buffers (the total) to *dst_total.
+ *   buffer order, for one copy back: the k_b = min(out_counts[b],
+ *   out_offsets[b + 1] - out_offsets[b]) values and statuses buffer b holds
+ *   go to dst_f64 / dst_status from the sum of the earlier buffers' k_b on,
+ *   and that sum over all buffers (the total) to *dst_total.
  *   dst_f64 (8-byte aligned), dst_status and dst_total are addresses the
  *   device can write (device memory, or pinned host memory through its
- *   device address), with room for the total (at most out_offsets[nbuf]
- *   entries); they must not overlap the plan's outputs.  Queued on `stream`
- *   after the launch (two kernels: a scan of the counts, then a copy in
- *   pieces of 8192 fields); no host synchronisation.  Returns FP_ERR_ARG
+ *   device address), with room for the total (at most out_offsets[nbuf] -
+ *   out_offsets[0] entries); they must not overlap the plan's outputs.
+ *   Queued on `stream` after the launch (two kernels: a scan of the counts,
+ *   then a copy in pieces of 8192 fields); no host synchronisation.  Returns FP_ERR_ARG
  *   for a null plan, or null arrays when the plan has outputs.
  */
 FP_API fp_err_t fp_batch_plan_gather(fp_batch_plan *plan, double *dst_f64, uint8_t *dst_status,

@@ -49,6 +49,47 @@ def _check_text(text: torch.Tensor) -> None:
         raise TypeError("text must be contiguous")
 
 
+# dtypes of a field-count tensor (8-byte integers)
+_COUNT_DTYPES = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+
+
+def _check_out(t, dtypes, need: int, dev, name: str) -> None:
+    """An array the library writes: a contiguous tensor of one of `dtypes` on
+    `dev` with at least `need` entries (the kernels write through its address,
+    so a tensor elsewhere or too small is refused before the call)."""
+    if not isinstance(t, torch.Tensor) or t.dtype not in dtypes:
+        raise TypeError("%s must be a tensor of dtype %s"
+                        % (name, " or ".join(str(d) for d in dtypes)))
+    if t.device != dev:
+        raise TypeError("%s must be on %s, not %s" % (name, dev, t.device))
+    if not t.is_contiguous():
+        raise TypeError("%s must be contiguous" % name)
+    if t.numel() < need:
+        raise ValueError("%s needs at least %d entries, has %d" % (name, need, t.numel()))
+
+
+def _host_array(a, dtype, need: int, name: str, writable: bool = True) -> int:
+    """Address of a host array (numpy array or CPU tensor) of `dtype`,
+    contiguous, with at least `need` entries."""
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu" or a.dtype != getattr(torch, np.dtype(dtype).name):
+            raise TypeError("%s must be a CPU tensor of %s" % (name, np.dtype(dtype).name))
+        if not a.is_contiguous():
+            raise TypeError("%s must be contiguous" % name)
+        size, addr = a.numel(), a.data_ptr()
+    elif isinstance(a, np.ndarray):
+        if a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
+            raise TypeError("%s must be a contiguous numpy array of %s" % (name, np.dtype(dtype).name))
+        if writable and not a.flags.writeable:
+            raise TypeError("%s must be writable" % name)
+        size, addr = a.size, a.ctypes.data
+    else:
+        raise TypeError("%s must be a numpy array or a CPU tensor" % name)
+    if size < need:
+        raise ValueError("%s needs at least %d entries, has %d" % (name, need, size))
+    return addr
+
+
 def max_fields(nbytes: int) -> int:
     return int(_lib.load().fp_max_fields(nbytes))
 
@@ -62,10 +103,9 @@ def parse_f64_into(text: torch.Tensor, out_f64: torch.Tensor, out_status: torch.
     """
     _check_text(text)
     n = text.numel()
-    if out_f64.dtype != torch.float64 or out_status.dtype != torch.uint8:
-        raise TypeError("out_f64 must be float64 and out_status uint8")
-    if n and (out_f64.numel() < n or out_status.numel() < n):
-        raise ValueError("output arrays need max_fields(len) entries")
+    _check_out(out_f64, (torch.float64,), n, text.device, "out_f64")
+    _check_out(out_status, (torch.uint8,), n, text.device, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
     lib = _lib.load()
     rc = lib.fp_parse_f64(text.data_ptr() if n else None, n, _delim_byte(delim),
                           out_f64.data_ptr() if n else None,
@@ -96,10 +136,9 @@ def parse_f32_into(text: torch.Tensor, out_f32: torch.Tensor, out_status: torch.
     """As parse_f64_into, to binary32 (out_f32 float32)."""
     _check_text(text)
     n = text.numel()
-    if out_f32.dtype != torch.float32 or out_status.dtype != torch.uint8:
-        raise TypeError("out_f32 must be float32 and out_status uint8")
-    if n and (out_f32.numel() < n or out_status.numel() < n):
-        raise ValueError("output arrays need max_fields(len) entries")
+    _check_out(out_f32, (torch.float32,), n, text.device, "out_f32")
+    _check_out(out_status, (torch.uint8,), n, text.device, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
     lib = _lib.load()
     rc = lib.fp_parse_f32(text.data_ptr() if n else None, n, _delim_byte(delim),
                           out_f32.data_ptr() if n else None,
@@ -135,11 +174,10 @@ def parse_ex_into(text: torch.Tensor, out_values: torch.Tensor, out_status: torc
     (i mod K) * rows_cap + i div K."""
     _check_text(text)
     n = text.numel()
-    if out_values.dtype not in (torch.float64, torch.float32) or out_status.dtype != torch.uint8:
-        raise TypeError("out_values must be float64 or float32 and out_status uint8")
     need = columns * rows_cap if columns else n
-    if need and (out_values.numel() < need or out_status.numel() < need):
-        raise ValueError("output arrays need %d entries" % need)
+    _check_out(out_values, (torch.float64, torch.float32), need, text.device, "out_values")
+    _check_out(out_status, (torch.uint8,), need, text.device, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
     opt = _lib.Options(_delim_byte(delim), 1 if out_values.dtype == torch.float32 else 0,
                        _GRAMMARS[grammar], 0, columns, rows_cap)
     rc = _lib.load().fp_parse_ex(text.data_ptr() if n else None, n, ctypes.byref(opt),
@@ -173,14 +211,14 @@ def parse_f64_host_into(host_text, host_f64, host_status, delim=b"\n", stream=No
     """End-to-end parse of host memory through the C ABI (fp_parse_f64_host):
     host_text is a uint8 numpy array or CPU tensor (pinned copies fastest),
     host_f64 / host_status receive the results.  Returns the field count."""
-    def ptr(a):
-        return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
-    n = host_text.numel() if isinstance(host_text, torch.Tensor) else host_text.size
+    n = host_text.numel() if isinstance(host_text, torch.Tensor) else getattr(host_text, "size", 0)
+    p_text = _host_array(host_text, np.uint8, n, "host_text", writable=False)
+    p_f64 = _host_array(host_f64, np.float64, n, "host_f64")  # max_fields(n) entries
+    p_st = _host_array(host_status, np.uint8, n, "host_status")
     cnt = ctypes.c_uint64()
-    rc = _lib.load().fp_parse_f64_host(ptr(host_text) if n else None, n, _delim_byte(delim),
-                                       ptr(host_f64) if n else None,
-                                       ptr(host_status) if n else None, ctypes.byref(cnt),
-                                       _stream_handle(stream))
+    rc = _lib.load().fp_parse_f64_host(p_text if n else None, n, _delim_byte(delim),
+                                       p_f64 if n else None, p_st if n else None,
+                                       ctypes.byref(cnt), _stream_handle(stream))
     _lib.check(rc, "fp_parse_f64_host")
     return int(cnt.value)
 
@@ -198,6 +236,30 @@ def parse_f64_host(data, delim=b"\n", stream=None):
     return vals[:n], st[:n]
 
 
+def _batch_args(texts, out_f64, out_status, out_offsets, out_counts):
+    """Checked ctypes arrays (text pointers, lengths, output offsets) of a
+    batch: device buffers on one device, outputs there with room for
+    out_offsets[-1] entries, one count per buffer."""
+    nbuf = len(texts)
+    if nbuf == 0:
+        raise ValueError("no buffers")
+    for t in texts:
+        _check_text(t)
+        if t.device != texts[0].device:
+            raise TypeError("all buffers must be on one device")
+    offsets = [int(o) for o in out_offsets]
+    if len(offsets) != nbuf + 1:
+        raise ValueError("out_offsets needs nbuf + 1 entries")
+    dev = texts[0].device
+    _check_out(out_f64, (torch.float64,), offsets[-1], dev, "out_f64")
+    _check_out(out_status, (torch.uint8,), offsets[-1], dev, "out_status")
+    _check_out(out_counts, _COUNT_DTYPES, nbuf, dev, "out_counts")
+    ptrs = (ctypes.c_void_p * nbuf)(*[t.data_ptr() if t.numel() else None for t in texts])
+    lens = (ctypes.c_size_t * nbuf)(*[t.numel() for t in texts])
+    offs = (ctypes.c_uint64 * (nbuf + 1))(*offsets)
+    return ptrs, lens, offs
+
+
 def parse_f64_batch_into(texts, out_f64: torch.Tensor, out_status: torch.Tensor,
                          out_offsets, out_counts: torch.Tensor, delim=b"\n",
                          stream=None) -> None:
@@ -207,16 +269,8 @@ def parse_f64_batch_into(texts, out_f64: torch.Tensor, out_status: torch.Tensor,
     [out_offsets[b], out_offsets[b+1]).  out_counts: nbuf-element device
     tensor receiving the field counts.
     """
+    ptrs, lens, offs = _batch_args(texts, out_f64, out_status, out_offsets, out_counts)
     nbuf = len(texts)
-    if nbuf == 0:
-        raise ValueError("no buffers")
-    for t in texts:
-        _check_text(t)
-    ptrs = (ctypes.c_void_p * nbuf)(*[t.data_ptr() if t.numel() else None for t in texts])
-    lens = (ctypes.c_size_t * nbuf)(*[t.numel() for t in texts])
-    offs = (ctypes.c_uint64 * (nbuf + 1))(*[int(o) for o in out_offsets])
-    if out_counts.numel() < nbuf:
-        raise ValueError("out_counts needs one entry per buffer")
     lib = _lib.load()
     rc = lib.fp_parse_f64_batch(ptrs, lens, nbuf, _delim_byte(delim), out_f64.data_ptr(),
                                 out_status.data_ptr(), offs, out_counts.data_ptr(),
@@ -250,13 +304,10 @@ class BatchPlan:
 
     def __init__(self, texts, out_f64, out_status, out_offsets, out_counts, delim=b"\n",
                  graph=False):
+        ptrs, lens, offs = _batch_args(texts, out_f64, out_status, out_offsets, out_counts)
         nbuf = len(texts)
-        for t in texts:
-            _check_text(t)
-        ptrs = (ctypes.c_void_p * nbuf)(*[t.data_ptr() if t.numel() else None for t in texts])
-        lens = (ctypes.c_size_t * nbuf)(*[t.numel() for t in texts])
-        offs = (ctypes.c_uint64 * (nbuf + 1))(*[int(o) for o in out_offsets])
         self._keep = (texts, out_f64, out_status, out_counts)
+        self.capacity = offs[nbuf] - offs[0]  # the packed results fit in this many entries
         self._h = ctypes.c_void_p()
         _lib.check(_lib.load().fp_batch_plan_create(ptrs, lens, nbuf, _delim_byte(delim),
                                                     out_f64.data_ptr(), out_status.data_ptr(),
@@ -271,12 +322,16 @@ class BatchPlan:
     def gather(self, dst_f64: torch.Tensor, dst_status: torch.Tensor, dst_total: torch.Tensor,
                stream=None) -> None:
         """Pack the last launch's results in buffer order into dst_f64 /
-        dst_status (float64 / uint8 device tensors) and their number into
-        dst_total (one int64 device element), on the stream, without
-        synchronising (fp_batch_plan_gather)."""
-        for t, dt in ((dst_f64, torch.float64), (dst_status, torch.uint8), (dst_total, torch.int64)):
-            if t.device.type != "cuda" or t.dtype != dt or not t.is_contiguous():
-                raise ValueError("gather targets are contiguous device tensors")
+        dst_status (float64 / uint8 device tensors with room for the total,
+        at most self.capacity entries) and their number into dst_total (one
+        int64 device element), on the stream, without synchronising
+        (fp_batch_plan_gather)."""
+        dev = self._keep[0][0].device
+        # room for the total: the caller may know it (fixed inputs); it is at
+        # most the plan's output capacity, self.capacity
+        _check_out(dst_f64, (torch.float64,), 0, dev, "dst_f64")
+        _check_out(dst_status, (torch.uint8,), 0, dev, "dst_status")
+        _check_out(dst_total, _COUNT_DTYPES, 1, dev, "dst_total")
         _lib.check(_lib.load().fp_batch_plan_gather(self._h, dst_f64.data_ptr(),
                                                     dst_status.data_ptr(), dst_total.data_ptr(),
                                                     _stream_handle(stream)),

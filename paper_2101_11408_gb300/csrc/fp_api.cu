@@ -1131,7 +1131,7 @@ struct fp_batch_plan {
   cudaGraphExec_t graph;           // the captured launch sequence, or null
   // packing of the results (fp_batch_plan_gather)
   const unsigned long long* counts;  // the caller's out_counts (device)
-  void* pack;                      // one allocation: bases[nbuf], starts[nbuf + 1], pieces
+  void* pack;                      // one allocation: bases[nbuf + 1], starts[nbuf + 1], pieces
   const unsigned long long* bases;
   unsigned long long* starts;
   const unsigned long long* pieces;
@@ -1260,20 +1260,21 @@ extern "C" fp_err_t fp_batch_plan_create(const char* const* texts, const size_t*
       for (unsigned long long f0 = 0; f0 < out_offsets[b + 1] - out_offsets[b]; f0 += fp::PACK_PIECE)
         pk.push_back(((unsigned long long)b << 40) | f0);
     pl->npieces = pk.size();
-    const size_t n_words = (size_t)nbuf + (nbuf + 1) + pk.size();
+    const size_t n_words = (size_t)(nbuf + 1) + (nbuf + 1) + pk.size();
     if (cudaMalloc(&pl->pack, n_words * sizeof(unsigned long long)) != cudaSuccess) {
       cudaFree(pl->dmem);
       delete pl;
       return FP_ERR_CUDA;
     }
     unsigned long long* w = static_cast<unsigned long long*>(pl->pack);
-    pl->bases = w;
-    pl->starts = w + nbuf;
-    pl->pieces = w + nbuf + nbuf + 1;
-    std::vector<unsigned long long> bs(out_offsets, out_offsets + nbuf);
-    if (cudaMemcpy(w, bs.data(), nbuf * sizeof(unsigned long long), cudaMemcpyHostToDevice) !=
+    pl->bases = w;  // the nbuf + 1 output offsets (capacities are their differences)
+    pl->starts = w + nbuf + 1;
+    pl->pieces = w + 2 * (nbuf + 1);
+    std::vector<unsigned long long> bs(out_offsets, out_offsets + nbuf + 1);
+    if (cudaMemcpy(w, bs.data(), (nbuf + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
-        (!pk.empty() && cudaMemcpy(w + 2 * nbuf + 1, pk.data(), pk.size() * sizeof(unsigned long long),
+        (!pk.empty() && cudaMemcpy(w + 2 * (nbuf + 1), pk.data(),
+                                   pk.size() * sizeof(unsigned long long),
                                    cudaMemcpyHostToDevice) != cudaSuccess)) {
       cudaFree(pl->pack);
       cudaFree(pl->dmem);
@@ -1311,7 +1312,7 @@ extern "C" fp_err_t fp_batch_plan_gather(fp_batch_plan* pl, double* dst_f64, uin
   if (!pl) return FP_ERR_ARG;
   if (pl->npieces && (!dst_f64 || !dst_status)) return FP_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  FP_CUDA(fp::launch_pack_scan(pl->counts, pl->p.nbuf, pl->starts,
+  FP_CUDA(fp::launch_pack_scan(pl->counts, pl->bases, pl->p.nbuf, pl->starts,
                                reinterpret_cast<unsigned long long*>(dst_total), stream));
   FP_CUDA(fp::launch_pack_copy(pl->pieces, pl->npieces, pl->counts, pl->bases, pl->starts,
                                pl->p.out_bits, pl->p.out_status,

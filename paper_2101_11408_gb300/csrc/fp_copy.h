@@ -35,14 +35,16 @@ struct ScatterPiece {
 };
 constexpr uint32_t SCATTER_PIECE = 32768;  // fields per piece at most
 
-// Packing of a batch's results: buffer b's count_b results, at output index
-// base_b, go to dst at the sum of the earlier buffers' counts.  A piece is
-// (b << 40) | f0: fields [f0, f0 + PACK_PIECE) of buffer b's capacity.
+// Packing of a batch's results: buffer b owns output entries [bases[b],
+// bases[b + 1]) (nbuf + 1 offsets) and keeps kept_b = min(counts[b],
+// bases[b + 1] - bases[b]) results there; they go to dst at the sum of the
+// earlier buffers' kept_b.  A piece is (b << 40) | f0: fields [f0, f0 +
+// PACK_PIECE) of buffer b's capacity.
 constexpr uint32_t PACK_PIECE = 8192;  // fields per piece at most
-// starts[b] = sum of counts[b'] for b' < b (b <= nbuf; starts[nbuf] is the
+// starts[b] = sum of kept_b' for b' < b (b <= nbuf; starts[nbuf] is the
 // total, also written to *total when total is not null); one block.
-cudaError_t launch_pack_scan(const unsigned long long* counts, uint32_t nbuf,
-                             unsigned long long* starts, unsigned long long* total,
+cudaError_t launch_pack_scan(const unsigned long long* counts, const unsigned long long* bases,
+                             uint32_t nbuf, unsigned long long* starts, unsigned long long* total,
                              cudaStream_t stream);
 cudaError_t launch_pack_copy(const unsigned long long* pieces, unsigned long long npieces,
                              const unsigned long long* counts,

@@ -73,7 +73,16 @@ __global__ void __launch_bounds__(COPY_NT) scatter_kernel(const ScatterItem* ite
 
 constexpr int SCAN_NT = 1024;
 
+// The results buffer b holds: its count, at most its output capacity (a
+// buffer with more fields than room keeps only the first ones).
+__device__ __forceinline__ unsigned long long kept(const unsigned long long* counts,
+                                                   const unsigned long long* bases, uint32_t b) {
+  const unsigned long long cap = bases[b + 1] - bases[b];
+  return counts[b] < cap ? counts[b] : cap;
+}
+
 __global__ void __launch_bounds__(SCAN_NT) pack_scan_kernel(const unsigned long long* counts,
+                                                            const unsigned long long* bases,
                                                             uint32_t nbuf,
                                                             unsigned long long* starts,
                                                             unsigned long long* total) {
@@ -83,7 +92,7 @@ __global__ void __launch_bounds__(SCAN_NT) pack_scan_kernel(const unsigned long 
   const uint32_t per = (nbuf + SCAN_NT - 1) / SCAN_NT;
   const uint32_t b0 = t * per, b1 = min(b0 + per, nbuf);
   unsigned long long mine = 0;
-  for (uint32_t b = b0; b < b1; b++) mine += counts[b];
+  for (uint32_t b = b0; b < b1; b++) mine += kept(counts, bases, b);
   unsigned long long incl = mine;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -100,7 +109,7 @@ __global__ void __launch_bounds__(SCAN_NT) pack_scan_kernel(const unsigned long 
   unsigned long long run = before + incl - mine;  // exclusive prefix of this thread's first buffer
   for (uint32_t b = b0; b < b1; b++) {
     starts[b] = run;
-    run += counts[b];
+    run += kept(counts, bases, b);
   }
   if (t == 0) {
     starts[nbuf] = all;
@@ -117,7 +126,7 @@ __global__ void __launch_bounds__(COPY_NT) pack_copy_kernel(
     const unsigned long long pc = pieces[k];
     const uint32_t b = (uint32_t)(pc >> 40);
     const unsigned long long f0 = pc & ((1ull << 40) - 1);
-    const unsigned long long count = counts[b];
+    const unsigned long long count = kept(counts, bases, b);
     if (f0 >= count) continue;
     const unsigned long long m0 = count - f0;
     const uint32_t m = m0 < PACK_PIECE ? (uint32_t)m0 : PACK_PIECE;
@@ -132,10 +141,10 @@ __global__ void __launch_bounds__(COPY_NT) pack_copy_kernel(
 
 }  // namespace
 
-cudaError_t launch_pack_scan(const unsigned long long* counts, uint32_t nbuf,
-                             unsigned long long* starts, unsigned long long* total,
+cudaError_t launch_pack_scan(const unsigned long long* counts, const unsigned long long* bases,
+                             uint32_t nbuf, unsigned long long* starts, unsigned long long* total,
                              cudaStream_t stream) {
-  pack_scan_kernel<<<1, SCAN_NT, 0, stream>>>(counts, nbuf, starts, total);
+  pack_scan_kernel<<<1, SCAN_NT, 0, stream>>>(counts, bases, nbuf, starts, total);
   return cudaGetLastError();
 }
 

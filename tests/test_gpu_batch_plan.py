@@ -193,3 +193,63 @@ def test_gather_packs_the_results_in_buffer_order(graph):
             assert (dst[n:].cpu().numpy() == -7.0).all() and (dst_st[n:].cpu().numpy() == 0xAB).all()
     finally:
         plan.close()
+
+
+def test_gather_keeps_what_each_buffer_holds():
+    """A buffer with more fields than output room keeps its first ones and
+    reports all of them; the packing takes min(count, room) of each buffer,
+    the last one's included, so nothing past the plan's outputs is read and
+    the total fits the room the offsets reserve."""
+    texts = [workloads.uniform_text(20000, 31), workloads.bulk_mixed_text(3000, 32), b"",
+             workloads.uniform_text(700, 33)]
+    want = [oracle.parse_buffer(t) for t in texts]
+    rooms = [10000, want[1][0].size + 5, 0, 5]  # first and last below their counts
+    offs = [0]
+    for r in rooms:
+        offs.append(offs[-1] + r)
+    _, views = pack_to_device(texts)
+    out = torch.full((offs[-1],), -3.0, dtype=torch.float64, device="cuda")
+    st = torch.full((offs[-1],), 0xEE, dtype=torch.uint8, device="cuda")
+    cnt = torch.full((len(texts),), -1, dtype=torch.int64, device="cuda")
+    plan = fp.BatchPlan(views, out, st, offs, cnt)
+    try:
+        plan.launch()
+        total = sum(min(w[0].size, r) for w, r in zip(want, rooms))
+        dst = torch.full((total + 16,), -7.0, dtype=torch.float64, device="cuda")
+        dst_st = torch.full((total + 16,), 0xAB, dtype=torch.uint8, device="cuda")
+        tot = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        plan.gather(dst, dst_st, tot)
+        torch.cuda.synchronize()
+        assert cnt.cpu().tolist() == [w[0].size for w in want]
+        assert int(tot.item()) == total
+        want_v = np.concatenate([w[0][:r] for w, r in zip(want, rooms)])
+        want_s = np.concatenate([w[1][:r] for w, r in zip(want, rooms)])
+        assert np.array_equal(dst[:total].cpu().numpy().view(np.uint64), want_v)
+        assert np.array_equal(dst_st[:total].cpu().numpy(), want_s)
+        assert (dst[total:].cpu().numpy() == -7.0).all()
+        assert (dst_st[total:].cpu().numpy() == 0xAB).all()
+    finally:
+        plan.close()
+
+
+def test_binding_refuses_misplaced_outputs():
+    """Outputs the kernels would write through a wrong address are refused
+    before any call: host tensors, another dtype, too few entries, counts of
+    the wrong width."""
+    text = torch.frombuffer(bytearray(b"1.5\n2\n"), dtype=torch.uint8).cuda()
+    good = dict(out_f64=torch.empty(6, dtype=torch.float64, device="cuda"),
+                out_status=torch.empty(6, dtype=torch.uint8, device="cuda"),
+                out_count=torch.zeros(1, dtype=torch.int64, device="cuda"))
+    bad = [("out_f64", torch.empty(6, dtype=torch.float64)),
+           ("out_f64", torch.empty(6, dtype=torch.float32, device="cuda")),
+           ("out_f64", torch.empty(5, dtype=torch.float64, device="cuda")),
+           ("out_status", torch.empty(6, dtype=torch.uint8)),
+           ("out_count", torch.zeros(1, dtype=torch.int32, device="cuda")),
+           ("out_count", torch.zeros(1, dtype=torch.int64))]
+    for name, t in bad:
+        args = dict(good, **{name: t})
+        with pytest.raises((TypeError, ValueError)):
+            fp.parse_f64_into(text, args["out_f64"], args["out_status"], args["out_count"])
+    fp.parse_f64_into(text, good["out_f64"], good["out_status"], good["out_count"])
+    torch.cuda.synchronize()
+    assert int(good["out_count"].item()) == 2

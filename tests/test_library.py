@@ -88,3 +88,26 @@ def test_python_api_rejects_host_tensors():
         fp.parse_f64(torch.zeros(4, dtype=torch.uint8))
     with pytest.raises(TypeError):
         fp.parse_f64(torch.zeros(4, dtype=torch.int32))
+
+
+def test_host_entry_refuses_arrays_it_would_overrun():
+    """parse_f64_host_into writes up to len(text) results through raw host
+    addresses: arrays of another dtype, too short, non-contiguous or
+    read-only are refused before the library is called."""
+    import numpy as np
+    import torch
+    text = np.frombuffer(b"1.5\n2\n3\n", dtype=np.uint8)
+    n = text.size
+    ok_v, ok_s = np.empty(n, np.float64), np.empty(n, np.uint8)
+    bad = [(np.empty(n - 1, np.float64), ok_s),
+           (ok_v, np.empty(n - 1, np.uint8)),
+           (np.empty(n, np.float32), ok_s),
+           (np.empty(2 * n, np.float64)[::2], ok_s),
+           (ok_v, np.frombuffer(bytes(n), dtype=np.uint8)),
+           (torch.empty(n, dtype=torch.float32), ok_s),
+           ([0.0] * n, ok_s)]
+    for v, s in bad:
+        with pytest.raises((TypeError, ValueError)):
+            fp.parse_f64_host_into(text, v, s)
+    with pytest.raises(TypeError):
+        fp.parse_f64_host_into(text.astype(np.int8), ok_v, ok_s)
