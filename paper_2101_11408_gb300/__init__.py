@@ -51,35 +51,40 @@ def _check_text(text: torch.Tensor) -> None:
 
 # dtypes of a field-count tensor (8-byte integers)
 _COUNT_DTYPES = (torch.int64,) + ((torch.uint64,) if hasattr(torch, "uint64") else ())
+# host arrays: the torch and numpy forms of each element type
+_HOST_TYPES = {"uint8": (torch.uint8, np.dtype(np.uint8)),
+               "float64": (torch.float64, np.dtype(np.float64))}
 
 
-def _check_out(t, dtypes, need: int, dev, name: str) -> None:
+def _check_out(t, dtypes, need: int, dev: int, name: str) -> None:
     """An array the library writes: a contiguous tensor of one of `dtypes` on
-    `dev` with at least `need` entries (the kernels write through its address,
-    so a tensor elsewhere or too small is refused before the call)."""
+    CUDA device `dev` with at least `need` entries (the kernels write through
+    its address, so a tensor elsewhere or too small is refused before the
+    call).  Cheap on the accepted path: it runs on every call."""
     if not isinstance(t, torch.Tensor) or t.dtype not in dtypes:
         raise TypeError("%s must be a tensor of dtype %s"
                         % (name, " or ".join(str(d) for d in dtypes)))
-    if t.device != dev:
-        raise TypeError("%s must be on %s, not %s" % (name, dev, t.device))
+    if not t.is_cuda or t.get_device() != dev:
+        raise TypeError("%s must be on cuda:%d, not %s" % (name, dev, t.device))
     if not t.is_contiguous():
         raise TypeError("%s must be contiguous" % name)
     if t.numel() < need:
         raise ValueError("%s needs at least %d entries, has %d" % (name, need, t.numel()))
 
 
-def _host_array(a, dtype, need: int, name: str, writable: bool = True) -> int:
-    """Address of a host array (numpy array or CPU tensor) of `dtype`,
-    contiguous, with at least `need` entries."""
+def _host_array(a, kind: str, need: int, name: str, writable: bool = True) -> int:
+    """Address of a host array (numpy array or CPU tensor) of element type
+    `kind` ("uint8" or "float64"), contiguous, with at least `need` entries."""
+    tdt, ndt = _HOST_TYPES[kind]
     if isinstance(a, torch.Tensor):
-        if a.device.type != "cpu" or a.dtype != getattr(torch, np.dtype(dtype).name):
-            raise TypeError("%s must be a CPU tensor of %s" % (name, np.dtype(dtype).name))
+        if not a.is_cpu or a.dtype is not tdt:
+            raise TypeError("%s must be a CPU tensor of %s" % (name, kind))
         if not a.is_contiguous():
             raise TypeError("%s must be contiguous" % name)
         size, addr = a.numel(), a.data_ptr()
     elif isinstance(a, np.ndarray):
-        if a.dtype != np.dtype(dtype) or not a.flags.c_contiguous:
-            raise TypeError("%s must be a contiguous numpy array of %s" % (name, np.dtype(dtype).name))
+        if a.dtype != ndt or not a.flags.c_contiguous:
+            raise TypeError("%s must be a contiguous numpy array of %s" % (name, kind))
         if writable and not a.flags.writeable:
             raise TypeError("%s must be writable" % name)
         size, addr = a.size, a.ctypes.data
@@ -102,10 +107,10 @@ def parse_f64_into(text: torch.Tensor, out_f64: torch.Tensor, out_status: torch.
     same device; out_count is a one-element int64/uint64 device tensor.
     """
     _check_text(text)
-    n = text.numel()
-    _check_out(out_f64, (torch.float64,), n, text.device, "out_f64")
-    _check_out(out_status, (torch.uint8,), n, text.device, "out_status")
-    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
+    n, dev = text.numel(), text.get_device()
+    _check_out(out_f64, (torch.float64,), n, dev, "out_f64")
+    _check_out(out_status, (torch.uint8,), n, dev, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, dev, "out_count")
     lib = _lib.load()
     rc = lib.fp_parse_f64(text.data_ptr() if n else None, n, _delim_byte(delim),
                           out_f64.data_ptr() if n else None,
@@ -135,10 +140,10 @@ def parse_f32_into(text: torch.Tensor, out_f32: torch.Tensor, out_status: torch.
                    out_count: torch.Tensor, delim=b"\n", stream=None) -> None:
     """As parse_f64_into, to binary32 (out_f32 float32)."""
     _check_text(text)
-    n = text.numel()
-    _check_out(out_f32, (torch.float32,), n, text.device, "out_f32")
-    _check_out(out_status, (torch.uint8,), n, text.device, "out_status")
-    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
+    n, dev = text.numel(), text.get_device()
+    _check_out(out_f32, (torch.float32,), n, dev, "out_f32")
+    _check_out(out_status, (torch.uint8,), n, dev, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, dev, "out_count")
     lib = _lib.load()
     rc = lib.fp_parse_f32(text.data_ptr() if n else None, n, _delim_byte(delim),
                           out_f32.data_ptr() if n else None,
@@ -175,9 +180,10 @@ def parse_ex_into(text: torch.Tensor, out_values: torch.Tensor, out_status: torc
     _check_text(text)
     n = text.numel()
     need = columns * rows_cap if columns else n
-    _check_out(out_values, (torch.float64, torch.float32), need, text.device, "out_values")
-    _check_out(out_status, (torch.uint8,), need, text.device, "out_status")
-    _check_out(out_count, _COUNT_DTYPES, 1, text.device, "out_count")
+    dev = text.get_device()
+    _check_out(out_values, (torch.float64, torch.float32), need, dev, "out_values")
+    _check_out(out_status, (torch.uint8,), need, dev, "out_status")
+    _check_out(out_count, _COUNT_DTYPES, 1, dev, "out_count")
     opt = _lib.Options(_delim_byte(delim), 1 if out_values.dtype == torch.float32 else 0,
                        _GRAMMARS[grammar], 0, columns, rows_cap)
     rc = _lib.load().fp_parse_ex(text.data_ptr() if n else None, n, ctypes.byref(opt),
@@ -212,9 +218,9 @@ def parse_f64_host_into(host_text, host_f64, host_status, delim=b"\n", stream=No
     host_text is a uint8 numpy array or CPU tensor (pinned copies fastest),
     host_f64 / host_status receive the results.  Returns the field count."""
     n = host_text.numel() if isinstance(host_text, torch.Tensor) else getattr(host_text, "size", 0)
-    p_text = _host_array(host_text, np.uint8, n, "host_text", writable=False)
-    p_f64 = _host_array(host_f64, np.float64, n, "host_f64")  # max_fields(n) entries
-    p_st = _host_array(host_status, np.uint8, n, "host_status")
+    p_text = _host_array(host_text, "uint8", n, "host_text", writable=False)
+    p_f64 = _host_array(host_f64, "float64", n, "host_f64")  # max_fields(n) entries
+    p_st = _host_array(host_status, "uint8", n, "host_status")
     cnt = ctypes.c_uint64()
     rc = _lib.load().fp_parse_f64_host(p_text if n else None, n, _delim_byte(delim),
                                        p_f64 if n else None, p_st if n else None,
@@ -245,12 +251,12 @@ def _batch_args(texts, out_f64, out_status, out_offsets, out_counts):
         raise ValueError("no buffers")
     for t in texts:
         _check_text(t)
-        if t.device != texts[0].device:
+        if t.get_device() != texts[0].get_device():
             raise TypeError("all buffers must be on one device")
     offsets = [int(o) for o in out_offsets]
     if len(offsets) != nbuf + 1:
         raise ValueError("out_offsets needs nbuf + 1 entries")
-    dev = texts[0].device
+    dev = texts[0].get_device()
     _check_out(out_f64, (torch.float64,), offsets[-1], dev, "out_f64")
     _check_out(out_status, (torch.uint8,), offsets[-1], dev, "out_status")
     _check_out(out_counts, _COUNT_DTYPES, nbuf, dev, "out_counts")
@@ -326,7 +332,7 @@ class BatchPlan:
         at most self.capacity entries) and their number into dst_total (one
         int64 device element), on the stream, without synchronising
         (fp_batch_plan_gather)."""
-        dev = self._keep[0][0].device
+        dev = self._keep[0][0].get_device()
         # room for the total: the caller may know it (fixed inputs); it is at
         # most the plan's output capacity, self.capacity
         _check_out(dst_f64, (torch.float64,), 0, dev, "dst_f64")

@@ -671,6 +671,12 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
   WarpSmem& sm = smem[wib];
   Ctl* ctl = p.ctl;
   const unsigned long long nq_all = *(volatile unsigned long long*)&ctl->qcount;
+  const unsigned long long nov_all = *(volatile unsigned long long*)&ctl->ovf_count;
+  // Nothing pending (the usual case): nothing to decide and nothing to
+  // reset.  Every block sees the same two words (the parse kernel has ended
+  // and the reset below happens only when one of them is nonzero, after
+  // every block has read them), so either all blocks leave here or none.
+  if ((nq_all | nov_all) == 0) return;
   const unsigned long long nq = nq_all < p.qcap ? nq_all : p.qcap;
   unsigned long long n_items = 0, n_big = 0, n_scan = 0;
   const unsigned long long gwarp = (unsigned long long)blockIdx.x * FB_WARPS + wib;
@@ -679,7 +685,6 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
     resolve<F>(p, p.queue[i], sm, lane, n_items, n_big);
   // Chunks whose pending fields did not fit the queue: one warp per chunk
   // finds them among its outputs and decides them one at a time.
-  const unsigned long long nov_all = *(volatile unsigned long long*)&ctl->ovf_count;
   const unsigned long long nov = nov_all < p.ovf_cap ? nov_all : p.ovf_cap;
   for (unsigned long long c = gwarp; c < nov; c += gwarps) {
     const unsigned long long n = p.ovf[2 * c] & LOC_OFF_MASK;
