@@ -66,10 +66,28 @@ constexpr int DIG_CAP = 832;          // digit bytes per warp (KMAX + 1, rounded
 constexpr long long EXP_SAT = 1000000000000000ll;  // explicit exponent saturation
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
-// per warp: three big naturals and the digit buffer
+// per warp: three big naturals and the digits of a field that needs them
 struct WarpSmem {
   uint32_t P[LIMBS], B[LIMBS], Q[LIMBS];
   uint8_t dig[DIG_CAP];
+};
+
+// The significant digits of a field, read from its text: digit j (j = 0 is
+// the first nonzero one) is the byte at fz + j, one further on from the
+// point on (the digits of a valid significand are contiguous but for one
+// point).  The first nreal digits are the text's (at most KMAX); a sticky
+// digit 1 follows when the field has more (a nonzero digit lies beyond,
+// since the last significant digit is nonzero); every later digit is 0.
+struct DigitSrc {
+  const uint8_t* f;
+  long long fz;        // text offset of digit 0
+  long long shift_at;  // first digit index after the point (or beyond all digits)
+  long long nreal;
+  bool sticky;
+  __device__ __forceinline__ uint32_t at(long long j) const {
+    if (j < nreal) return (uint32_t)f[fz + j + (j >= shift_at ? 1 : 0)] - '0';
+    return (sticky && j == nreal) ? 1u : 0u;
+  }
 };
 
 // A big natural in shared memory; n (the number of limbs, top limb nonzero)
@@ -159,8 +177,8 @@ __device__ __forceinline__ int dec_digits(uint32_t v) {  // decimal digits of 0 
 // Sign of V - h, V = dig[0 .. nD) * 10^ED (dig[0] != 0), h = H * 10^Eh (H > 0
 // in base 10^9): the leading digits' exponents, then V's digits regrouped
 // into H's base-10^9 chunks (the first chunk as wide as H's top limb).
-__device__ __noinline__ int dec_compare(const uint8_t* dig, long long nD, long long ED, const WBig& H,
-                           long long Eh, int lane) {
+__device__ __noinline__ int dec_compare(const uint8_t* dig, long long nD, long long ED,
+                                        const WBig& H, long long Eh, int lane) {
   const int nl = H.n;
   const int ltop = dec_digits(H.p[nl - 1]);
   const long long nH = ltop + 9ll * (nl - 1);
@@ -173,9 +191,14 @@ __device__ __noinline__ int dec_compare(const uint8_t* dig, long long nD, long l
     uint32_t hv = 0, vv = 0;
     if (c < nch) {
       hv = c < nl ? H.p[nl - 1 - c] : 0u;
-      const long long start = c == 0 ? 0 : ltop + 9 * (c - 1);
-      const int len = c == 0 ? ltop : 9;
-      for (int k = 0; k < len; k++) vv = vv * 10 + (start + k < nD ? dig[start + k] : 0u);
+      // chunk c holds digits [end - 9, end), end = ltop + 9c; digits before
+      // 0 (in the first chunk) and from nD on are zeros
+      const long long end = ltop + 9 * c;
+#pragma unroll
+      for (int k = 0; k < 9; k++) {
+        const long long j = end - 9 + k;
+        vv = vv * 10 + ((j >= 0 && j < nD) ? (uint32_t)dig[j] : 0u);
+      }
     }
     const uint32_t diff = __ballot_sync(FULL, hv != vv);
     if (diff) {
@@ -200,7 +223,6 @@ __device__ __forceinline__ void float_parts(uint64_t x, uint64_t& M, int& e) {
   }
 }
 
-__device__ __forceinline__ bool is_sep(uint32_t c, uint32_t delim) { return c == '\n' || c == delim; }
 
 // The power part of a midpoint, 2^(e-1) or 5^(1-e) (times 10^Eh), for the
 // exponent e of the last call: the midpoints on both sides of a candidate
@@ -212,7 +234,7 @@ struct MidPower {
   WBig X;  // in sm.P or sm.Q
 };
 
-// Sign of V - h into c, V = dig[0 .. nD) 10^ED and h the midpoint between
+// Sign of V - h into c, V = sm.dig[0 .. nD) 10^ED and h the midpoint between
 // the positive patterns lowbits and lowbits + 1 of F; false on a size error.
 template <class F>
 __device__ __noinline__ bool cmp_midpoint(uint64_t lowbits, WarpSmem& sm, long long nD,
@@ -340,7 +362,6 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
   r.bignum = 0;
   r.error = 0;
   const uint8_t* f = fg;
-  const uint32_t lt_mask = (1u << lane) - 1;
   auto invalid = [&]() {
     r.bits = F::QNAN;
     r.status = ST_INVALID;
@@ -427,52 +448,48 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     h.error = 0;
     return h;
   }
-  // ---- structure: the exponent marker, the point, the digits ---------------
-  // One pass over [s, the marker): the digits from the first nonzero one on
-  // go to shared memory in order (the point skipped), ranked by ballots;
-  // the last nonzero digit's rank gives the significant digits, the digits
-  // stored after it are the trailing zeros, and the digits after the point
-  // are counted on the way.
+  // ---- structure: the exponent marker, the point, the nonzero digits -------
+  // One pass over [s, the marker), a byte per lane: the first marker ends
+  // the significand; the first point, the first and the last nonzero digit
+  // are located and any other byte flags the field.  A valid significand is
+  // digits and at most one point, so every count below follows from these
+  // positions, and its digits are read from the text where needed.
   long long ep = p1;  // first 'e' / 'E' in [s, p1)
   long long dp = -1;  // the point
-  long long ndot = 0, nbad = 0, ndig = 0;
-  long long fz = -1;                       // first nonzero digit of the significand
-  long long nst = 0, nsig = 0, n_frac = 0;  // digits stored; up to the last nonzero one; after the point
+  long long fz = -1;  // first nonzero digit of the significand
+  long long lz = -1;  // last nonzero digit of the significand
+  long long ndot = 0;
+  bool bad = false;
+  // each round's byte is read one round ahead, so that its load overlaps the
+  // ballots of the round before
+  uint32_t cnext = s + lane < p1 ? f[s + lane] : '0';
   for (long long base = s; base < p1; base += 32) {
-    const long long i = base + lane;
-    const bool in = i < p1;
-    const uint32_t c = in ? f[i] : '0';
-    const uint32_t E = __ballot_sync(FULL, in && (c | 0x20) == 'e');
-    const uint32_t cut = E ? ((E & (0u - E)) - 1) : FULL;  // lanes before the marker
-    const uint32_t inm = __ballot_sync(FULL, in) & cut;
+    const long long left = p1 - base;  // bytes of [s, p1) from this round on
+    const uint32_t inr = left >= 32 ? FULL : ((1u << left) - 1u);
+    const uint32_t c = cnext;
+    cnext = base + 32 + lane < p1 ? f[base + 32 + lane] : '0';
+    const bool dig = is_digit(c);
+    const uint32_t E = __ballot_sync(FULL, (c | 0x20) == 'e') & inr;
+    const uint32_t inm = inr & (E ? ((E & (0u - E)) - 1) : FULL);  // lanes before the marker
     const uint32_t dots = __ballot_sync(FULL, c == '.') & inm;
-    const uint32_t digs = __ballot_sync(FULL, is_digit(c)) & inm;
-    const uint32_t nz = __ballot_sync(FULL, is_digit(c) && c != '0') & inm;
-    nbad += __popc(inm & ~dots & ~digs);
-    ndig += __popc(digs);
+    const uint32_t other = __ballot_sync(FULL, !dig && c != '.') & inm;
+    const uint32_t nz = __ballot_sync(FULL, dig && c != '0') & inm;
+    bad |= other != 0;
     if (dots) {
       ndot += __popc(dots);
       if (dp < 0) dp = base + __ffs(dots) - 1;
     }
-    if (dp >= 0) {  // digits after the point (it may lie in this round)
-      const long long k = dp - base;  // the point's lane, or below 0
-      n_frac += __popc(k < 0 ? digs : (k >= 31 ? 0u : digs & (FULL << (k + 1))));
-    }
-    if (fz < 0 && nz) fz = base + __ffs(nz) - 1;
-    if (fz >= 0) {
-      const long long k = fz - base;  // lanes from fz on
-      const uint32_t st = k <= 0 ? digs : digs & (FULL << k);
-      const long long rank = nst + __popc(st & lt_mask);
-      if (((st >> lane) & 1u) && rank < KMAX) sm.dig[rank] = (uint8_t)(c - '0');
-      if (nz) nsig = nst + __popc(st & (FULL >> __clz(nz)));  // through the last nonzero digit
-      nst += __popc(st);
+    if (nz) {
+      if (fz < 0) fz = base + __ffs(nz) - 1;
+      lz = base + 31 - __clz(nz);
     }
     if (E) {
       ep = base + __ffs(E) - 1;
       break;
     }
   }
-  if (nbad || ndot > 1 || ndig == 0) return invalid();
+  // [s, ep) holds ep - s - ndot digits
+  if (bad || ndot > 1 || ep - s - ndot == 0) return invalid();
   if (grammar == GRAMMAR_JSON) {
     // an integer part without leading zeros; digits after a point
     const uint32_t a = f[s];
@@ -521,9 +538,15 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     return r;
   }
   // ---- the decimal exponent E ----------------------------------------------
+  // significant digits fz .. lz and the zeros after them (the point
+  // excluded); digits after the point
+  const long long nsig = lz - fz + 1 - ((dp > fz && dp < lz) ? 1 : 0);
+  const long long nst = ep - fz - (dp > fz ? 1 : 0);
+  const long long n_frac = dp >= 0 ? ep - dp - 1 : 0;
   const long long tz = nst - nsig;  // the zero digits after the last nonzero one
-  __syncwarp();
   const long long E = ex - n_frac + tz;  // value = (digits fz..lz) * 10^E
+  const DigitSrc src{f, fz, dp > fz ? dp - fz : (long long)(1ll << 62), nsig < KMAX ? nsig : KMAX,
+                     nsig > KMAX};
   // ---- quick exits: 10^(nsig-1+E) <= V < 10^(nsig+E) ----------------------
   if (nsig - 1 + E >= F::DEC_OVF) {
     r.bits = F::INF | sign;
@@ -539,7 +562,7 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
   const int n19 = nsig < 19 ? (int)nsig : 19;
   // w = the first n19 digits: lane k < n19 weighs digit k by 10^(n19-1-k),
   // and a butterfly adds the terms
-  uint64_t w = lane < n19 ? (uint64_t)sm.dig[lane] * kPow10[n19 - 1 - lane] : 0ull;
+  uint64_t w = lane < n19 ? (uint64_t)src.at(lane) * kPow10[n19 - 1 - lane] : 0ull;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(FULL, w, off);
   const long long q19 = E + (nsig - n19);
@@ -559,14 +582,13 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
   // ---- exact comparison with midpoints, in decimal --------------------------
   r.bignum = 1;
   {
-    long long nD = nsig < KMAX ? nsig : KMAX;
-    long long ED = E + (nsig - nD);
-    if (nsig > KMAX) {  // the sticky digit
-      if (lane == 0) sm.dig[nD] = 1;
-      __syncwarp();
-      nD += 1;
-      ED -= 1;
-    }
+    // the first KMAX digits and, for more, a sticky digit 1 one place below,
+    // to shared memory (lanes take digits j = lane mod 32)
+    const long long nD = src.nreal + (src.sticky ? 1 : 0);
+    const long long ED = E + (nsig - src.nreal) - (src.sticky ? 1 : 0);
+#pragma unroll 4
+    for (long long j = lane; j < nD; j += 32) sm.dig[j] = (uint8_t)src.at(j);
+    __syncwarp();
     MidPower mp;
     mp.valid = false;
     mp.e = 0;
