@@ -449,42 +449,48 @@ __device__ LongResult warp_field(const uint8_t* fg, unsigned long long lim, uint
     return h;
   }
   // ---- structure: the exponent marker, the point, the nonzero digits -------
-  // One pass over [s, the marker), a byte per lane: the first marker ends
+  // One pass over [s, the marker), 64 bytes per round (lane L takes bytes L
+  // and 32 + L; 64-bit masks from pairs of ballots): the first marker ends
   // the significand; the first point, the first and the last nonzero digit
   // are located and any other byte flags the field.  A valid significand is
   // digits and at most one point, so every count below follows from these
-  // positions, and its digits are read from the text where needed.
+  // positions, and its digits are read from the text where needed.  Each
+  // round's bytes are read one round ahead, so that their loads overlap the
+  // ballots of the round before.
   long long ep = p1;  // first 'e' / 'E' in [s, p1)
   long long dp = -1;  // the point
   long long fz = -1;  // first nonzero digit of the significand
   long long lz = -1;  // last nonzero digit of the significand
   long long ndot = 0;
   bool bad = false;
-  // each round's byte is read one round ahead, so that its load overlaps the
-  // ballots of the round before
-  uint32_t cnext = s + lane < p1 ? f[s + lane] : '0';
-  for (long long base = s; base < p1; base += 32) {
+  auto pair = [&](bool lo, bool hi) -> unsigned long long {
+    return ((unsigned long long)__ballot_sync(FULL, hi) << 32) | __ballot_sync(FULL, lo);
+  };
+  uint32_t cn0 = s + lane < p1 ? f[s + lane] : '0';
+  uint32_t cn1 = s + 32 + lane < p1 ? f[s + 32 + lane] : '0';
+  for (long long base = s; base < p1; base += 64) {
     const long long left = p1 - base;  // bytes of [s, p1) from this round on
-    const uint32_t inr = left >= 32 ? FULL : ((1u << left) - 1u);
-    const uint32_t c = cnext;
-    cnext = base + 32 + lane < p1 ? f[base + 32 + lane] : '0';
-    const bool dig = is_digit(c);
-    const uint32_t E = __ballot_sync(FULL, (c | 0x20) == 'e') & inr;
-    const uint32_t inm = inr & (E ? ((E & (0u - E)) - 1) : FULL);  // lanes before the marker
-    const uint32_t dots = __ballot_sync(FULL, c == '.') & inm;
-    const uint32_t other = __ballot_sync(FULL, !dig && c != '.') & inm;
-    const uint32_t nz = __ballot_sync(FULL, dig && c != '0') & inm;
+    const unsigned long long inr = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
+    const uint32_t c0 = cn0, c1 = cn1;
+    cn0 = base + 64 + lane < p1 ? f[base + 64 + lane] : '0';
+    cn1 = base + 96 + lane < p1 ? f[base + 96 + lane] : '0';
+    const bool d0 = is_digit(c0), d1 = is_digit(c1);
+    const unsigned long long E = pair((c0 | 0x20) == 'e', (c1 | 0x20) == 'e') & inr;
+    const unsigned long long inm = inr & (E ? ((E & (0ull - E)) - 1ull) : ~0ull);  // before the marker
+    const unsigned long long dots = pair(c0 == '.', c1 == '.') & inm;
+    const unsigned long long other = pair(!d0 && c0 != '.', !d1 && c1 != '.') & inm;
+    const unsigned long long nz = pair(d0 && c0 != '0', d1 && c1 != '0') & inm;
     bad |= other != 0;
     if (dots) {
-      ndot += __popc(dots);
-      if (dp < 0) dp = base + __ffs(dots) - 1;
+      ndot += __popcll(dots);
+      if (dp < 0) dp = base + __ffsll((long long)dots) - 1;
     }
     if (nz) {
-      if (fz < 0) fz = base + __ffs(nz) - 1;
-      lz = base + 31 - __clz(nz);
+      if (fz < 0) fz = base + __ffsll((long long)nz) - 1;
+      lz = base + 63 - __clzll((long long)nz);
     }
     if (E) {
-      ep = base + __ffs(E) - 1;
+      ep = base + __ffsll((long long)E) - 1;
       break;
     }
   }
