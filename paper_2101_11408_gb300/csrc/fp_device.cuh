@@ -578,8 +578,9 @@ struct FastToken {
 // by a byte permute, bytes before the significand become '0', and the 20
 // low digits are converted four at a time.  Returns false for anything
 // else; the general tokenizer then decides (with identical results for the
-// shapes accepted here).  tile is 4-byte aligned; reads may touch up to 8
-// bytes before s and 8 after e.
+// shapes accepted here).  tile is 4-byte aligned; reads may touch up to 26
+// bytes before s (the window's first word, for a one-character significand)
+// and 4 after e, and those bytes never change the result.
 FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
   const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
   auto load4 = [&](int p) -> uint32_t {

@@ -1,0 +1,88 @@
+// hot_path_check.cpp -- the parse kernel's per-field steps, built for the
+// host from the device header (its functions are host-callable) and run on
+// every '\n'-separated field of standard input: the straight-line tokenizer
+// of Section 4 on a padded tile, Algorithm 1 (Section 5) on its (w, q), and
+// the general tokenizer with the 19-digit check of Section 11 for the fields
+// the first one declines; fields both leave undecided are printed as "P"
+// (the fallback kernel's).  One line per field: "<bits hex> <status>" or
+// "P".  The test compares the decided ones with the oracle.
+//
+// usage: hot_path_check <64|32> <grammar 0|1|2> < text
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fp_device.cuh"
+
+namespace {
+
+constexpr int LEAD = 32;  // tile bytes before the field (parse_fast reads up to 26)
+
+template <class F>
+void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& tab) {
+  using namespace fp;
+  alignas(16) uint8_t tile[LEAD + LMAX + 32];
+  std::memset(tile, 0, sizeof(tile));
+  if (n > LMAX) {  // the kernel hands longer fields to the fallback kernel
+    std::printf("P\n");
+    return;
+  }
+  std::memcpy(tile + LEAD, field, (size_t)n);
+  tile[LEAD + n] = '\n';
+  const int s = LEAD, e = LEAD + n;
+  FastToken ft;
+  ft.w = 0;
+  ft.q = 0;
+  bool ok = parse_fast(tile, s, e, ft);
+  if (grammar == GRAMMAR_JSON) ok = ok && json_ok_fast(tile, s, ft);
+  const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, tab, true);
+  uint64_t sgn = ft.sign;
+  if (F::MBITS != F64::MBITS) sgn = ft.sign ? F::SIGN : 0;
+  uint64_t bits = ft.w ? (r.bits | sgn) : sgn;
+  unsigned status = ft.w ? status_of<F>(r.bits) : ST_OK;
+  if (!ok || (ft.w && r.bits == EL_ABORT)) {
+    const FieldResult g = parse_short_field<F>(tile + s, n, tab, grammar);
+    if (g.status == ST_PENDING) {
+      std::printf("P\n");
+      return;
+    }
+    bits = g.bits;
+    status = g.status;
+  }
+  std::printf("%016llx %u\n", (unsigned long long)bits, status);
+}
+
+}  // namespace
+
+int main(int argc, char** argv) {
+  if (argc != 3) {
+    std::fprintf(stderr, "usage: %s <64|32> <grammar>\n", argv[0]);
+    return 2;
+  }
+  const bool f32 = std::atoi(argv[1]) == 32;
+  const uint32_t grammar = (uint32_t)std::atoi(argv[2]);
+  // the table as the kernel holds it: dense high words, interleaved low words
+  static const unsigned long long table[2 * FP_POW5_ENTRIES] = {FP_POW5_TABLE_VALUES};
+  static uint64_t hi[FP_POW5_ENTRIES];
+  for (int i = 0; i < FP_POW5_ENTRIES; i++) hi[i] = table[2 * i];
+  const fp::Pow5 tab{hi, 1, reinterpret_cast<const uint64_t*>(table) + 1};
+  std::string text;
+  char buf[1 << 16];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), stdin)) > 0) text.append(buf, got);
+  // fields: the pieces between '\n's; a text ending in '\n' has no empty
+  // field after it
+  size_t p = 0;
+  while (p < text.size()) {
+    size_t q = text.find('\n', p);
+    if (q == std::string::npos) q = text.size();
+    const uint8_t* f = reinterpret_cast<const uint8_t*>(text.data()) + p;
+    const int n = (int)(q - p);
+    if (f32) check_field<fp::F32>(f, n, grammar, tab);
+    else check_field<fp::F64>(f, n, grammar, tab);
+    p = q + 1;
+  }
+  return 0;
+}

@@ -1,0 +1,204 @@
+"""The parse kernel's per-field arithmetic on the CPU: the device header's
+straight-line tokenizer (Section 4), Algorithm 1 (Section 5) and the general
+tokenizer with the 19-digit check (Section 11), built for the host
+(tests/native/hot_path_check.cpp), against the oracle on seeded fields.
+
+Every field the two tokenizers decide must carry the oracle's bit pattern
+and status; the rest are the fallback kernel's and are only counted (the
+GPU parity tests cover them).  This catches a slip in the hot path's
+arithmetic without a GPU; the kernel's indexing, staging and look-back are
+the GPU tests' part.
+"""
+import os
+import random
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2101_11408_gb300 import workloads
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2101_11408_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def hot_path(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("hot") / "hot_path_check")
+    subprocess.run([cxx, "-std=c++17", "-O2", "-Wall", "-Wno-unknown-pragmas", "-I", CSRC,
+                    "-o", exe, os.path.join(HERE, "native", "hot_path_check.cpp")], check=True)
+    return exe
+
+
+def run_hot_path(exe, text: bytes, f32=False, grammar=0):
+    """Decided fields as (index, bits, status) arrays, and the pending count."""
+    r = subprocess.run([exe, "32" if f32 else "64", str(grammar)], input=text,
+                       capture_output=True, timeout=600, check=True)
+    lines = r.stdout.split(b"\n")[:-1]
+    idx, bits, st = [], [], []
+    pending = 0
+    for i, ln in enumerate(lines):
+        if ln == b"P":
+            pending += 1
+            continue
+        b, s = ln.split()
+        idx.append(i)
+        bits.append(int(b, 16))
+        st.append(int(s))
+    return len(lines), np.array(idx, dtype=np.int64), np.array(bits, dtype=np.uint64), \
+        np.array(st, dtype=np.uint8), pending
+
+
+def check(exe, text: bytes, f32=False, grammar=0, max_pending=None):
+    n, idx, bits, st, pending = run_hot_path(exe, text, f32, grammar)
+    rb, rs = oracle.parse_buffer(text, f32=f32, grammar=grammar)
+    assert n == rb.size, "field counts differ"
+    want_b = rb.astype(np.uint64)[idx]
+    want_s = rs[idx]
+    bad = np.nonzero((want_b != bits) | (want_s != st))[0]
+    if bad.size:
+        fields = text.split(b"\n")
+        k = int(idx[bad[0]])
+        raise AssertionError("field %d %r: hot path %016x/%d, oracle %016x/%d (%d mismatches)"
+                             % (k, fields[k], int(bits[bad[0]]), int(st[bad[0]]),
+                                int(want_b[bad[0]]), int(want_s[bad[0]]), bad.size))
+    if max_pending is not None:
+        assert pending <= max_pending, "%d fields left to the fallback" % pending
+    return n, pending
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_bulk_mixed_fields(hot_path, f32):
+    """The bulk workload's shapes (17-digit uniforms, coordinates, integers
+    below 2^63, d.ddddE+-xxx): all decided on the hot path."""
+    n, pending = check(hot_path, workloads.bulk_mixed_text(30000, workloads.SEED_BASE + 71), f32,
+                       max_pending=0)
+    assert n == 30000
+
+
+def test_uniform_fields(hot_path):
+    check(hot_path, workloads.uniform_text(20000, workloads.SEED_BASE + 72), max_pending=0)
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_decimal_range_boundaries(hot_path, f32):
+    """One- and two-digit significands at every exponent from 10^-345 to
+    10^310: underflow to zero, subnormals, the normal range, overflow."""
+    lines = []
+    for d in list(range(1, 10)) + list(range(10, 100, 7)):
+        for ex in range(-345, 311):
+            lines.append("%de%d" % (d, ex))
+            lines.append("-%d.%de%d" % (d // 10 or d, d % 10, ex))
+    check(hot_path, "\n".join(lines).encode(), f32, max_pending=0)
+
+
+def _fuzz_fields(count, seed, alphabet):
+    rnd = random.Random(seed)
+    out = []
+    for _ in range(count):
+        n = rnd.randrange(0, 32)
+        out.append("".join(rnd.choice(alphabet) for _ in range(n)))
+    return "\n".join(out).encode()
+
+
+@pytest.mark.parametrize("grammar", [0, 2])
+def test_grammar_fuzz(hot_path, grammar):
+    """Short fields over digits, points, markers, signs and blanks: most
+    are malformed, and the two tokenizers must classify every one as the
+    oracle does (decimal and JSON grammars)."""
+    alphabet = "0123456789" * 3 + "..eE+-  \t\r0x"
+    text = _fuzz_fields(40000, 73 + grammar, alphabet)
+    check(hot_path, text, grammar=grammar)
+
+
+def test_digit_heavy_fuzz(hot_path):
+    """Mostly digits with at most a point and an exponent: lengths around
+    the 19-digit and 24-character limits of the straight-line tokenizer."""
+    rnd = random.Random(74)
+    lines = []
+    for _ in range(40000):
+        nd = rnd.randrange(1, 27)
+        digs = "".join(rnd.choice("0123456789") for _ in range(nd))
+        if rnd.random() < 0.6:
+            p = rnd.randrange(0, nd + 1)
+            digs = digs[:p] + "." + digs[p:]
+        if rnd.random() < 0.4:
+            digs += rnd.choice("eE") + rnd.choice(["", "+", "-"]) + str(rnd.randrange(0, 400))
+        if rnd.random() < 0.3:
+            digs = rnd.choice("+-") + digs
+        lines.append(digs)
+    n, pending = check(hot_path, "\n".join(lines).encode())
+    assert pending < n // 4
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_hex_floats(hot_path, f32):
+    """Hexadecimal floats (Appendix C's grammar option) and decimal fields
+    under the hexadecimal grammar."""
+    rnd = random.Random(75)
+    lines = []
+    for _ in range(20000):
+        m = "".join(rnd.choice("0123456789abcdefABCDEF") for _ in range(rnd.randrange(1, 20)))
+        if rnd.random() < 0.5:
+            p = rnd.randrange(0, len(m) + 1)
+            m = m[:p] + "." + m[p:]
+        s = rnd.choice(["", "-", "+"]) + rnd.choice(["0x", "0X"]) + m
+        if rnd.random() < 0.8:
+            s += rnd.choice("pP") + rnd.choice(["", "+", "-"]) + str(rnd.randrange(0, 1100))
+        lines.append(s)
+    lines += ["1.5", "-0.25e-3", "0x", "0x.p1", "0x1p", "0x1g", "0X1P-1074", "0x1p-1075",
+              "0x1.fffffffffffff8p1023", "0x1.fffffffffffff7p1023"]
+    check(hot_path, "\n".join(lines).encode(), f32, grammar=1)
+
+
+def test_hard_cases_decided_where_possible(hot_path):
+    """The hard-case mix: long fields go to the fallback kernel; the short
+    ones the hot path settles (17-25 digits near the range ends) must be
+    exact."""
+    n, pending = check(hot_path, workloads.hard_case_text(3000, workloads.SEED_BASE + 76))
+    assert pending < n
+
+
+def _exact_midpoints(count, seed):
+    """Midpoints between adjacent doubles of magnitude 2^49 .. 2^63 (unit in
+    the last place 2^-3 .. 2^10; below 10^19, so no 20-digit integers),
+    written exactly in decimal with at most 19
+    significant digits (so q lies in [-4, 23], the range of exact ties,
+    Section 6), and each one's neighbours one unit away in its last digit."""
+    import math
+    from decimal import Decimal, getcontext
+    getcontext().prec = 60
+    rnd = random.Random(seed)
+    out = []
+    while len(out) < count:
+        e = rnd.randrange(49, 63)
+        x = float(rnd.randrange(1 << 52, 1 << 53)) * 2.0 ** (e - 52)
+        h = Decimal(x) + Decimal(math.ulp(x)) / 2  # exact
+        digits, exp = h.as_tuple().digits, h.as_tuple().exponent
+        sig = "".join(map(str, digits)).rstrip("0")
+        if len(sig) > 19:
+            continue
+        last = Decimal(1).scaleb(exp)
+        for v in (h, h + last, h - last):
+            s = format(v, "f")
+            if "." not in s and rnd.random() < 0.5:  # trailing zeros as an exponent: q > 0
+                t = s.rstrip("0")
+                s = "%se%d" % (t, len(s) - len(t)) if len(t) < len(s) else s
+            out.append(s)
+    return out
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_exact_ties_and_their_neighbours(hot_path, f32):
+    """Ties go to the even significand (Algorithm 1's tie test, Sections 6,
+    8.1 and 9.1); one unit above or below in the last digit goes to that
+    side.  Half of them with a point, so q runs over [-4, 0] too."""
+    lines = _exact_midpoints(6000, 77)
+    lines += ["9007199254740993", "9007199254740995", "4503599627370496.5", "4503599627370497.5",
+              "2251799813685248.25", "2251799813685248.75", "1125899906842624.125"]
+    check(hot_path, "\n".join(lines).encode(), f32, max_pending=0)
