@@ -1,0 +1,81 @@
+// swar_check.cpp -- the word-wide byte tests of the device header, built for
+// the host, against byte-by-byte definitions: the zero-byte flags are exact
+// in every byte; the first non-digit flag is exact (the only one the
+// tokenizers use); two words of flags become the right 8-bit mask; four
+// ASCII digits give their value; the funnel shifts and the clamped left
+// shift match their definitions.  Prints "ok" or the first failure.
+#include <cstdio>
+#include <cstdint>
+#include <random>
+
+#include "fp_device.cuh"
+
+using namespace fp;
+
+namespace {
+
+uint8_t byte_of(uint32_t w, int i) { return (uint8_t)(w >> (8 * i)); }
+
+bool is_dig(uint8_t c) { return c >= '0' && c <= '9'; }
+
+int fail(const char* what, uint32_t a, uint32_t b = 0) {
+  std::printf("FAIL %s %08x %08x\n", what, a, b);
+  return 1;
+}
+
+}  // namespace
+
+int main() {
+  std::mt19937_64 rng(0x2101114081ull);
+  // a byte drawn to hit digits, their neighbours and the separators often
+  const uint8_t special[] = {'0', '1', '5', '9', '/', ':', '.', 'e', 'E', '+', '-', ' ', '\n',
+                             ',', 0, 0x7F, 0x80, 0xFF, 0x2F, 0x3A, 0xB0, 0xB9};
+  auto rand_byte = [&]() -> uint8_t {
+    const uint64_t r = rng();
+    return (r & 1) ? special[(r >> 1) % sizeof(special)] : (uint8_t)(r >> 8);
+  };
+  auto rand_word = [&]() -> uint32_t {
+    uint32_t w = 0;
+    for (int i = 0; i < 4; i++) w |= (uint32_t)rand_byte() << (8 * i);
+    return w;
+  };
+  for (int it = 0; it < 4000000; it++) {
+    const uint32_t w = rand_word();
+    // zero_bytes: 0x80 exactly in the zero bytes
+    const uint32_t z = zero_bytes(w);
+    for (int i = 0; i < 4; i++)
+      if ((byte_of(z, i) == 0x80) != (byte_of(w, i) == 0) || (byte_of(z, i) & 0x7F))
+        return fail("zero_bytes", w, z);
+    // nondigit_flags: the lowest flagged byte is the first non-digit
+    const uint32_t nd = nondigit_flags(w);
+    int first = -1;
+    for (int i = 0; i < 4 && first < 0; i++)
+      if (!is_dig(byte_of(w, i))) first = i;
+    const int flagged = nd ? ctz32(nd) / 8 : -1;
+    if (first != flagged || (nd & ~0x80808080u)) return fail("nondigit_flags", w, nd);
+    // the funnel shifts
+    const uint32_t w2 = rand_word();
+    const uint32_t sh = (uint32_t)(rng() % 32), n = (uint32_t)(rng() % 40);
+    const uint64_t cat = ((uint64_t)w2 << 32) | w;
+    if (fshr(w, w2, sh) != (uint32_t)(cat >> sh)) return fail("fshr", w, sh);
+    if (fshl_clamp(w, w2, n) != (uint32_t)((n >= 32 ? cat << 32 : cat << n) >> 32))
+      return fail("fshl_clamp", w, n);
+  }
+  // flag_pair: every pattern of flags in two words
+  for (uint32_t m = 0; m < 256; m++) {
+    uint32_t w0 = 0, w1 = 0;
+    for (int b = 0; b < 4; b++) {
+      if (m & (1u << b)) w0 |= 0x80u << (8 * b);
+      if (m & (1u << (4 + b))) w1 |= 0x80u << (8 * b);
+    }
+    if (flag_pair(w0, w1) != 128u * m) return fail("flag_pair", w0, w1);
+  }
+  // dig4: all four-digit strings, first byte most significant
+  for (uint32_t v = 0; v < 10000; v++) {
+    const uint32_t x = (uint32_t)('0' + v / 1000) | (uint32_t)('0' + v / 100 % 10) << 8 |
+                       (uint32_t)('0' + v / 10 % 10) << 16 | (uint32_t)('0' + v % 10) << 24;
+    if (dig4(x) != v) return fail("dig4", x, v);
+  }
+  std::printf("ok\n");
+  return 0;
+}

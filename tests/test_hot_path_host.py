@@ -202,3 +202,18 @@ def test_exact_ties_and_their_neighbours(hot_path, f32):
     lines += ["9007199254740993", "9007199254740995", "4503599627370496.5", "4503599627370497.5",
               "2251799813685248.25", "2251799813685248.75", "1125899906842624.125"]
     check(hot_path, "\n".join(lines).encode(), f32, max_pending=0)
+
+
+def test_word_wide_byte_tests():
+    """The tokenizers' word-wide byte tests (tests/native/swar_check.cpp)
+    against byte-by-byte definitions, on four million words."""
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if not cxx:
+        pytest.skip("no host C++ compiler")
+    import tempfile
+    with tempfile.TemporaryDirectory() as d:
+        exe = os.path.join(d, "swar_check")
+        subprocess.run([cxx, "-std=c++17", "-O2", "-Wall", "-Wno-unknown-pragmas", "-I", CSRC,
+                        "-o", exe, os.path.join(HERE, "native", "swar_check.cpp")], check=True)
+        r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
