@@ -9,13 +9,14 @@
 // One warp per field, all lanes on the same field:
 //   1. tokenize the whole field (Section 4 grammar, or the JSON one): its end
 //      from aligned 16-byte reads, 512 bytes per round; then one pass of
-//      byte ballots, 32 bytes per round, for the sign, point, digits and
-//      exponent marker, which also writes the significant digits to shared
-//      memory;
-//   2. Algorithm 1 on the 19-digit prefix w and on w+1 (one lane); equal
-//      results settle the field;
+//      byte ballots, 64 bytes per round, that checks the grammar and finds
+//      the exponent marker, the point and the first and last nonzero digit,
+//      from which every digit count follows;
+//   2. Algorithm 1 on the 19-digit prefix w (read from the text) and on w+1
+//      (two lanes); equal results settle the field;
 //   3. otherwise V = D 10^E with D the first 800 significant digits and one
-//      extra digit 1 appended when there are more (the last one is nonzero).
+//      extra digit 1 appended when there are more (the last one is nonzero),
+//      copied from the text to shared memory by the lanes together.
 //      Every midpoint between adjacent floating-point values has at most
 //      768 significant digits (Section 11), so V and the exact value lie on
 //      the same side of every midpoint;
