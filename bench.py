@@ -196,32 +196,34 @@ def cut_at_line(text: bytes, nbytes: int) -> bytes:
     return text[:k] if k > 0 else text[:nbytes]
 
 
-def oracle_time(sample: bytes, threads: int, f32: bool = False) -> float:
+def oracle_time(sample: bytes, threads: int, f32: bool = False, delim: bytes = b"\n",
+                grammar: int = 0) -> float:
     import oracle
     t = time.perf_counter()
-    oracle.parse_buffer(sample, b"\n", nthreads=threads, f32=f32)
+    oracle.parse_buffer(sample, delim, nthreads=threads, f32=f32, grammar=grammar)
     return time.perf_counter() - t
 
 
-def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0, f32: bool = False) -> dict:
+def cpu_baseline(text: bytes, kind: str = "bulk", seconds: float = 10.0, f32: bool = False,
+                 delim: bytes = b"\n", grammar: int = 0) -> dict:
     """The oracle on every host core, on a prefix of the workload sized for
     about `seconds` of work (from a 1 MB calibration), repeated when the
     whole text takes less."""
     cores = os.cpu_count() or 1
     calib = cut_at_line(text, 1 << 20)
-    rate = len(calib) / oracle_time(calib, cores, f32)
+    rate = len(calib) / oracle_time(calib, cores, f32, delim, grammar)
     sample = cut_at_line(text, int(min(64 << 20, max(1 << 20, rate * seconds))))
     passes = max(1, int(rate * seconds / max(len(sample), 1) / 4))
     t = time.perf_counter()
     for _ in range(passes):
-        oracle_time(sample, cores, f32)
+        oracle_time(sample, cores, f32, delim, grammar)
     dt = time.perf_counter() - t
     base = {"value": passes * len(sample) / dt / 1e9, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": "first %d bytes (%.2f MB, cut at a line break) of the %s workload, %d "
                       "pass(es), %d threads, %.2f s" % (len(sample), len(sample) / 1e6, kind,
                                                       passes, cores, dt)}
-    if not f32:
+    if not f32 and grammar == 0 and delim == b"\n":
         base["context"] = {"glibc_strtod": strtod_context(sample, cores)}
     return base
 
@@ -455,6 +457,151 @@ def run_ours(args, world, rank, dist) -> None:
         line["e2e"] = e2e
     if not args.skip_baseline:
         line["cpu_baseline"] = cpu_baseline(text, kind, f32=f32)
+    print(json.dumps(line), flush=True)
+
+
+EXT_WORKLOADS = {
+    "json": ("JSON numbers: the bulk mixed text (10M numbers newline-separated, every one a valid "
+             "JSON number) under the JSON number grammar (fp_parse_ex)"),
+    "hex": ("hexadecimal floats, 10M newline-separated: half float.hex() of uniform [0,1) "
+            "doubles, half of random finite binary64 bit patterns of either sign (fp_parse_ex, "
+            "hexadecimal grammar)"),
+    "columns": ("CSV to columns: 1.25M rows of 8 comma-separated uniform [0,1) %.17g values, "
+                "stored column-major, field i at column i mod 8, row i div 8 (fp_parse_ex)"),
+}
+
+
+def run_ext(args, world, rank, dist) -> None:
+    """The other grammars and the columnar layout (fp_parse_ex), measured
+    like the bulk line: text resident in HBM, larger than L2, K timed calls."""
+    import torch
+
+    import paper_2101_11408_gb300 as fp
+    from paper_2101_11408_gb300 import workloads
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fp._lib.load()
+    kind = args.workload
+    n = args.n or 10_000_000
+    columns, rows_cap, delim, grammar = 0, 0, b"\n", "decimal"
+    if kind == "json":
+        text = workloads.bulk_mixed_text(n, shard_seed(workloads.SEED_BASE + 2, rank))
+        grammar = "json"
+    elif kind == "hex":
+        text = workloads.hex_float_text(n, shard_seed(workloads.SEED_BASE + 6, rank))
+        grammar = "hex"
+    else:
+        columns = 8
+        rows_cap = n // columns
+        text = workloads.csv_columns_text(rows_cap, columns,
+                                          shard_seed(workloads.SEED_BASE + 7, rank))
+        delim = b","
+    gid = {"decimal": 0, "hex": 1, "json": 2}[grammar]
+    B = len(text)
+    d_text = torch.frombuffer(bytearray(text), dtype=torch.uint8).to(dev)
+    cap = columns * rows_cap if columns else B
+    out = torch.empty(cap, dtype=torch.float64, device=dev)
+    st = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def call():
+        fp.parse_ex_into(d_text, out, st, cnt, delim, grammar, columns, rows_cap, stream)
+
+    # one untimed call, checked against the oracle on a prefix of whole lines
+    call()
+    torch.cuda.synchronize()
+    N = int(cnt.item())
+    check_fields = 0
+    if rank == 0 and not args.skip_check:
+        import oracle
+        prefix = cut_at_line(text, 4 << 20)
+        rb, rs = oracle.parse_buffer(prefix, delim, grammar=gid)
+        k = rb.size
+        if columns:
+            i = np.arange(k)
+            where = (i % columns) * rows_cap + i // columns  # column-major slots
+            got = out.cpu().numpy().view(np.uint64)[where]
+            gst = st.cpu().numpy()[where]
+        else:
+            got = out[:k].cpu().numpy().view(np.uint64)
+            gst = st[:k].cpu().numpy()
+        if not (np.array_equal(got, rb) and np.array_equal(gst, rs)):
+            raise SystemExit("bench: GPU output differs from the oracle")
+        check_fields = int(k)
+    if fp.get_error():
+        raise SystemExit("bench: device error flag set")
+
+    sampler = ClockSampler(local).start() if rank == 0 else None
+    for _ in range(args.warmup):
+        call()
+    t_end = time.perf_counter() + args.clock_settle
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            call()
+        torch.cuda.synchronize()
+    fp.timing_enable(True)
+    fp.timing_read(stream)
+    fp.stats(reset=True, stream=stream)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        dist.barrier()
+    kt = fp.timing_read(stream)
+    fp.timing_enable(False)
+    s = fp.stats(reset=True, stream=stream)
+    clocks = sampler.stop() if sampler else None
+    if dist is not None:
+        elapsed_ms = max_over_ranks(dist, elapsed_ms, dev)
+    if rank != 0:
+        return
+    value = whole_job_gbs(world, B, args.steps, elapsed_ms)
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = B + 9 * N
+    parse_ms = kt["parse_ms"] / max(kt["calls"], 1)
+    fb_ms = kt["fallback_ms"] / max(kt["calls"], 1)
+    achieved = alg_bytes / (parse_ms / 1e3) / 1e9
+    mode = {"json": "MODE_JSON", "hex": "hexadecimal grammar", "columns": "MODE_COLUMNS"}[kind]
+    line = {
+        "metric": "GB/s of text parsed to binary64 (bit-exact), " + kind, "value": value,
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": EXT_WORKLOADS[kind], "numbers": N, "text_bytes": B,
+                   "grammar": grammar, "columns": columns, "rows_cap": rows_cap,
+                   "mfloats_per_s": world * N * args.steps / (elapsed_ms / 1e3) / 1e6,
+                   "l2": "no flush: each step reads %.0f MB of text and writes %.0f MB of "
+                         "results, more than the %.0f MB L2" % (B / 1e6, 9 * N / 1e6,
+                                                                L2_BYTES / 1e6),
+                   "parallelism": "replicas: one independent shard per GPU",
+                   "checked_fields": check_fields},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "parse_kernel (%s)" % mode, "kernel_ms": parse_ms,
+                     "fallback_kernel_ms": fb_ms, "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "path_counts_per_step": {k: s[k] // max(s["calls"], 1) for k in (
+            "fields", "one_multiply", "two_multiplies", "general_tokenizer", "long_fields",
+            "fallback")},
+        "e2e": None,
+        "e2e_note": "fp_parse_ex has no host-buffer form; the host-to-host path is "
+                    "fp_parse_f64_host (decimal grammar, the default line)",
+    }
+    if not args.skip_baseline:
+        line["cpu_baseline"] = cpu_baseline(text, kind, delim=delim, grammar=gid)
     print(json.dumps(line), flush=True)
 
 
@@ -921,11 +1068,13 @@ def main() -> None:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
-    ap.add_argument("--workload", choices=["bulk", "uniform", "hard", "batch", "serve"],
+    ap.add_argument("--workload", choices=["bulk", "uniform", "hard", "batch", "serve", "json",
+                                           "hex", "columns"],
                     default="bulk",
                     help="bulk: one 10M-number buffer (default); uniform: 10,000 numbers; hard: "
                          "1M hard cases; batch: 4096 uneven buffers; serve: Poisson request "
-                         "traces through the request server")
+                         "traces through the request server; json / hex / columns: fp_parse_ex "
+                         "under the JSON or hexadecimal grammar, or CSV to column-major")
     ap.add_argument("--serve-bodies", type=int, default=256, help="serve: distinct requests")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="serve: trace length")
     ap.add_argument("--serve-max-requests", type=int, default=60000)
@@ -954,6 +1103,8 @@ def main() -> None:
         run_batch(args, world, rank, dist)
     elif args.workload == "serve":
         run_serve(args, world, rank, dist)
+    elif args.workload in EXT_WORKLOADS:
+        run_ext(args, world, rank, dist)
     else:
         run_ours(args, world, rank, dist)
     if dist is not None:

@@ -237,6 +237,39 @@ def hard_case_text(n: int = 1_000_000, seed: int = SEED_BASE + 3) -> bytes:
 
 
 # ---------------------------------------------------------------------------
+# the other grammars and the columnar layout
+# ---------------------------------------------------------------------------
+
+def hex_float_lines(n: int, seed: int) -> list[str]:
+    """n hexadecimal floats (Python's float.hex, e.g. 0x1.921fb54442d18p+1):
+    half of uniform [0,1) doubles, half of random finite binary64 bit
+    patterns of either sign (subnormals and zeros included)."""
+    rng = _rng(seed)
+    k = n // 2
+    u = _uniform_doubles(rng, k)
+    bits = rng.integers(0, 0x7FF0000000000000, size=n - k, dtype=np.int64)
+    sign = rng.integers(0, 2, size=n - k).astype(np.int64) << 63
+    r = (bits | sign).view(np.float64)
+    vals = np.concatenate([u, r])
+    order = rng.permutation(n)
+    return [float(x).hex() for x in vals[order].tolist()]
+
+
+def hex_float_text(n: int = 10_000_000, seed: int = SEED_BASE + 6) -> bytes:
+    """The hexadecimal-float workload: n newline-separated values (about 21 B each)."""
+    return _cached("hex:%d:%d" % (n, seed), lambda: "\n".join(hex_float_lines(n, seed)).encode())
+
+
+def csv_columns_text(rows: int, cols: int = 8, seed: int = SEED_BASE + 7) -> bytes:
+    """rows lines of `cols` comma-separated uniform [0,1) %.17g values (the
+    served requests' content), for the column-major layout."""
+    def make():
+        vals = uniform_lines(rows * cols, seed)
+        return "\n".join(",".join(vals[r * cols:(r + 1) * cols]) for r in range(rows)).encode()
+    return _cached("csvcols:%d:%d:%d" % (rows, cols, seed), make)
+
+
+# ---------------------------------------------------------------------------
 # batched and served
 # ---------------------------------------------------------------------------
 

@@ -171,3 +171,27 @@ def test_paper_grammar_examples():
                 # and JSON rejects none of the plain spellings it allows
             n += 1
     assert n == 10
+
+
+def test_hex_float_text_round_trips():
+    """Appendix C's hexadecimal floats are dyadic, so parsing float.hex(x)
+    gives x exactly (Python's own conversion, independent of the oracle);
+    to binary32 it gives the one rounding of that exact value (numpy's),
+    with overflow to infinity and underflow to zero flagged.  Uniform
+    values, random finite bit patterns of both signs, subnormals, zeros."""
+    import numpy as np
+    from paper_2101_11408_gb300 import workloads
+    lines = workloads.hex_float_lines(20000, 91) + [
+        (5e-324).hex(), (-5e-324).hex(), (2.2250738585072014e-308).hex(), (0.0).hex(),
+        (-0.0).hex(), (1.7976931348623157e308).hex()]
+    text = "\n".join(lines).encode()
+    xs = np.array([float.fromhex(s) for s in lines])
+    bits, st = oracle.parse_buffer(text, grammar=oracle.GRAMMAR_HEX)
+    assert np.array_equal(bits, xs.view(np.uint64))
+    assert (st == 0).all()
+    b32, s32 = oracle.parse_buffer(text, f32=True, grammar=oracle.GRAMMAR_HEX)
+    with np.errstate(over="ignore", under="ignore"):
+        want = xs.astype(np.float32)
+    assert np.array_equal(b32, want.view(np.uint32))
+    want_st = np.where(np.isinf(want), 2, np.where((want == 0) & (xs != 0), 3, 0))
+    assert np.array_equal(s32, want_st.astype(np.uint8))
