@@ -164,6 +164,70 @@ def test_long_fields():
     assert_parity(join(lines), lines=lines)
 
 
+def _long_defects(rnd, count):
+    """Fields longer than the parse kernel's 64-byte limit (the fallback
+    kernel's), most with one defect -- a stray byte, a second point, a
+    blank, a sign, an empty or broken exponent -- at an offset on or next to
+    the fallback pass's 32- and 64-byte round boundaries, and valid
+    controls, leading zeros and points included."""
+    spots = [0, 1, 2, 31, 32, 33, 63, 64, 65, 95, 96, 97, 127, 128, 129, 191, 192, 193]
+    out = []
+    for _ in range(count):
+        n = rnd.randrange(66, 260)
+        d = "".join(rnd.choice("0123456789") for _ in range(n))
+        if rnd.random() < 0.3:
+            d = "0" * rnd.randrange(1, 40) + d
+        if rnd.random() < 0.6:
+            p = rnd.randrange(0, len(d) + 1)
+            d = d[:p] + "." + d[p:]
+        k = rnd.randrange(8)
+        at = min(rnd.choice(spots + [rnd.randrange(0, len(d))]), len(d) - 1)
+        if k == 0:
+            f = d[:at] + rnd.choice("x/:-+ ,") + d[at + 1:]
+        elif k == 1:
+            f = d[:at] + "." + d[at:]
+        elif k == 2:
+            f = d + rnd.choice(["e", "E", "e+", "e-", "e1x", "e--1", "ee1", "e 1"])
+        elif k == 3:
+            f = d[:at] + "e" + d[at:]  # the marker mid-significand: the rest is the exponent
+        elif k == 4:
+            f = d + "e" + str(rnd.randrange(-400, 400))
+        elif k == 5:
+            f = rnd.choice(["", "-", "+", " ", "\t"]) + d + rnd.choice(["", " ", "\r"])
+        elif k == 6:
+            f = d[:at] + "\t" + d[at:]
+        else:
+            f = d
+        out.append(f)
+    return out
+
+
+def test_long_malformed_fields():
+    """The fallback kernel's grammar checks agree with the oracle's on long
+    fields, valid or with one defect near its pass's round boundaries."""
+    lines = _long_defects(random.Random(123), 12000)
+    assert_parity(join(lines), lines=lines)
+
+
+def test_long_fields_json_grammar():
+    """The JSON number grammar on long fields (the fallback kernel's copy of
+    its rules): leading zeros, a point with no digit on one side, '+'."""
+    rnd = random.Random(124)
+    lines = _long_defects(rnd, 4000)
+    for _ in range(2000):
+        d = "".join(rnd.choice("0123456789") for _ in range(rnd.randrange(66, 200)))
+        lines += ["0" + d, "-0" + d, "0." + d, "." + d, d + ".", d + ".e5", "+" + d,
+                  d[:5] + "." + d[5:] + "E+12", "-" + d + "e-7"]
+    text = join(lines)
+    t = to_device(text)
+    vals, st = fp.parse_ex(t, grammar="json")
+    rb, rs = oracle.parse_buffer(text, grammar=oracle.GRAMMAR_JSON)
+    got = vals.cpu().numpy().view(np.uint64)
+    assert got.size == rb.size
+    bad = np.nonzero((got != rb) | (st.cpu().numpy() != rs))[0]
+    assert bad.size == 0, "first mismatch at %r" % lines[int(bad[0])][:90]
+
+
 def test_huge_single_field():
     """A 16 MB field: 1 + 10^-16M rounds to 1.0; its integer twin overflows."""
     n = 16 << 20
