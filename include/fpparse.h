@@ -22,6 +22,16 @@
  * reached that point.  Calls on the same stream are ordered.  Calls on
  * different streams may run concurrently; each stream gets its own scratch.
  *
+ * Host threads.  Every entry point may be called from any host thread; the
+ * library's shared state (the per-stream scratch table, the configuration,
+ * device properties) is guarded by one lock, held while a call queues its
+ * work.  A stream's scratch is reused by its next call, so calls on the SAME
+ * stream must not overlap in time across threads (fp_parse_f64_host keeps
+ * that stream's staging buffers while it copies); threads that each use
+ * their own stream need no coordination.  fp_set_config applies to calls
+ * that start after it returns.  A request server has its own scheduler
+ * thread and streams; its submit / wait calls may come from any thread.
+ *
  * Fields.  A field is a maximal run of bytes between separators, the
  * separators being '\n' and `delim` (pass '\n' for newline-only).  Field i of
  * the buffer is written to out_f64[i] / out_status[i].  A buffer ending in a
