@@ -373,8 +373,9 @@ FP_API fp_err_t fp_get_error(struct CUstream_st *stream);
  * (all streams).  chunk_bytes: text bytes per work tile (4096, 8192, 12288
  * or 16384; at the default 16384, fp_parse_f64 / fp_parse_f32 calls on
  * texts below 4 MB use 4096, so that more blocks share a small text);
- * ctas_per_sm: resident blocks per SM for the persistent grid (1..8);
- * fallback_queue: entries of the per-stream fallback queue (>= 1024).
+ * ctas_per_sm: resident blocks per SM for the persistent grid (1..8, or 0
+ * for as many as fit, the default; a value above what fits is capped);
+ * fallback_queue: entries of the per-stream fallback queue (1024 .. 2^28).
  * Returns FP_ERR_ARG for values outside those sets.
  */
 typedef struct {
@@ -392,7 +393,10 @@ FP_API fp_err_t fp_get_config(fp_config_t *cfg);
  * if cache_path is not NULL, write it to that file as one JSON object.  If
  * cache_path names an existing file written for the same GPU, its entry is
  * loaded instead and nothing is timed.  Synchronous; allocates temporary
- * output arrays with cudaMalloc.
+ * output arrays with cudaMalloc and frees them before returning.  While it
+ * times, the candidates are the current configuration (fp_set_config), so
+ * calls from other threads meanwhile may run under any of them; on an error
+ * the configuration from before the call is restored.
  */
 FP_API fp_err_t fp_autotune(const char *text, size_t len, char delim, const char *cache_path,
                      fp_config_t *chosen);

@@ -1050,16 +1050,17 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
   uint64_t* cnt = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  FP_CUDA(cudaMalloc(&out, len * sizeof(double)));
-  FP_CUDA(cudaMalloc(&st, len));
-  FP_CUDA(cudaMalloc(&cnt, sizeof(uint64_t)));
-  FP_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-  FP_CUDA(cudaEventCreate(&e0));
-  FP_CUDA(cudaEventCreate(&e1));
   fp_config_t best = cur;
   float best_ms = 1e30f;
   fp_err_t err = FP_OK;
+  // every resource is released below, also when one of these fails
+  if (cudaMalloc(&out, len * sizeof(double)) != cudaSuccess || cudaMalloc(&st, len) != cudaSuccess ||
+      cudaMalloc(&cnt, sizeof(uint64_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    err = FP_ERR_CUDA;
   for (uint32_t chunk : {8192u, 12288u, 16384u}) {
+    if (err != FP_OK) break;
     for (uint32_t per_sm : {1u, 2u, 3u, 4u, 0u}) {
       fp_config_t c = cur;
       c.chunk_bytes = chunk;
@@ -1082,8 +1083,9 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
       }
     }
   }
-  {
+  if (stream) {
     // release this temporary stream's scratch
+    cudaStreamSynchronize(stream);
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_scratch.find(std::make_pair(dev, stream));
     if (it != g_scratch.end()) {
@@ -1091,12 +1093,13 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
       g_scratch.erase(it);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (stream) cudaStreamDestroy(stream);
   cudaFree(out);
   cudaFree(st);
   cudaFree(cnt);
+  if (err == FP_ERR_CUDA) cudaGetLastError();  // reported by the return value
   if (err != FP_OK) {
     fp_set_config(&cur);
     return err;
