@@ -111,3 +111,51 @@ def test_host_entry_refuses_arrays_it_would_overrun():
             fp.parse_f64_host_into(text, v, s)
     with pytest.raises(TypeError):
         fp.parse_f64_host_into(text.astype(np.int8), ok_v, ok_s)
+
+
+def test_struct_layouts_and_constants_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field
+    offsets, and its constants the header's values: a C program built from
+    include/fpparse.h (as C11) prints them."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"fp_stats_t": _lib.Stats, "fp_config_t": _lib.Config,
+               "fp_server_config_t": _lib.ServerConfig, "fp_request_info_t": _lib.RequestInfo,
+               "fp_server_stats_t": _lib.ServerStats, "fp_options_t": _lib.Options}
+    consts = {"FP_OK": _lib.FP_OK, "FP_ERR_ARG": _lib.FP_ERR_ARG,
+              "FP_ERR_CAPACITY": _lib.FP_ERR_CAPACITY, "FP_ERR_CUDA": _lib.FP_ERR_CUDA,
+              "FP_ERR_BUDGET": _lib.FP_ERR_BUDGET, "FP_ERR_TIMEOUT": _lib.FP_ERR_TIMEOUT,
+              "FP_ERR_INTERNAL": _lib.FP_ERR_INTERNAL, "FP_STATUS_OK": _lib.STATUS_OK,
+              "FP_STATUS_INVALID": _lib.STATUS_INVALID, "FP_STATUS_OVERFLOW": _lib.STATUS_OVERFLOW,
+              "FP_STATUS_UNDERFLOW": _lib.STATUS_UNDERFLOW,
+              "FP_STATUS_BAD_SHAPE": _lib.STATUS_BAD_SHAPE, "FP_FORMAT_F64": _lib.FORMAT_F64,
+              "FP_FORMAT_F32": _lib.FORMAT_F32, "FP_GRAMMAR_DECIMAL": _lib.GRAMMAR_DECIMAL,
+              "FP_GRAMMAR_HEX": _lib.GRAMMAR_HEX, "FP_GRAMMAR_JSON": _lib.GRAMMAR_JSON}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "fpparse.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('  printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    for name in consts:
+        lines.append('  printf("%s %%lld\\n", (long long)%s);' % (name, name))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = str(tmp_path / "abi")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, str(src)], check=True)
+    out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            *key, val = ln.split(" ")
+            got[" ".join(key)] = int(val)
+    for name, cls in structs.items():
+        assert got[name + " size"] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got["%s %s" % (name, field)] == getattr(cls, field).offset, (name, field)
+    for name, v in consts.items():
+        assert got[name] == v, name
