@@ -159,3 +159,20 @@ def test_struct_layouts_and_constants_match_the_header(tmp_path):
             assert got["%s %s" % (name, field)] == getattr(cls, field).offset, (name, field)
     for name, v in consts.items():
         assert got[name] == v, name
+
+
+def test_c_program_links_and_calls_the_library(tmp_path):
+    """A plain C program (tests/native/c_client.c) links against the
+    library and gets the header's answers from the calls that need no GPU."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lib = _lib.library_path()
+    exe = str(tmp_path / "c_client")
+    subprocess.run([cc, "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", exe, os.path.join(ROOT, "tests", "native", "c_client.c"),
+                    lib, "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
