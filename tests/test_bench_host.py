@@ -99,3 +99,19 @@ def test_reference_arm_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_fields():
+    """The bench line's cpu_baseline: the oracle on all host cores on a
+    bounded prefix, with the strtod context for the default grammar only."""
+    from paper_2101_11408_gb300 import workloads
+    text = workloads.bulk_mixed_text(100000, workloads.SEED_BASE + 81)
+    b = bench.cpu_baseline(text, "bulk", seconds=0.3)
+    assert b["kind"] == "oracle" and b["unit"] == "GB/s" and b["value"] > 0
+    assert b["cores"] == (os.cpu_count() or 1) and "bulk workload" in b["sample"]
+    assert b["context"]["glibc_strtod"]["value"] > 0
+    j = bench.cpu_baseline(text, "json", seconds=0.2, grammar=2)
+    assert j["value"] > 0 and "context" not in j
+    c = bench.cpu_baseline(workloads.csv_columns_text(2000, 8, 5), "columns", seconds=0.2,
+                           delim=b",")
+    assert c["value"] > 0 and "context" not in c
