@@ -217,3 +217,32 @@ def test_word_wide_byte_tests():
                         "-o", exe, os.path.join(HERE, "native", "swar_check.cpp")], check=True)
         r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def test_hot_path_under_sanitizers(tmp_path):
+    """The device header's per-field arithmetic, built for the host with
+    AddressSanitizer and UndefinedBehaviorSanitizer: no read outside the
+    padded tile, no oversized shift or signed overflow, on bulk fields, the
+    grammar fuzz, exact ties, range boundaries and hexadecimal floats."""
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("no g++")
+    exe = str(tmp_path / "hot_path_san")
+    r = subprocess.run([cxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined",
+                        "-fno-sanitize-recover=undefined", "-Wno-unknown-pragmas", "-I", CSRC,
+                        "-o", exe, os.path.join(HERE, "native", "hot_path_check.cpp")],
+                       capture_output=True, text=True)
+    if r.returncode:
+        pytest.skip("sanitizer runtime not available: " + r.stderr.strip()[:200])
+    texts = [workloads.bulk_mixed_text(10000, workloads.SEED_BASE + 78),
+             _fuzz_fields(10000, 79, "0123456789" * 3 + "..eE+-  \t\r0x"),
+             "\n".join(_exact_midpoints(1000, 80)).encode(),
+             "\n".join("%de%d" % (d, e) for d in (1, 9, 47, 99) for e in range(-400, 400)).encode(),
+             workloads.hex_float_text(3000, workloads.SEED_BASE + 82)]
+    for t in texts:
+        for fmt in ("64", "32"):
+            for grammar in ("0", "1", "2"):
+                r = subprocess.run([exe, fmt, grammar], input=t, capture_output=True, timeout=300)
+                err = r.stderr.decode()
+                assert r.returncode == 0 and "runtime error" not in err and "Sanitizer" not in err, \
+                    err[:2000]
