@@ -26,3 +26,23 @@ def test_arena_matches_bitmap_model(arena_check, cap, steps, seed):
     r = subprocess.run([arena_check, str(cap), str(steps), str(seed)], capture_output=True,
                        text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+def test_arena_under_sanitizers(tmp_path):
+    """The same model check built with AddressSanitizer and
+    UndefinedBehaviorSanitizer."""
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("no g++")
+    exe = str(tmp_path / "arena_check_san")
+    r = subprocess.run([cxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined",
+                        "-fno-sanitize-recover=undefined", "-Wall", "-Werror", "-o", exe,
+                        os.path.join(HERE, "native", "arena_check.cpp")],
+                       capture_output=True, text=True)
+    if r.returncode:
+        pytest.skip("sanitizer runtime not available: " + r.stderr.strip()[:200])
+    for cap, steps, seed in ((64, 20000, 1), (4096, 60000, 2), (1, 1000, 4)):
+        r = subprocess.run([exe, str(cap), str(steps), str(seed)], capture_output=True, text=True,
+                           timeout=300)
+        assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+        assert "runtime error" not in r.stderr, r.stderr
