@@ -246,3 +246,51 @@ def test_hot_path_under_sanitizers(tmp_path):
                 err = r.stderr.decode()
                 assert r.returncode == 0 and "runtime error" not in err and "Sanitizer" not in err, \
                     err[:2000]
+
+
+HOT_MUTANTS = [
+    ("tie range", "static constexpr int TIE_QMIN = -4, TIE_QMAX = 23;",
+     "static constexpr int TIE_QMIN = -4, TIE_QMAX = 22;"),
+    ("point's exponent", "t.q = ex - (dpos >= 0 ? 23 - dpos : 0);",
+     "t.q = ex - (dpos >= 0 ? 22 - dpos : 0);"),
+    ("rounding step", "  m += (m & 1);\n  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))",
+     "  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))"),
+    ("19-digit truncation", "      exp_adj++;\n      sticky |= (d != 0);", "      sticky |= (d != 0);"),
+    ("w+1 check", "    ElResult b = convert_wq<F>(w + 1, q, tab, true);",
+     "    ElResult b = convert_wq<F>(w, q, tab, true);"),
+    ("JSON leading zero",
+     "    ok = ok && nint > 0 && !(nint > 1 && s[int_start] == '0') && !(point && ndig == nint);",
+     "    ok = ok && nint > 0 && !(point && ndig == nint);"),
+]
+
+
+@pytest.mark.parametrize("what,old,new", HOT_MUTANTS, ids=[m[0] for m in HOT_MUTANTS])
+def test_planted_slip_in_the_hot_path_is_caught(tmp_path, what, old, new):
+    """Each slip planted in a host copy of the device header fails one of the
+    checks above (bulk fields, range boundaries, digit-heavy and grammar
+    fuzz, exact ties, hard cases)."""
+    cxx = shutil.which("g++")
+    if not cxx:
+        pytest.skip("no g++")
+    d = tmp_path / "csrc"
+    shutil.copytree(CSRC, d, ignore=shutil.ignore_patterns("*.o", "*.so", "_build"))
+    hdr = d / "fp_device.cuh"
+    src = hdr.read_text()
+    assert src.count(old) == 1, what
+    hdr.write_text(src.replace(old, new))
+    exe = str(tmp_path / "hot_mutant")
+    subprocess.run([cxx, "-std=c++17", "-O2", "-Wno-unknown-pragmas", "-I", str(d), "-o", exe,
+                    os.path.join(HERE, "native", "hot_path_check.cpp")], check=True)
+    checks = [lambda: check(exe, workloads.bulk_mixed_text(30000, workloads.SEED_BASE + 71)),
+              lambda: test_decimal_range_boundaries(exe, False),
+              lambda: test_digit_heavy_fuzz(exe),
+              lambda: test_exact_ties_and_their_neighbours(exe, False),
+              lambda: test_grammar_fuzz(exe, 2),
+              lambda: test_hard_cases_decided_where_possible(exe)]
+    caught = 0
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, what
