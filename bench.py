@@ -818,6 +818,39 @@ def _percentile_ms(lat_ns, q):
 SERVE_RING_BYTES = 1 << 32  # pinned result space of the serving bench's client
 
 
+class ResultRing:
+    """Byte regions of a ring of `cap` bytes, handed out in request order:
+    each starts where the newest held one ends, or at the ring's start when
+    it does not fit there, and the oldest held regions are given back (their
+    requests waited for, by `release(tag)`) only until the new one fits."""
+
+    def __init__(self, cap: int):
+        self.cap = cap
+        self.held = collections.deque()  # (start, end, tag), oldest first
+        self.head = 0                    # the end of the newest region
+
+    def reserve(self, need: int, tag, release) -> int:
+        if need > self.cap:
+            raise ValueError("region larger than the ring")
+        start = 0
+        while self.held:
+            tail = self.held[0][0]
+            if self.held[-1][0] >= tail:  # held: [tail, head)
+                if self.head + need <= self.cap:
+                    start = self.head
+                    break
+                if need <= tail:
+                    start = 0
+                    break
+            elif self.head + need <= tail:  # held: [tail, cap) and [0, head)
+                start = self.head
+                break
+            release(self.held.popleft()[2])
+        self.held.append((start, start + need, tag))
+        self.head = start + need
+        return start
+
+
 def run_serve(args, world, rank, dist) -> None:
     """The request server against the plain per-request path, both fed the
     same Poisson arrival traces of host-memory requests."""
@@ -884,41 +917,24 @@ def run_serve(args, world, rank, dist) -> None:
         t0 = time.monotonic_ns() + 2_000_000
         infos = [None] * n
         rids = [0] * n
-        held = collections.deque()  # (start, end, request), oldest first
-        head = 0                    # the end of the newest region
         where = [0] * n
+        results = ResultRing(SERVE_RING_BYTES)
 
-        def reserve(need):
-            """Start of `need` free bytes after the newest region (or at the
-            ring's start), waiting for the oldest requests until they fit."""
-            nonlocal head
-            while held:
-                tail = held[0][0]
-                if held[-1][0] >= tail:  # held: [tail, head)
-                    if head + need <= SERVE_RING_BYTES:
-                        return head
-                    if need <= tail:
-                        return 0
-                elif head + need <= tail:  # held: [tail, end) and [0, head)
-                    return head
-                _, _, p = held.popleft()
-                if infos[p] is None:
-                    infos[p] = srv.wait(rids[p])
-            return 0
+        def release(p):  # request p's region is reused: wait for it first
+            if infos[p] is None:
+                infos[p] = srv.wait(rids[p])
 
         for i in range(n):
             j = int(order[i])
             fields = bodies[j][3]
             need = (9 * fields + 63) // 64 * 64
-            a = reserve(need)
+            a = results.reserve(need, i, release)
             ta = t0 + int(arr_ns[i])
             while time.monotonic_ns() < ta:
                 pass
             v, s_ = ring_views(a, fields)
             rids[i] = srv.submit(bodies[j][0], v, s_)
-            held.append((a, a + need, i))
             where[i] = a
-            head = a + need
         for i in range(n):
             if infos[i] is None:
                 infos[i] = srv.wait(rids[i])
