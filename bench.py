@@ -1068,7 +1068,7 @@ def run_serve(args, world, rank, dist) -> None:
     print(json.dumps(line), flush=True)
 
 
-def main() -> None:
+def make_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
@@ -1102,6 +1102,11 @@ def main() -> None:
                     help="bulk/uniform/hard: binary64 (fp_parse_f64) or binary32 (fp_parse_f32)")
     ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")
     ap.add_argument("--batch-bytes", type=int, default=2 << 30, help="batch: total text bytes")
+    return ap
+
+
+def main() -> None:
+    ap = make_parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

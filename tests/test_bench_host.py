@@ -149,3 +149,24 @@ def test_result_ring_never_overlaps_a_held_region(seed):
     assert released == sorted(released)
     with pytest.raises(ValueError):
         ring.reserve(cap + 1, -1, release)
+
+
+def test_profile_commands_run_committed_files():
+    """Every profile summary gives the command that made it; each bench
+    invocation there still parses with the bench's current arguments, and
+    each ncu line keeps its clocks unlocked."""
+    import glob
+    import shlex
+    found = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as f:
+            text = f.read().replace("\\\n", " ")
+        for line in text.splitlines():
+            if "ncu " in line:
+                assert "--clock-control none" in line, (path, line)
+            if "python bench.py" not in line:
+                continue
+            argv = shlex.split(line.split("python bench.py", 1)[1])
+            bench.make_parser().parse_args(argv)  # exits on an unknown flag
+            found += 1
+    assert found >= 3
