@@ -88,3 +88,21 @@ def test_packed_buffers_layout():
     for (s0, t0), s1 in zip(zip(starts, texts), starts[1:]):
         assert s0 + len(t0) + 16 <= s1  # digits between neighbours
         assert set(bytes(arr[s0 + len(t0):s1])) == {ord("7")}
+
+
+def test_midpoint_decimal_is_the_exact_midpoint():
+    """The constructed midpoints the pins and parity tests use are exact:
+    digits * 10^exp10 == (x + next(x)) / 2 in rational arithmetic, for
+    normal and subnormal patterns, zero, and DBL_MAX (next = 2^1024)."""
+    import struct
+    from fractions import Fraction
+    rng = np.random.Generator(np.random.PCG64(71))
+    pats = [int(b) for b in rng.integers(0, 0x7FEFFFFFFFFFFFFF, size=400, dtype=np.int64)]
+    pats += [0, 1, 0x000FFFFFFFFFFFFF, 0x0010000000000000, 0x7FEFFFFFFFFFFFFF]
+    for b in pats:
+        digits, e10 = w.midpoint_decimal(b)
+        x = Fraction(struct.unpack("<d", struct.pack("<Q", b))[0])
+        nxt = Fraction(2) ** 1024 if b == 0x7FEFFFFFFFFFFFFF else \
+            Fraction(struct.unpack("<d", struct.pack("<Q", b + 1))[0])
+        assert Fraction(int(digits)) * Fraction(10) ** e10 == (x + nxt) / 2, hex(b)
+        assert not digits.endswith("0") or digits == "0"
