@@ -8,7 +8,9 @@
 // block.  Blocks take chunk tickets in turn, so a chunk's look-back reads
 // other blocks' words.  The text is placed at a chosen offset modulo 16.
 //
-// usage: parse_block_emu <64|32> <grammar 0|1> <chunk bytes> <offset 0..15> [blocks] < text
+// usage: parse_block_emu <64|32> <grammar 0|1|2> <chunk bytes> <offset 0..15> [blocks
+//        [columns rows_cap]] < text   (grammar 2 runs the JSON mode; columns K >= 2
+//        the column-major mode, '\n' rows of K ','-separated fields)
 // One line per field: "<bits hex> <status>" as stored (pending fields keep
 // their location word and a pending status), then "count <n>".
 #include <ucontext.h>
@@ -169,11 +171,15 @@ inline uint8_t* emu_block_smem() { return emu_smem_all[emu::cur / emu::BT]; }
 
 namespace {
 fp::LaunchParams g_p;
-int g_f32 = 0, g_chunk = 16384;
+int g_f32 = 0, g_chunk = 16384, g_mode = 0;
 
 template <int C, class F>
 void body() {
-  fp::parse_kernel<C, F, 0>(g_p);
+  switch (g_mode) {
+    case fp::MODE_JSON: fp::parse_kernel<C, F, fp::MODE_JSON>(g_p); break;
+    case fp::MODE_COLUMNS: fp::parse_kernel<C, F, fp::MODE_COLUMNS>(g_p); break;
+    default: fp::parse_kernel<C, F, 0>(g_p); break;
+  }
 }
 void thread_entry(int t) {
   (void)t;
@@ -270,11 +276,13 @@ bool run_block() {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 5 && argc != 6) {
+  if (argc != 5 && argc != 6 && argc != 8) {
     std::fprintf(stderr, "usage: %s <64|32> <grammar> <chunk> <offset> [blocks]\n", argv[0]);
     return 2;
   }
-  emu::nblocks = argc == 6 ? std::atoi(argv[5]) : 1;
+  emu::nblocks = argc >= 6 ? std::atoi(argv[5]) : 1;
+  const unsigned long long columns = argc == 8 ? std::strtoull(argv[6], nullptr, 10) : 0;
+  const unsigned long long rows_cap = argc == 8 ? std::strtoull(argv[7], nullptr, 10) : 0;
   if (emu::nblocks < 1 || emu::nblocks > emu::MAXB) return 2;
   emu::nthreads = emu::nblocks * emu::BT;
   g_f32 = std::atoi(argv[1]) == 32;
@@ -286,6 +294,8 @@ int main(int argc, char** argv) {
   size_t got;
   while ((got = std::fread(buf, 1, sizeof(buf), stdin)) > 0) text.append(buf, got);
   const size_t len = text.size();
+  g_mode = columns ? fp::MODE_COLUMNS : (grammar == fp::GRAMMAR_JSON ? fp::MODE_JSON : 0);
+  const size_t cap = columns ? columns * rows_cap : len;
   // the text at `offset` modulo 16, with digits around it (never used)
   std::vector<uint8_t> mem(len + 256, '7');
   uint8_t* a16 = mem.data() + ((16 - (reinterpret_cast<uintptr_t>(mem.data()) & 15)) & 15) + 64;
@@ -294,9 +304,9 @@ int main(int argc, char** argv) {
   const unsigned long long o = reinterpret_cast<uintptr_t>(tp) & 15;
   unsigned long long nch = (o + len + g_chunk - 1) / g_chunk;
   if (nch == 0) nch = 1;
-  std::vector<unsigned long long> out(len + 1, 0x5A5A5A5A5A5A5A5Aull), loc(len + 1, 0),
+  std::vector<unsigned long long> out(cap + 1, 0x5A5A5A5A5A5A5A5Aull), loc(len + 1, 0),
       chunk_status(nch, 0), queue(1 << 20), ovf(2 * nch);
-  std::vector<uint8_t> status(len + 1, 0xEE);
+  std::vector<uint8_t> status(cap + 1, 0xEE);
   static fp::Ctl ctl;
   std::memset(&ctl, 0, sizeof(ctl));
   unsigned long long count = ~0ull;
@@ -308,10 +318,10 @@ int main(int argc, char** argv) {
   p.one.chunk0 = 0;
   p.one.nchunks = nch;
   p.one.out_base = 0;
-  p.one.out_cap = len;
+  p.one.out_cap = columns ? columns * rows_cap : len;  // as fp_parse_ex sets it
   p.one.out_count = &count;
   p.nbuf = 1;
-  p.delim = '\n';
+  p.delim = columns ? ',' : '\n';
   p.total_chunks = nch;
   p.out_bits = out.data();
   p.out_status = status.data();
@@ -324,6 +334,12 @@ int main(int argc, char** argv) {
   p.ovf_cap = nch;
   p.loc = g_f32 ? loc.data() : p.out_bits;
   p.grammar = grammar;
+  if (columns) {
+    p.columns = (unsigned int)columns;
+    p.rows_cap = rows_cap;
+    p.col_magic = (unsigned long long)((((unsigned __int128)1 << 64) + columns - 1) / columns);
+    p.loc = loc.data();  // pending locations beside the column-major results
+  }
   if (!run_block()) {
     std::printf("EMULATION %s\n", emu::why);
     return 1;
@@ -333,9 +349,11 @@ int main(int argc, char** argv) {
     return 1;
   }
   for (unsigned long long i = 0; i < count && i < len; i++) {
+    // field i's slot: i, or column i mod K, row i div K
+    const unsigned long long k = columns ? (i % columns) * rows_cap + i / columns : i;
     const unsigned long long b =
-        g_f32 ? (unsigned long long)reinterpret_cast<const uint32_t*>(out.data())[i] : out[i];
-    std::printf("%016llx %u\n", b, (unsigned)status[i]);
+        g_f32 ? (unsigned long long)reinterpret_cast<const uint32_t*>(out.data())[k] : out[k];
+    std::printf("%016llx %u\n", b, (unsigned)status[k]);
   }
   std::printf("count %llu\n", count);
   return 0;

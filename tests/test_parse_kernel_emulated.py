@@ -45,14 +45,15 @@ def emu(tmp_path_factory):
 
 
 def _check(exe, text: bytes, f32=False, grammar=0, chunk=16384, offset=0, max_pending=None,
-           blocks=1):
+           blocks=1, columns=0, rows_cap=0):
+    extra = [str(columns), str(rows_cap)] if columns else []
     r = subprocess.run([exe, "32" if f32 else "64", str(grammar), str(chunk), str(offset),
-                        str(blocks)], input=text, capture_output=True, timeout=600)
+                        str(blocks)] + extra, input=text, capture_output=True, timeout=600)
     out = r.stdout.decode().split("\n")[:-1]
     assert r.returncode == 0, out[-1:] + [r.stderr.decode()[-800:]]
     assert out[-1].startswith("count ")
     n = int(out[-1].split()[1])
-    rb, rs = oracle.parse_buffer(text, f32=f32, grammar=grammar)
+    rb, rs = oracle.parse_buffer(text, b"," if columns else b"\n", f32=f32, grammar=grammar)
     assert n == rb.size, (n, rb.size)
     pending = 0
     for i in range(n):
@@ -62,7 +63,7 @@ def _check(exe, text: bytes, f32=False, grammar=0, chunk=16384, offset=0, max_pe
             pending += 1
             continue
         assert (int(b, 16), s) == (int(rb[i]), int(rs[i])), \
-            (i, text.split(b"\n")[i][:80], out[i], hex(int(rb[i])), int(rs[i]))
+            (i, out[i], hex(int(rb[i])), int(rs[i]))
     if max_pending is not None:
         assert pending <= max_pending, pending
     return n, pending
@@ -125,3 +126,21 @@ def test_several_blocks_look_back_across_blocks(emu, blocks, chunk):
     rnd = random.Random(blocks)
     dense = "\n".join(rnd.choice(["1", "", "2.5", "x", "-3e2"]) for _ in range(40000)).encode()
     _check(emu, dense, chunk=chunk, offset=1, blocks=blocks, max_pending=0)
+
+
+def test_json_mode(emu):
+    """The kernel's JSON mode (its fast-path check of the JSON number rules)."""
+    rnd = random.Random(102)
+    lines = workloads.bulk_mixed_lines(6000, 103) + [
+        rnd.choice(["+1", "01", "1.", ".5", "-0", "0.0", "1e5", "-1.5E-3", "00", "0e0", "-", "1.e2"])
+        for _ in range(3000)]
+    rnd.shuffle(lines)
+    _check(emu, "\n".join(lines).encode(), grammar=2, offset=4, max_pending=0, blocks=2)
+
+
+def test_column_major_mode(emu):
+    """The column-major mode on well-formed rows: field i at column i mod 8,
+    row i div 8 (a row's last field ends at '\n', the others at ',').
+    Rows of the wrong shape (BAD_SHAPE) are the GPU tests' part."""
+    text = workloads.csv_columns_text(3000, 8, 104)
+    _check(emu, text, grammar=0, offset=8, columns=8, rows_cap=3000, max_pending=0, blocks=2)
