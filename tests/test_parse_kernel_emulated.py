@@ -144,3 +144,35 @@ def test_column_major_mode(emu):
     Rows of the wrong shape (BAD_SHAPE) are the GPU tests' part."""
     text = workloads.csv_columns_text(3000, 8, 104)
     _check(emu, text, grammar=0, offset=8, columns=8, rows_cap=3000, max_pending=0, blocks=2)
+
+
+def test_whole_path_on_the_hard_mix(emu, tmp_path):
+    """Both kernels' code end to end on the CPU: the emulated parse kernel
+    decides what it can and queues the rest (their statuses say so); the
+    fallback kernel's per-field code, emulated, decides each queued field.
+    Together every field of the hard-case mix equals the oracle."""
+    from test_fallback_emulated import _body
+    d = tmp_path / "fb"
+    d.mkdir()
+    (d / "fallback_body.inc").write_text(_body())
+    fb = str(d / "fallback_emu")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-Wno-unknown-pragmas", "-Wno-unused-function",
+                    "-I", str(d), "-I", CSRC, "-o", fb,
+                    os.path.join(HERE, "native", "fallback_emu.cpp")], check=True)
+    lines = workloads.hard_case_lines(1500, workloads.SEED_BASE + 105)
+    text = "\n".join(lines).encode()
+    r = subprocess.run([emu, "64", "0", "16384", "5", "2"], input=text, capture_output=True,
+                       timeout=600, check=True)
+    out = r.stdout.decode().split("\n")[:-2]  # without the count line
+    assert len(out) == len(lines)
+    results = [tuple(int(x, 16) if j == 0 else int(x) for j, x in enumerate(ln.split()))
+               for ln in out]
+    queued = [i for i, (_, s) in enumerate(results) if s == ST_PENDING_QUEUED]
+    assert queued
+    r = subprocess.run([fb, "64", "0"], input="\n".join(lines[i] for i in queued).encode(),
+                       capture_output=True, timeout=600, check=True)
+    for i, ln in zip(queued, r.stdout.decode().split("\n")):
+        b, s = ln.split()
+        results[i] = (int(b, 16), int(s))
+    rb, rs = oracle.parse_buffer(text)
+    assert [(int(b), int(s)) for b, s in zip(rb, rs)] == results
