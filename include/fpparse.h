@@ -390,13 +390,22 @@ FP_API fp_err_t fp_get_config(fp_config_t *cfg);
  * fp_autotune -- time the candidate configurations on a device buffer
  * supplied by the caller (text/len as for fp_parse_f64; it should be
  * representative of the workload), pick the fastest, make it current and,
- * if cache_path is not NULL, write it to that file as one JSON object.  If
- * cache_path names an existing file written for the same GPU, its entry is
- * loaded instead and nothing is timed.  Synchronous; allocates temporary
- * output arrays with cudaMalloc and frees them before returning.  While it
- * times, the candidates are the current configuration (fp_set_config), so
- * calls from other threads meanwhile may run under any of them; on an error
- * the configuration from before the call is restored.
+ * if cache_path is not NULL, record it in that file.  The candidates: chunk
+ * sizes 4096, 8192, 12288 and 16384 x blocks per SM 1, 2, 3, 4 or all that
+ * fit; then, for the fastest of those, fallback queue depths 2^16, 2^18,
+ * 2^20 and 2^22 (the smallest within 2% of the fastest is kept).  The
+ * mapping of threads to numbers is fixed by field class and not tuned: one
+ * thread per field of up to 30 bytes, one warp per field in the fallback.
+ * The cache holds one JSON object per line, keyed by the GPU's name and the
+ * workload's class: the text's size (below 4 MB, below 64 MB, larger) and
+ * the share of its fields that reach the fallback kernel (below 0.1%,
+ * below 10%, more), measured by one untimed call first.  If the file holds
+ * an entry for the same GPU and class, it is loaded instead and nothing
+ * else is timed.  Synchronous; allocates temporary output arrays with
+ * cudaMalloc and frees them before returning.  While it times, the
+ * candidates are the current configuration (fp_set_config), so calls from
+ * other threads meanwhile may run under any of them; on an error the
+ * configuration from before the call is restored.
  */
 FP_API fp_err_t fp_autotune(const char *text, size_t len, char delim, const char *cache_path,
                      fp_config_t *chosen);
@@ -451,11 +460,19 @@ FP_API fp_err_t fp_parse_f64_host(const char *host_text, size_t len, char delim,
  *   may not allocate once running -- fixed-memory or certified processes,
  *   plugins whose host owns all allocations, services that must not fail on
  *   an allocation mid-request.
- *   Limits: at most 65,536 chunks of the current chunk size (len + (text % 16)
- *   <= 65,536 * chunk_bytes: 1 GiB at the default 16 KiB chunks); beyond that
- *   it returns FP_ERR_CAPACITY and queues nothing.  The first call on each
- *   device looks up the array's device address (cudaGetSymbolAddress) and the
- *   launch shape.
+ *   Limits: len < 2^40 (else FP_ERR_ARG), and at most 65,536 chunks of the
+ *   current chunk size (len + (text % 16) <= 65,536 * chunk_bytes: 1 GiB at
+ *   the default 16 KiB chunks; texts below 4 MB use 4 KiB chunks, as
+ *   fp_parse_f64 does); beyond that it returns FP_ERR_CAPACITY.  Both checks
+ *   come before any CUDA call, so a refused call queues nothing.  The first
+ *   call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) and the launch shape.  Under CUDA's lazy module
+ *   loading (CUDA_MODULE_LOADING=LAZY, the default) the library's device
+ *   code, and with it the array, is loaded on a device only when first used,
+ *   which can allocate device memory at that moment: a caller that must not
+ *   allocate once running makes one call (len 0 is enough) on each device at
+ *   start-up, or runs with CUDA_MODULE_LOADING=EAGER.  Later calls allocate
+ *   nothing.
  *   Every call on every stream shares the one array and clears its control
  *   part on `stream` first: calls whose work overlaps on the GPU (different
  *   streams without ordering) race and give wrong results.  Order them, or

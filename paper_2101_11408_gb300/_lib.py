@@ -17,14 +17,14 @@ STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW, STATUS_BAD_SHAPE =
 FORMAT_F64, FORMAT_F32 = 0, 1
 GRAMMAR_DECIMAL, GRAMMAR_HEX, GRAMMAR_JSON = 0, 1, 2
 
-# every symbol include/fpparse.h declares
+# every symbol include/*.h declares (fpparse_test.h: test hooks)
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_ex", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
            "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
            "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_batch_plan_gather",
            "fp_server_create", "fp_server_submit",
            "fp_server_wait", "fp_server_get_stats", "fp_server_destroy", "fp_shutdown",
-           "fp_strerror"]
+           "fp_strerror", "fp_test_arm_stalled_lookback"]
 
 
 class Stats(ctypes.Structure):
@@ -153,6 +153,8 @@ def load(build_if_missing: bool = True):
         lib.fp_server_destroy.restype = ctypes.c_int
         lib.fp_shutdown.argtypes = []
         lib.fp_shutdown.restype = ctypes.c_int
+        lib.fp_test_arm_stalled_lookback.argtypes = [vp, ctypes.c_uint64]
+        lib.fp_test_arm_stalled_lookback.restype = ctypes.c_int
         lib.fp_strerror.argtypes = [ctypes.c_int]
         lib.fp_strerror.restype = ctypes.c_char_p
         _lib = lib

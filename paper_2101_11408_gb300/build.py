@@ -2,7 +2,8 @@
 
 Every translation unit is compiled for sm_103a only (-gencode
 arch=compute_103a,code=sm_103a), in parallel, and linked with nvcc into one
-shared object exporting the C ABI of include/fpparse.h.
+shared object exporting the C ABI of include/fpparse.h (and the test hooks of
+include/fpparse_test.h).
 """
 from __future__ import annotations
 
@@ -21,7 +22,7 @@ SOURCES = ["fp_parse_kernel.cu", "fp_parse_kernel_ext.cu", "fp_fallback_kernel.c
            "fp_noalloc.cu", "fp_server.cu", "fp_copy_kernel.cu"]
 HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "fp_internal.h",
            "fp_parse_kernel.cuh", "fp_copy.h", "fp_arena.h", "pow5_table.inc", "dec_tables.inc",
-           os.path.join(INCLUDE, "fpparse.h")]
+           os.path.join(INCLUDE, "fpparse.h"), os.path.join(INCLUDE, "fpparse_test.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",

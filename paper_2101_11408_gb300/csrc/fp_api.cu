@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/fpparse.h"
+#include "../../include/fpparse_test.h"
 #include "fp_device.cuh"
 #include "fp_internal.h"
 #include "fp_copy.h"
@@ -110,6 +111,10 @@ struct Scratch {
   unsigned long long* pipe_counts_dv = nullptr;  // ... and the address the parse kernel writes them at
   unsigned long long* pipe_host = nullptr;       // one count (pinned) ...
   unsigned long long* pipe_host_dv = nullptr;    // ... and the address the parse kernel writes it at
+  // fp_test_arm_stalled_lookback: the next call skips chunk 0 and waits at
+  // most test_wait_ns on the device
+  bool test_stall = false;
+  unsigned long long test_wait_ns = 0;
 };
 bool g_timing = false;
 
@@ -317,6 +322,15 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   p.ovf_cap = s->ovf_cap;
   p.total_chunks = total_chunks;
   if (!p.loc) p.loc = p.out_bits;  // binary64: the location sits in the output slot
+  if (s->test_stall) {
+    // the test hook: tickets start at 1, so no block ever takes chunk 0 and
+    // the look-back of the chunks after it waits for a word nothing writes
+    static const unsigned long long first_ticket = 1;
+    FP_CUDA(cudaMemcpyAsync(&s->ctl->ticket, &first_ticket, sizeof(first_ticket),
+                            cudaMemcpyHostToDevice, stream));
+    p.wait_ns = s->test_wait_ns;
+    s->test_stall = false;
+  }
   const int occ = (mode ? di.parse_occ_ext : (f32 ? di.parse_occ32 : di.parse_occ))
                       .at((int)cfg.chunk_bytes);
   const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
@@ -892,6 +906,18 @@ fp_err_t fp_get_error(struct CUstream_st* stream_) {
   return (fp_err_t)err;
 }
 
+fp_err_t fp_test_arm_stalled_lookback(struct CUstream_st* stream_, uint64_t wait_limit_ns) {
+  if (wait_limit_ns == 0 || wait_limit_ns > fp::WAIT_NS_DEFAULT) return FP_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Scratch* s = nullptr;
+  fp_err_t e = get_scratch(stream, 1, 1, g_cfg.fallback_queue, &s);
+  if (e != FP_OK) return e;
+  s->test_stall = true;
+  s->test_wait_ns = wait_limit_ns;
+  return FP_OK;
+}
+
 fp_err_t fp_set_config(const fp_config_t* cfg) {
   if (!cfg) return FP_ERR_ARG;
   if (cfg->chunk_bytes != 4096 && cfg->chunk_bytes != 8192 && cfg->chunk_bytes != 12288 &&
@@ -1000,25 +1026,65 @@ const char* fp_strerror(fp_err_t err) {
 // ---------------------------------------------------------------------------
 namespace {
 
-bool read_cache(const char* path, const char* gpu, fp_config_t* cfg) {
+// The class of a workload, part of the cache key beside the GPU's name: the
+// text's size (small texts take 4 KiB chunks by default and do not fill the
+// GPU with 16 KiB ones) and how many of its fields reach the fallback kernel
+// (long digit strings and near-midpoints, Section 11: the queue depth only
+// matters when there are many).
+std::string workload_class(size_t len, unsigned long long fields, unsigned long long pending) {
+  const char* size = len < SMALL_TEXT_BYTES ? "small" : (len < (64u << 20) ? "medium" : "large");
+  const double rate = fields ? (double)pending / (double)fields : 0.0;
+  const char* fb = rate < 0.001 ? "rare" : (rate < 0.1 ? "some" : "many");
+  return std::string("size=") + size + ",fallback=" + fb;
+}
+
+// The cache: one JSON object per line, one line per (GPU, class).
+bool read_cache(const char* path, const std::string& gpu, const std::string& cls,
+                fp_config_t* cfg) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
-  char buf[4096];
-  size_t n = fread(buf, 1, sizeof(buf) - 1, f);
+  char line[1024];
+  bool found = false;
+  const std::string kg = "\"gpu\": \"" + gpu + "\"", kc = "\"class\": \"" + cls + "\"";
+  while (!found && fgets(line, sizeof(line), f)) {
+    std::string s(line);
+    if (s.find(kg) == std::string::npos || s.find(kc) == std::string::npos) continue;
+    auto num = [&](const char* k, uint32_t* v) -> bool {
+      std::string kk = std::string("\"") + k + "\": ";
+      size_t p = s.find(kk);
+      if (p == std::string::npos) return false;
+      *v = (uint32_t)strtoul(s.c_str() + p + kk.size(), nullptr, 10);
+      return true;
+    };
+    found = num("chunk_bytes", &cfg->chunk_bytes) && num("ctas_per_sm", &cfg->ctas_per_sm) &&
+            num("fallback_queue", &cfg->fallback_queue);
+  }
   fclose(f);
-  buf[n] = 0;
-  std::string s(buf);
-  std::string key = std::string("\"gpu\": \"") + gpu + "\"";
-  if (s.find(key) == std::string::npos) return false;
-  auto num = [&](const char* k, uint32_t* v) -> bool {
-    std::string kk = std::string("\"") + k + "\": ";
-    size_t p = s.find(kk);
-    if (p == std::string::npos) return false;
-    *v = (uint32_t)strtoul(s.c_str() + p + kk.size(), nullptr, 10);
-    return true;
-  };
-  return num("chunk_bytes", &cfg->chunk_bytes) && num("ctas_per_sm", &cfg->ctas_per_sm) &&
-         num("fallback_queue", &cfg->fallback_queue);
+  return found;
+}
+
+// Replace (GPU, class)'s line of the cache, keeping the others.
+void write_cache(const char* path, const std::string& gpu, const std::string& cls,
+                 const fp_config_t& c, float ms, size_t len) {
+  std::vector<std::string> keep;
+  const std::string kg = "\"gpu\": \"" + gpu + "\"", kc = "\"class\": \"" + cls + "\"";
+  if (FILE* f = fopen(path, "r")) {
+    char line[1024];
+    while (fgets(line, sizeof(line), f)) {
+      std::string s(line);
+      if (s.find(kg) != std::string::npos && s.find(kc) != std::string::npos) continue;
+      if (s.find('{') != std::string::npos) keep.push_back(s);
+    }
+    fclose(f);
+  }
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  for (const std::string& s : keep) fputs(s.c_str(), f);
+  fprintf(f,
+          "{\"gpu\": \"%s\", \"class\": \"%s\", \"chunk_bytes\": %u, \"ctas_per_sm\": %u, "
+          "\"fallback_queue\": %u, \"ms\": %.6f, \"bytes\": %zu}\n",
+          gpu.c_str(), cls.c_str(), c.chunk_bytes, c.ctas_per_sm, c.fallback_queue, ms, len);
+  fclose(f);
 }
 
 }  // namespace
@@ -1028,23 +1094,16 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
   if (!text || len == 0 || len >= MAX_LEN) return FP_ERR_ARG;
   int dev = 0;
   FP_CUDA(cudaGetDevice(&dev));
-  char gpu[256];
+  std::string gpu;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     DeviceInfo* di = nullptr;
     fp_err_t e = device_info(dev, &di);
     if (e != FP_OK) return e;
-    snprintf(gpu, sizeof(gpu), "%s", di->name);
+    gpu = di->name;
   }
   fp_config_t cur;
   fp_get_config(&cur);
-  if (cache_path) {
-    fp_config_t c = cur;
-    if (read_cache(cache_path, gpu, &c) && fp_set_config(&c) == FP_OK) {
-      if (chosen) *chosen = c;
-      return FP_OK;
-    }
-  }
   double* out = nullptr;
   uint8_t* st = nullptr;
   uint64_t* cnt = nullptr;
@@ -1053,33 +1112,97 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
   fp_config_t best = cur;
   float best_ms = 1e30f;
   fp_err_t err = FP_OK;
+  bool from_cache = false;
+  std::string cls;
   // every resource is released below, also when one of these fails
   if (cudaMalloc(&out, len * sizeof(double)) != cudaSuccess || cudaMalloc(&st, len) != cudaSuccess ||
       cudaMalloc(&cnt, sizeof(uint64_t)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     err = FP_ERR_CUDA;
-  for (uint32_t chunk : {8192u, 12288u, 16384u}) {
-    if (err != FP_OK) break;
+  // Time one configuration: the best of three calls after one warm-up.
+  auto time_config = [&](const fp_config_t& c, float* ms_out) -> fp_err_t {
+    if (fp_set_config(&c) != FP_OK) return FP_ERR_ARG;
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 4; rep++) {
+      if (cudaEventRecord(e0, stream) != cudaSuccess) return FP_ERR_CUDA;
+      fp_err_t e = fp_parse_f64(text, len, delim, out, st, cnt, stream);
+      if (e != FP_OK) return e;
+      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        return FP_ERR_CUDA;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_min = std::min(ms_min, ms);
+    }
+    *ms_out = ms_min;
+    return FP_OK;
+  };
+  // The workload's class: one call with the current configuration, and the
+  // share of its fields that reached the fallback kernel.
+  if (err == FP_OK) {
+    fp_stats_t before, after;
+    float ms = 0;
+    err = fp_get_stats(&before, 0, stream);
+    if (err == FP_OK) err = time_config(cur, &ms);
+    if (err == FP_OK) err = fp_get_stats(&after, 0, stream);
+    if (err == FP_OK) {
+      const unsigned long long calls = std::max<unsigned long long>(after.calls - before.calls, 1);
+      cls = workload_class(len, (after.fields - before.fields) / calls,
+                           (after.fallback - before.fallback) / calls);
+    }
+  }
+  if (err == FP_OK && cache_path) {
+    fp_config_t c = cur;
+    if (read_cache(cache_path, gpu, cls, &c) && fp_set_config(&c) == FP_OK) {
+      best = c;
+      from_cache = true;
+    }
+  }
+  // chunk size x blocks per SM, at the current queue depth
+  for (uint32_t chunk : {4096u, 8192u, 12288u, 16384u}) {
+    if (err != FP_OK || from_cache) break;
     for (uint32_t per_sm : {1u, 2u, 3u, 4u, 0u}) {
       fp_config_t c = cur;
       c.chunk_bytes = chunk;
       c.ctas_per_sm = per_sm;
-      if (fp_set_config(&c) != FP_OK) continue;
-      float ms_min = 1e30f;
-      for (int rep = 0; rep < 4 && err == FP_OK; rep++) {
-        cudaEventRecord(e0, stream);
-        err = fp_parse_f64(text, len, delim, out, st, cnt, stream);
-        cudaEventRecord(e1, stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) err = FP_ERR_CUDA;
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) ms_min = std::min(ms_min, ms);
-      }
+      float ms = 0;
+      err = time_config(c, &ms);
       if (err != FP_OK) break;
-      if (ms_min < best_ms) {
-        best_ms = ms_min;
+      if (ms < best_ms) {
+        best_ms = ms;
         best = c;
+      }
+    }
+  }
+  // the fallback queue's depth, for the best launch shape: fields beyond the
+  // queue are found by scanning their chunks instead, which costs time when
+  // many fields are pending and nothing when none are; the smallest depth
+  // within 2% of the fastest is kept (it is per-stream device memory)
+  if (err == FP_OK && !from_cache) {
+    fp_config_t base = best;
+    float t_cur = best_ms;
+    std::vector<std::pair<uint32_t, float>> qt;
+    for (uint32_t q : {1u << 16, 1u << 18, 1u << 20, 1u << 22}) {
+      fp_config_t c = base;
+      c.fallback_queue = q;
+      float ms = 0;
+      if (q == base.fallback_queue) {
+        ms = t_cur;
+      } else {
+        err = time_config(c, &ms);
+        if (err != FP_OK) break;
+      }
+      qt.emplace_back(q, ms);
+    }
+    if (err == FP_OK) {
+      float fastest = 1e30f;
+      for (auto& x : qt) fastest = std::min(fastest, x.second);
+      for (auto& x : qt) {  // ascending depths: the first within 2% wins
+        if (x.second <= fastest * 1.02f) {
+          best.fallback_queue = x.first;
+          best_ms = x.second;
+          break;
+        }
       }
     }
   }
@@ -1106,16 +1229,7 @@ extern "C" fp_err_t fp_autotune(const char* text, size_t len, char delim, const 
   }
   fp_set_config(&best);
   if (chosen) *chosen = best;
-  if (cache_path) {
-    FILE* f = fopen(cache_path, "w");
-    if (f) {
-      fprintf(f,
-              "{\"gpu\": \"%s\", \"chunk_bytes\": %u, \"ctas_per_sm\": %u, \"fallback_queue\": %u, "
-              "\"ms\": %.6f, \"bytes\": %zu}\n",
-              gpu, best.chunk_bytes, best.ctas_per_sm, best.fallback_queue, best_ms, len);
-      fclose(f);
-    }
-  }
+  if (cache_path && !from_cache) write_cache(cache_path, gpu, cls, best, best_ms, len);
   return FP_OK;
 }
 

@@ -500,23 +500,6 @@ FP_HD uint32_t dig4(uint32_t x) {
 
 FP_HD uint32_t dig8(uint32_t a, uint32_t b) { return dig4(a) * 10000u + dig4(b); }
 
-// 0x80 in the first byte of x that is not an ASCII digit.  Only that first
-// flag is exact (a borrow or carry out of a non-digit byte may mark later
-// bytes), which is all the callers use.
-FP_HD uint32_t nondigit_flags(uint32_t x) {
-  return ((x + 0x46464646u) | (x - 0x30303030u)) & 0x80808080u;
-}
-
-// (hi:lo) << n, upper word, n clamped to [0, 32]: ~0u << n for lo=0, hi=~0.
-FP_HD uint32_t fshl_clamp(uint32_t lo, uint32_t hi, uint32_t n) {
-#ifdef __CUDA_ARCH__
-  return __funnelshift_lc(lo, hi, n);
-#else
-  n = n > 32 ? 32 : n;
-  return (uint32_t)(((((uint64_t)hi << 32) | lo) << n) >> 32);
-#endif
-}
-
 // Byte permute: byte i of the result is byte ((sel >> 4i) & 7) of (y:x).
 FP_HD uint32_t byte_perm(uint32_t x, uint32_t y, uint32_t sel) {
 #ifdef __CUDA_ARCH__
@@ -568,54 +551,84 @@ struct FastToken {
   int s1, send, dot;
 };
 
-// Straight-line tokenizer for the common field shape
-//     [+-] digits-with-at-most-one-'.' [ [eE] [+-] d{1,4} ]
-// with at most 24 significand characters whose value stays below 10^19
-// (Section 4).  s is the field's first byte and e its terminator (both tile
-// offsets; the bytes in [s, e) are text).  The significand is read as one
-// 24-byte window ending where it ends, so every field of this shape runs the
-// same instructions: the point is found with an exact byte test and removed
-// by a byte permute, bytes before the significand become '0', and the 20
-// low digits are converted four at a time.  Returns false for anything
-// else; the general tokenizer then decides (with identical results for the
-// shapes accepted here).  tile is 4-byte aligned; reads may touch up to 26
-// bytes before s (the window's first word, for a one-character significand)
-// and 4 after e, and those bytes never change the result.
-FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
-  const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
-  auto load4 = [&](int p) -> uint32_t {
-    const int i = p >> 2;  // floor, also for negative p
-    return fshr(t32[i], t32[i + 1], (uint32_t)(p & 3) * 8);
-  };
-  if (e - s < 1 || e - s > 30) return false;
-  const uint32_t c0 = tile[s];
-  t.sign = (c0 == '-') ? SIGN_BIT : 0;
-  const int s1 = s + ((c0 == '-') | (c0 == '+'));
-  // exponent: the last 'e' or 'E' among bytes e-5 .. e-2
-  int sig_end = e;
-  int ex = 0;
-  {
-    const uint32_t Q = load4(e - 5);
-    const uint32_t ez = zero_bytes((Q | 0x20202020u) ^ 0x65656565u);
-    const int ep = e - 5 + ((31 - clz32(ez)) >> 3);
-    if (ez && ep > s1) {
-      const uint32_t cs = tile[ep + 1];
-      const int sg = (cs == '-') | (cs == '+');
-      const int ne = e - ep - 1 - sg;  // exponent digits, at most 4
-      if (ne < 1) return false;
-      const uint32_t keep = 0xFFFFFFFFu << (8 * (4 - ne));
-      const uint32_t R = (load4(e - 4) & keep) | (0x30303030u & ~keep);
-      if (nondigit_flags(R)) return false;
-      ex = (int)dig4(R);
-      if (cs == '-') ex = -ex;
-      sig_end = ep;
-    }
+// 0x80 in every byte of x that is not an ASCII digit, exactly: for a byte b
+// below 0x80, (b ^ '0') is below 10 exactly for '0'..'9', and adding 0x76
+// sets bit 7 exactly when it is not (the sum stays below 0x100, so nothing
+// carries into the next byte); bytes from 0x80 up have bit 7 already.
+FP_HD uint32_t nondigit_exact(uint32_t x) {
+  const uint32_t t = (x ^ 0x30303030u) & 0x7F7F7F7Fu;
+  return ((t + 0x76767676u) | x) & 0x80808080u;
+}
+
+// Shared-memory tables of the window tokenizer (1,672 bytes), so that the
+// per-field byte moves are table lookups instead of computed masks:
+//   sel[d][j]        byte-permute selector of window word j that moves the
+//                    bytes at or before window position d (a point) one place
+//                    toward the end, over the point (d = 24: no point, the
+//                    identity);
+//   keep_from[l][j]  mask of the bytes of word j at window positions >= l;
+//   keep_below[m-16] masks of words 4 and 5 for the positions below m (an
+//                    exponent marker at m >= 16).
+struct WindowTables {
+  uint32_t sel[25][8];
+  uint32_t keep_from[25][8];
+  uint32_t keep_below[9][2];
+};
+constexpr int WINDOW_TABLE_WORDS = (int)(sizeof(WindowTables) / 4);
+
+// Word i of the tables (in the struct's order).
+FP_HD uint32_t window_table_word(int i) {
+  if (i < 25 * 8) {  // sel
+    const int d = i >> 3, j = i & 7;
+    if (j >= 6 || d == 24) return 0x7654u;
+    int c = d + 1 - 4 * j;  // bytes of word j at or before the point
+    c = c < 0 ? 0 : (c > 4 ? 4 : c);
+    const uint32_t m = 0xFFFFu >> (16 - 4 * c);
+    return (0x6543u & m) | (0x7654u & ~m & 0xFFFFu);
   }
-  const int Ls = sig_end - s1;  // significand characters, point included
-  if (Ls < 1 || Ls > 24) return false;
-  // the 24-byte window [sig_end - 24, sig_end)
-  const int w0 = sig_end - 24;
-  const int i0 = w0 >> 2;
+  i -= 25 * 8;
+  if (i < 25 * 8) {  // keep_from
+    const int l = i >> 3, j = i & 7;
+    uint32_t m = 0;
+    for (int b = 0; b < 4; b++)
+      if (4 * j + b >= l) m |= 0xFFu << (8 * b);
+    return j < 6 ? m : 0;
+  }
+  i -= 25 * 8;
+  const int mk = 16 + (i >> 1), j = 4 + (i & 1);  // keep_below
+  uint32_t m = 0;
+  for (int b = 0; b < 4; b++)
+    if (4 * j + b < mk) m |= 0xFFu << (8 * b);
+  return m;
+}
+
+// Straight-line tokenizer for the common field shape (Section 4)
+//     [+-] digits-with-at-most-one-'.' [ [eE] [+-] d{1,4} ]
+// with at most 24 bytes after the sign and a value of the significand
+// below 10^19 when the exponent part's bytes count as trailing zero digits.
+// s is the field's first byte and e its terminator (tile offsets; the bytes
+// in [s, e) are text).  The 24 bytes that end at e are read as one window;
+// exact per-byte non-digit flags locate the point and the exponent marker;
+// the bytes up to the point move one place over it (table selectors), the
+// bytes before the significand and the exponent part become '0' (table
+// masks), and the 20 low digits are converted four at a time.  Every field
+// of this shape runs the same instructions.  Returns false for anything
+// else; the general tokenizer then decides (with identical results for the
+// shapes accepted here).  tile is 4-byte aligned; reads may touch up to 28
+// bytes before e and 4 after it, and those bytes never change the result.
+FP_HD bool parse_window(const uint8_t* tile, const WindowTables& wt, int s, int e, FastToken& t) {
+  const int L = e - s;
+  if (L < 1 || L > 25) return false;
+  const uint32_t c0 = tile[s];
+  const int sg = (c0 == '-') | (c0 == '+');
+  t.sign = (c0 == '-') ? SIGN_BIT : 0;
+  const int s1 = s + sg;
+  const int tsig = 24 - (e - s1);  // window position of the first byte after the sign
+  if (tsig < 0) return false;
+  // the window [e - 24, e)
+  const int w0 = e - 24;
+  const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
+  const int i0 = w0 >> 2;  // floor, also for negative w0
   const uint32_t sh = (uint32_t)(w0 & 3) * 8;
   uint32_t x[6];
   {
@@ -625,61 +638,74 @@ FP_HD bool parse_fast(const uint8_t* tile, int s, int e, FastToken& t) {
 #pragma unroll
     for (int j = 0; j < 6; j++) x[j] = fshr(W[j], W[j + 1], sh);
   }
-  // bytes before the significand become '0'
-  const int tsig = 24 - Ls;  // window index of the first significand byte
-#pragma unroll
-  for (int j = 0; j < 6; j++) {
-    const int fill = 8 * (tsig - 4 * j);
-    const uint32_t m = fshl_clamp(0u, 0xFFFFFFFFu, (uint32_t)(fill > 0 ? fill : 0));
-    x[j] = (x[j] & m) | (0x30303030u & ~m);
-  }
-  // the point: the first non-digit of the window (the first flagged byte of
-  // a word is exact); anything else that is not a digit, or a second point,
-  // is still there after the point is removed and fails the check below
-  int dpos = -1;
+  // bit i: window byte i is not a digit (bytes before the field cleared)
+  uint32_t M;
   {
     uint32_t f[6];
 #pragma unroll
-    for (int j = 0; j < 6; j++) f[j] = nondigit_flags(x[j]);
-    // bit i: byte i of the window flagged (the lowest set bit is exact)
-    const uint32_t M = (flag_pair(f[0], f[1]) >> 7) | (flag_pair(f[2], f[3]) << 1) |
-                       (flag_pair(f[4], f[5]) << 9);
-    if (M) dpos = ctz32(M);
+    for (int j = 0; j < 6; j++) f[j] = nondigit_exact(x[j]);
+    M = (flag_pair(f[0], f[1]) >> 7) | (flag_pair(f[2], f[3]) << 1) | (flag_pair(f[4], f[5]) << 9);
+    M &= 0xFFFFFFFFu << tsig;
   }
-  if (dpos >= 0 && tile[w0 + dpos] != '.') return false;  // (dpos >= tsig: text byte)
-  // the bytes up to the point move one place toward the end, over it (a '0'
-  // enters at the front)
-  uint32_t prev = 0x30303030u;
-#pragma unroll
-  for (int j = 0; j < 6; j++) {
-    int c = dpos + 1 - 4 * j;  // bytes of word j at or before the point
-    c = c < 0 ? 0 : (c > 4 ? 4 : c);
-    const uint32_t M = 0xFFFFu >> (16 - 4 * c);
-    const uint32_t sel = (0x6543u & M) | (0x7654u & ~M);
-    const uint32_t xj = x[j];
-    x[j] = byte_perm(prev, xj, sel);
-    prev = xj;
+  // An exponent: the last non-digit is an 'e' or 'E', or a sign right after
+  // one, and 1 to 4 digits follow.  em: where the significand ends.
+  const int hb = 31 - clz32(M);  // -1 when M == 0
+  int em = 24, ex = 0;
+  if (hb >= 19 && hb <= 22) {
+    const uint32_t ch = tile[w0 + hb];
+    const int hs = (ch == '+') | (ch == '-');
+    const int m = hb - hs;
+    if ((tile[w0 + m] | 0x20u) == 'e' && m > tsig) {
+      em = m;
+      const uint32_t keep = 0xFFFFFFFFu << (8 * (hb - 19));  // the 23 - hb exponent digits
+      ex = (int)dig4((x[5] & keep) | (0x30303030u & ~keep));
+      if (ch == '-') ex = -ex;
+    }
   }
-  // all 24 bytes must be digits, and the four above the 20-digit frame plus
-  // its first one zero, so that the value is below 10^19
-  uint32_t bad = 0;
+  // the significand: digits and at most one non-digit, which is the point
+  const uint32_t Ms = M & ((1u << em) - 1u);
+  if (Ms & (Ms - 1u)) return false;
+  const int hp = Ms != 0;
+  const int dpos = hp ? ctz32(Ms) : 24;
+  if (hp && tile[w0 + dpos] != '.') return false;
+  const int lo = tsig + hp;  // the first digit's position once the point is gone
+  if (em - lo < 1) return false;  // no digit at all
+  {
+    const uint32_t* sel = wt.sel[dpos];
+    uint32_t prev = 0x30303030u;
 #pragma unroll
-  for (int j = 0; j < 6; j++) bad |= nondigit_flags(x[j]);
-  if (bad || x[0] != 0x30303030u || (x[1] & 0xFFu) != 0x30u) return false;
-  if (Ls - (dpos >= 0) < 1) return false;  // no digit at all
+    for (int j = 0; j < 6; j++) {
+      const uint32_t xj = x[j];
+      x[j] = byte_perm(prev, xj, sel[j]);
+      prev = xj;
+    }
+    const uint32_t* kf = wt.keep_from[lo];
+    const uint32_t* kb = wt.keep_below[em - 16];
+    uint32_t k[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) k[j] = kf[j];
+    k[4] &= kb[0];
+    k[5] &= kb[1];
+#pragma unroll
+    for (int j = 0; j < 6; j++) x[j] = (x[j] & k[j]) | (0x30303030u & ~k[j]);
+  }
+  // the five high positions zero, so that the value is below 10^19
+  if (x[0] != 0x30303030u || (x[1] & 0xFFu) != 0x30u) return false;
   uint64_t w = dig4(x[1]) * 10000u + dig4(x[2]);
   w = w * 10000u + dig4(x[3]);
   w = w * 10000u + dig4(x[4]);
   w = w * 10000u + dig4(x[5]);
   t.w = w;
-  t.q = ex - (dpos >= 0 ? 23 - dpos : 0);
+  // the last digit sits at window position 23 once the exponent part is
+  // zeros: with a point, 23 - dpos of the digits follow it
+  t.q = ex + (hp ? dpos - 23 : em - 24);
   t.s1 = s1;
-  t.send = sig_end;
-  t.dot = dpos >= 0 ? w0 + dpos : -1;
+  t.send = w0 + em;
+  t.dot = hp ? w0 + dpos : -1;
   return true;
 }
 
-// The JSON number grammar on a field parse_fast accepted: no '+', a digit
+// The JSON number grammar on a field parse_window accepted: no '+', a digit
 // before the point, a digit after it, and no leading zero before another
 // digit.
 FP_HD bool json_ok_fast(const uint8_t* tile, int s, const FastToken& t) {

@@ -73,25 +73,52 @@ fp_err_t setup_device(int dev, int chunk_bytes, DeviceSlot** out) {
   return FP_OK;
 }
 
+// Same bound on a buffer's length as the other entry points (pending
+// fields keep a 40-bit offset).
+constexpr unsigned long long NOALLOC_MAX_LEN = 1ull << 40;
+// Texts below this many bytes take 4 KiB chunks when the configured chunk is
+// the default 16 KiB, as fp_parse_f64 does (more blocks share a small text).
+constexpr size_t NOALLOC_SMALL_TEXT = 4u << 20;
+
+// Argument and capacity checks of fp_parse_f64_noalloc, before anything is
+// queued: the chunk size to use and the number of chunks, or an error.  The
+// length is compared with the fixed capacity before any sum that could wrap.
+fp_err_t noalloc_plan(const void* text, size_t len, const void* out_f64, const void* out_status,
+                         const void* out_count, uint32_t cfg_chunk, uint32_t* chunk_bytes,
+                         unsigned long long* nchunks) {
+  if (!out_count) return FP_ERR_ARG;
+  if (len >= NOALLOC_MAX_LEN) return FP_ERR_ARG;
+  if (len > 0 && (!text || !out_f64 || !out_status)) return FP_ERR_ARG;
+  uint32_t c = cfg_chunk;
+  if (len < NOALLOC_SMALL_TEXT && c == 16384) c = 4096;
+  const unsigned long long o = reinterpret_cast<uintptr_t>(text) & 15;
+  // o + len <= NOALLOC_MAX_CHUNKS * c, with len < 2^40 so the sum cannot wrap
+  if (o + len > NOALLOC_MAX_CHUNKS * (unsigned long long)c) return FP_ERR_CAPACITY;
+  unsigned long long n = (o + len + c - 1) / c;
+  *chunk_bytes = c;
+  *nchunks = n ? n : 1;
+  return FP_OK;
+}
+
 }  // namespace
 
 extern "C" fp_err_t fp_parse_f64_noalloc(const char* text, size_t len, char delim, double* out_f64,
                                          uint8_t* out_status, uint64_t* out_count,
                                          struct CUstream_st* stream_) {
-  if (!out_count) return FP_ERR_ARG;
-  if (len > 0 && (!text || !out_f64 || !out_status)) return FP_ERR_ARG;
   fp_config_t cfg;
   fp_get_config(&cfg);
+  uint32_t chunk_bytes = 0;
+  unsigned long long nchunks = 0;
+  const fp_err_t ce = noalloc_plan(text, len, out_f64, out_status, out_count, cfg.chunk_bytes,
+                                      &chunk_bytes, &nchunks);
+  if (ce != FP_OK) return ce;
   const unsigned long long o = reinterpret_cast<uintptr_t>(text) & 15;
-  unsigned long long nchunks = (o + len + cfg.chunk_bytes - 1) / cfg.chunk_bytes;
-  if (nchunks == 0) nchunks = 1;
-  if (nchunks > NOALLOC_MAX_CHUNKS) return FP_ERR_CAPACITY;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return FP_ERR_CUDA;
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   DeviceSlot* slot = nullptr;
-  fp_err_t e = setup_device(dev, (int)cfg.chunk_bytes, &slot);
+  fp_err_t e = setup_device(dev, (int)chunk_bytes, &slot);
   if (e != FP_OK) return e;
   unsigned char* base = slot->scratch;
   // The array keeps the previous call's contents: the control block and the
@@ -129,7 +156,7 @@ extern "C" fp_err_t fp_parse_f64_noalloc(const char* text, size_t len, char deli
                                      : slot->parse_occ;
   unsigned long long grid = (unsigned long long)slot->sms * per_sm;
   if (grid > nchunks) grid = nchunks;
-  if (fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream) != cudaSuccess) return FP_ERR_CUDA;
+  if (fp::launch_parse(p, (int)chunk_bytes, (int)grid, stream) != cudaSuccess) return FP_ERR_CUDA;
   if (fp::launch_fallback(p, slot->sms * slot->fallback_occ, stream) != cudaSuccess)
     return FP_ERR_CUDA;
   return FP_OK;

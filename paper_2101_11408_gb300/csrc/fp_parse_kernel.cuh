@@ -17,7 +17,7 @@
 //               the chunk's field count is published at once for the
 //               decoupled look-back;
 //   3. parse  : one thread per field, warps taking groups of 32 fields from a
-//               shared counter: the straight-line tokenizer for the common
+//               shared counter: the window tokenizer for the common
 //               shape, else the general tokenizer of Section 4; quick exits
 //               and Algorithm 1 against the table held in shared memory; the
 //               w / w+1 check of Section 11; results are staged in shared
@@ -60,7 +60,8 @@ struct Layout {
   static constexpr int S_CAP = STAGE;  // field starts listed at a time (denser chunks: windows)
   static constexpr int TABLE_BYTES = FP_POW5_ENTRIES * 8;  // high words only
   static constexpr int OFF_TABLE = 0;
-  static constexpr int OFF_TILE = (TABLE_BYTES + 127) / 128 * 128;
+  static constexpr int OFF_WTAB = (TABLE_BYTES + 127) / 128 * 128;  // the window tokenizer's tables
+  static constexpr int OFF_TILE = (OFF_WTAB + (int)sizeof(WindowTables) + 127) / 128 * 128;
   static constexpr int OFF_S = OFF_TILE + NSTAGE * TILE_ALLOC;
   static constexpr int S_BYTES = ((S_CAP + 2) * 2 + 15) / 16 * 16;  // one list of field starts
   static constexpr int S_STRIDE = S_BYTES / 2;                       // in uint16 entries
@@ -159,10 +160,11 @@ __device__ __forceinline__ unsigned long long lookback_round(const LaunchParams&
     const long long idx = top - (PER * lane + u);
     if ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0) {
       const uint64_t ts = globaltimer_ns();
+      const uint64_t limit = p.wait_ns ? p.wait_ns : WAIT_NS_DEFAULT;
       do {
         __nanosleep(64);
         wv[u] = ld_relaxed_u64(&p.chunk_status[idx]);
-        if (globaltimer_ns() - ts > 2000000000ull) {
+        if (globaltimer_ns() - ts > limit) {
           set_error(p.ctl, DERR_TIMEOUT);
           wv[u] = lb_word(p.epoch, LB_FLAG_INC, 0);
           break;
@@ -218,6 +220,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   using L = Layout<C>;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* table = reinterpret_cast<uint64_t*>(smem + L::OFF_TABLE);
+  WindowTables* wtab = reinterpret_cast<WindowTables*>(smem + L::OFF_WTAB);
   uint8_t* tiles = smem + L::OFF_TILE;
   uint16_t* S = reinterpret_cast<uint16_t*>(smem + L::OFF_S);
   Misc* ms = reinterpret_cast<Misc*>(smem + L::OFF_MISC);
@@ -249,6 +252,8 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   // table; 5,208 bytes); the low words, needed only for a second product,
   // are read from global memory.
   for (int i = tid; i < FP_POW5_ENTRIES; i += NT) table[i] = fp_pow5_table_dev[2 * i];
+  for (int i = tid; i < WINDOW_TABLE_WORDS; i += NT)
+    reinterpret_cast<uint32_t*>(wtab)[i] = window_table_word(i);
   const Pow5 pow5{table, 1, reinterpret_cast<const uint64_t*>(fp_pow5_table_dev) + 1};
   __syncthreads();
 
@@ -274,8 +279,9 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     const uint32_t par = (phases >> b) & 1u;
     if (!mbar_try_wait(&ms->bar[b], par)) {
       const uint64_t t_start = globaltimer_ns();
+      const uint64_t limit = p.wait_ns ? p.wait_ns : WAIT_NS_DEFAULT;
       while (!mbar_try_wait(&ms->bar[b], par)) {
-        if (globaltimer_ns() - t_start > 2000000000ull) {
+        if (globaltimer_ns() - t_start > limit) {
           set_error(ctl, DERR_TIMEOUT);
           break;
         }
@@ -469,7 +475,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     const int limit = vend < L::TILE ? (int)vend : L::TILE;
     const uint32_t n = cur.n;
 
-    // The hot path for one field [s, e): the straight-line tokenizer and
+    // The hot path for one field [s, e): the window tokenizer and
     // Algorithm 1.  Fields it cannot settle are marked for the general
     // tokenizer, which runs in a separate pass so that this loop stays free
     // of rare branches.
@@ -477,7 +483,8 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       FastToken ft;
       ft.w = 0;
       ft.q = 0;
-      bool ok = parse_fast(tile, s, e, ft);
+      ft.sign = 0;
+      bool ok = parse_window(tile, *wtab, s, e, ft);
       if constexpr ((MODE & MODE_JSON) != 0) ok = ok && json_ok_fast(tile, s, ft);
       const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
       c_el += ok;
@@ -517,42 +524,56 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     typename F::word* ob = nullptr;
     uint8_t* os = nullptr;
     // Field k of the chunk (its terminator at tile offset tpos) to the
-    // outputs.  In field order its slot is k; in column-major order it is
-    // column i mod K, row i div K of the field's index i.
-    auto store_one = [&](uint32_t k, unsigned long long bits, uint8_t status, int tpos) {
-      if (k >= cap) return;
+    // outputs, for the lanes with `act`; every lane of the warp calls it
+    // together (the queue append is one atomic per warp).  In field order the
+    // field's slot is k; in column-major order it is column i mod K, row
+    // i div K of the field's index i.
+    auto store_one = [&](bool act, uint32_t k, unsigned long long bits, uint8_t status, int tpos) {
+      const bool live = act && k < cap;
       typename F::word* vo = ob + k;
       uint8_t* so = os + k;
       if constexpr ((MODE & MODE_COLUMNS) != 0) {
-        const unsigned long long i = d.out_base + base + k;
-        const unsigned long long row = __umul64hi(i, p.col_magic);
-        const unsigned long long col = i - row * p.columns;
-        // the last column ends at '\n' (or the end of the text), the others
-        // at the delimiter
-        const bool nl = tpos >= limit || tile[tpos] == '\n';
-        if (status != ST_PENDING && nl != (col == p.columns - 1)) status = ST_BAD_SHAPE;
-        const unsigned long long dest = col * p.rows_cap + row;
-        vo = reinterpret_cast<typename F::word*>(p.out_bits) + dest;
-        so = p.out_status + dest;
-      }
-      constexpr bool in_slot = sizeof(typename F::word) == 8 && (MODE & MODE_COLUMNS) == 0;
-      if constexpr (in_slot) {
-        *vo = bits;  // a pending field's location stays in its own slot
-      } else {
-        if (status == ST_PENDING) p.loc[d.out_base + base + k] = bits;
-        else *vo = (typename F::word)bits;
-      }
-      if (status == ST_PENDING) {
-        const unsigned long long slot = atomicAdd(&ctl->qcount, 1ull);
-        if (slot < p.qcap) {
-          p.queue[slot] = d.out_base + base + k;
-          *so = ST_PENDING_QUEUED;
-        } else {
-          *so = ST_PENDING_SCAN;
-          ms->overflowed = 1;
+        if (live) {
+          const unsigned long long i = d.out_base + base + k;
+          const unsigned long long row = __umul64hi(i, p.col_magic);
+          const unsigned long long col = i - row * p.columns;
+          // the last column ends at '\n' (or the end of the text), the others
+          // at the delimiter
+          const bool nl = tpos >= limit || tile[tpos] == '\n';
+          if (status != ST_PENDING && nl != (col == p.columns - 1)) status = ST_BAD_SHAPE;
+          const unsigned long long dest = col * p.rows_cap + row;
+          vo = reinterpret_cast<typename F::word*>(p.out_bits) + dest;
+          so = p.out_status + dest;
         }
-      } else {
-        *so = status;
+      }
+      const bool pend = live && status == ST_PENDING;
+      constexpr bool in_slot = sizeof(typename F::word) == 8 && (MODE & MODE_COLUMNS) == 0;
+      if (live) {
+        if constexpr (in_slot) {
+          *vo = bits;  // a pending field's location stays in its own slot
+        } else {
+          if (pend) p.loc[d.out_base + base + k] = bits;
+          else *vo = (typename F::word)bits;
+        }
+        if (!pend) *so = status;
+      }
+      // pending fields: one queue append per warp (Section 11's rare slow path)
+      const unsigned int pm = __ballot_sync(0xFFFFFFFFu, pend);
+      if (pm) {
+        const int leader = __ffs(pm) - 1;
+        unsigned long long slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(&ctl->qcount, (unsigned long long)__popc(pm));
+        slot0 = __shfl_sync(0xFFFFFFFFu, slot0, leader);
+        if (pend) {
+          const unsigned long long slot = slot0 + __popc(pm & ((1u << lane) - 1u));
+          if (slot < p.qcap) {
+            p.queue[slot] = d.out_base + base + k;
+            *so = ST_PENDING_QUEUED;
+          } else {
+            *so = ST_PENDING_SCAN;
+            ms->overflowed = 1;
+          }
+        }
       }
     };
 
@@ -648,8 +669,12 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         ob = reinterpret_cast<typename F::word*>(p.out_bits) + d.out_base + base;
         os = p.out_status + d.out_base + base;
       }
-      for (uint32_t k = warp * share + lane; k < k_end; k += 32)
-        store_one(lo + k, stage_bits[k], stage_st[k], (int)Sw[k + 1] - 1);
+      for (uint32_t k0 = warp * share; k0 < k_end; k0 += 32) {  // warp-uniform trip count
+        const uint32_t k = k0 + lane;
+        const bool act = k < k_end;
+        store_one(act, lo + k, act ? stage_bits[k] : 0ull, act ? stage_st[k] : (uint8_t)ST_OK,
+                  act ? (int)Sw[k + 1] - 1 : 0);
+      }
       if (hi >= n) break;
       __syncthreads();  // S and the staged results are rewritten for the next window
     }

@@ -56,7 +56,12 @@ struct LaunchParams {
   unsigned int columns;     // K >= 2: column-major results (field i -> column i mod K)
   unsigned long long rows_cap;   // entries per column
   unsigned long long col_magic;  // ceil(2^64 / K): i div K = mulhi(i, magic) for i < 2^40
+  // How long a device wait (look-back word, staging barrier) may spin before
+  // it gives up with DERR_TIMEOUT; 0 means the default, WAIT_NS_DEFAULT.
+  unsigned long long wait_ns;
 };
+
+constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;  // 2 s
 
 // Look-back word: epoch (24 bits) | flag (2 bits) | value (38 bits).
 constexpr int LB_VALUE_BITS = 38;

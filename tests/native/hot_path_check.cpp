@@ -1,7 +1,8 @@
 // hot_path_check.cpp -- the parse kernel's per-field steps, built for the
 // host from the device header (its functions are host-callable) and run on
-// every '\n'-separated field of standard input: the straight-line tokenizer
-// of Section 4 on a padded tile, Algorithm 1 (Section 5) on its (w, q), and
+// every '\n'-separated field of standard input: the window tokenizer of
+// Section 4 on a padded tile (with its lookup tables as the kernel builds
+// them), Algorithm 1 (Section 5) on its (w, q), and
 // the general tokenizer with the 19-digit check of Section 11 for the fields
 // the first one declines; fields both leave undecided are printed as "P"
 // (the fallback kernel's).  One line per field: "<bits hex> <status>" or
@@ -18,7 +19,9 @@
 
 namespace {
 
-constexpr int LEAD = 32;  // tile bytes before the field (parse_fast reads up to 26)
+constexpr int LEAD = 32;  // tile bytes before the field (parse_window reads up to 28)
+
+fp::WindowTables g_wt;
 
 template <class F>
 void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& tab) {
@@ -35,7 +38,8 @@ void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& 
   FastToken ft;
   ft.w = 0;
   ft.q = 0;
-  bool ok = parse_fast(tile, s, e, ft);
+  ft.sign = 0;
+  bool ok = parse_window(tile, g_wt, s, e, ft);
   if (grammar == GRAMMAR_JSON) ok = ok && json_ok_fast(tile, s, ft);
   const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, tab, true);
   uint64_t sgn = ft.sign;
@@ -68,6 +72,8 @@ int main(int argc, char** argv) {
   static uint64_t hi[FP_POW5_ENTRIES];
   for (int i = 0; i < FP_POW5_ENTRIES; i++) hi[i] = table[2 * i];
   const fp::Pow5 tab{hi, 1, reinterpret_cast<const uint64_t*>(table) + 1};
+  for (int i = 0; i < fp::WINDOW_TABLE_WORDS; i++)
+    reinterpret_cast<uint32_t*>(&g_wt)[i] = fp::window_table_word(i);
   std::string text;
   char buf[1 << 16];
   size_t got;

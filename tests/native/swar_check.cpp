@@ -1,9 +1,9 @@
 // swar_check.cpp -- the word-wide byte tests of the device header, built for
-// the host, against byte-by-byte definitions: the zero-byte flags are exact
-// in every byte; the first non-digit flag is exact (the only one the
-// tokenizers use); two words of flags become the right 8-bit mask; four
-// ASCII digits give their value; the funnel shifts and the clamped left
-// shift match their definitions.  Prints "ok" or the first failure.
+// the host, against byte-by-byte definitions: the zero-byte flags and the
+// non-digit flags are exact in every byte; two words of flags become the
+// right 8-bit mask; four ASCII digits give their value; the funnel shift
+// matches its definition; the window tokenizer's tables move and keep the
+// bytes their definitions say.  Prints "ok" or the first failure.
 #include <cstdio>
 #include <cstdint>
 #include <random>
@@ -46,20 +46,50 @@ int main() {
     for (int i = 0; i < 4; i++)
       if ((byte_of(z, i) == 0x80) != (byte_of(w, i) == 0) || (byte_of(z, i) & 0x7F))
         return fail("zero_bytes", w, z);
-    // nondigit_flags: the lowest flagged byte is the first non-digit
-    const uint32_t nd = nondigit_flags(w);
-    int first = -1;
-    for (int i = 0; i < 4 && first < 0; i++)
-      if (!is_dig(byte_of(w, i))) first = i;
-    const int flagged = nd ? ctz32(nd) / 8 : -1;
-    if (first != flagged || (nd & ~0x80808080u)) return fail("nondigit_flags", w, nd);
-    // the funnel shifts
+    // nondigit_exact: 0x80 exactly in the bytes that are not '0'..'9'
+    const uint32_t nd = nondigit_exact(w);
+    for (int i = 0; i < 4; i++)
+      if ((byte_of(nd, i) == 0x80) == is_dig(byte_of(w, i)) || (byte_of(nd, i) & 0x7F))
+        return fail("nondigit_exact", w, nd);
+    // the funnel shift
     const uint32_t w2 = rand_word();
-    const uint32_t sh = (uint32_t)(rng() % 32), n = (uint32_t)(rng() % 40);
+    const uint32_t sh = (uint32_t)(rng() % 32);
     const uint64_t cat = ((uint64_t)w2 << 32) | w;
     if (fshr(w, w2, sh) != (uint32_t)(cat >> sh)) return fail("fshr", w, sh);
-    if (fshl_clamp(w, w2, n) != (uint32_t)((n >= 32 ? cat << 32 : cat << n) >> 32))
-      return fail("fshl_clamp", w, n);
+  }
+  // the window tables: every point position moves exactly the bytes at or
+  // before it one place toward the end; every mask keeps exactly its bytes
+  {
+    WindowTables wt;
+    for (int i = 0; i < WINDOW_TABLE_WORDS; i++)
+      reinterpret_cast<uint32_t*>(&wt)[i] = window_table_word(i);
+    uint8_t win[24];
+    for (int i = 0; i < 24; i++) win[i] = (uint8_t)('A' + i);
+    for (int d = 0; d <= 24; d++) {
+      uint32_t prev = 0x30303030u;
+      for (int j = 0; j < 6; j++) {
+        uint32_t xj = 0;
+        for (int b = 0; b < 4; b++) xj |= (uint32_t)win[4 * j + b] << (8 * b);
+        const uint32_t r = byte_perm(prev, xj, wt.sel[d][j]);
+        prev = xj;
+        for (int b = 0; b < 4; b++) {
+          const int p = 4 * j + b;
+          const uint8_t want = (d < 24 && p <= d) ? (p == 0 ? '0' : win[p - 1]) : win[p];
+          if (byte_of(r, b) != want) return fail("window sel", (uint32_t)d, (uint32_t)p);
+        }
+      }
+    }
+    for (int l = 0; l <= 24; l++)
+      for (int p = 0; p < 24; p++)
+        if ((byte_of(wt.keep_from[l][p / 4], p % 4) == 0xFF) != (p >= l) ||
+            (byte_of(wt.keep_from[l][p / 4], p % 4) != 0 && byte_of(wt.keep_from[l][p / 4], p % 4) != 0xFF))
+          return fail("window keep_from", (uint32_t)l, (uint32_t)p);
+    for (int m = 16; m <= 24; m++)
+      for (int p = 16; p < 24; p++) {
+        const uint8_t k = byte_of(wt.keep_below[m - 16][(p - 16) / 4], p % 4);
+        if ((k == 0xFF) != (p < m) || (k != 0 && k != 0xFF))
+          return fail("window keep_below", (uint32_t)m, (uint32_t)p);
+      }
   }
   // flag_pair: every pattern of flags in two words
   for (uint32_t m = 0; m < 256; m++) {

@@ -37,10 +37,18 @@ def test_source_hash_ignores_comments_and_sees_code():
     assert bench.kernel_source_sha(lambda n: changed[n]) != base
 
 
-def test_profiled_traffic_only_for_the_profiled_sources(monkeypatch):
-    t = bench.profiled_traffic("parse_kernel")
-    # the committed summary matches the committed sources
-    assert isinstance(t, int) and t > 100_000_000
+def test_profiled_traffic_only_for_the_profiled_sources(monkeypatch, tmp_path):
+    # a summary in the committed format, taken on the current sources
+    sha = bench.kernel_source_sha()
+    (tmp_path / "profiles").mkdir()
+    summary = tmp_path / "profiles" / "parse_kernel_bulk_mixed_10m.md"
+    summary.write_text("# parse_kernel\n\n- source_sha: `%s` (hash of the sources)\n"
+                       "- dram_bytes_per_launch: 244803840\n- duration_us: 252.5 (under ncu)\n"
+                       % sha)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda read=None: sha)
+    assert bench.profiled_traffic("parse_kernel") == 244803840
+    # sources changed since the capture: no traffic figure
     monkeypatch.setattr(bench, "kernel_source_sha", lambda read=None: "0000000000000000")
     assert bench.profiled_traffic("parse_kernel") is None
     assert bench.profiled_traffic("no_such_kernel") is None

@@ -418,16 +418,30 @@ def test_host_entry_point_direct():
 
 
 def test_autotune_picks_a_valid_config(tmp_path):
+    import json
     before = fp.get_config()
     try:
-        t = to_device(workloads.bulk_mixed_text(200000, 81))
         path = str(tmp_path / "tune.json")
-        c = fp.autotune(t, cache_path=path)
+        bulk = to_device(workloads.bulk_mixed_text(200000, 81))
+        c = fp.autotune(bulk, cache_path=path)
         assert c["chunk_bytes"] in (4096, 8192, 12288, 16384)
-        assert os.path.exists(path)
+        assert c["ctas_per_sm"] in (0, 1, 2, 3, 4)
+        assert c["fallback_queue"] in (1 << 16, 1 << 18, 1 << 20, 1 << 22)
         fp.set_config(**before)
-        c2 = fp.autotune(t, cache_path=path)  # loaded from the cache
+        c2 = fp.autotune(bulk, cache_path=path)  # loaded from the cache
         assert c2 == c
+        # another class of workload (most fields pending) gets its own entry
+        hard = to_device(workloads.hard_case_text(200000, 83))
+        fp.set_config(**before)
+        c3 = fp.autotune(hard, cache_path=path)
+        assert c3["fallback_queue"] in (1 << 16, 1 << 18, 1 << 20, 1 << 22)
+        with open(path) as f:
+            entries = [json.loads(line) for line in f if line.strip()]
+        classes = sorted(e["class"] for e in entries)
+        assert len(entries) == 2 and classes[0] != classes[1], entries
+        assert any("fallback=many" in k for k in classes) and any("fallback=rare" in k for k in classes)
+        fp.set_config(**before)
+        assert fp.autotune(bulk, cache_path=path) == c  # the first entry is still there
         assert_parity(workloads.bulk_mixed_text(50000, 82))
     finally:
         fp.set_config(**before)

@@ -1,5 +1,5 @@
 """The parse kernel's per-field arithmetic on the CPU: the device header's
-straight-line tokenizer (Section 4), Algorithm 1 (Section 5) and the general
+window tokenizer (Section 4), Algorithm 1 (Section 5) and the general
 tokenizer with the 19-digit check (Section 11), built for the host
 (tests/native/hot_path_check.cpp), against the oracle on seeded fields.
 
@@ -118,7 +118,7 @@ def test_grammar_fuzz(hot_path, grammar):
 
 def test_digit_heavy_fuzz(hot_path):
     """Mostly digits with at most a point and an exponent: lengths around
-    the 19-digit and 24-character limits of the straight-line tokenizer."""
+    the 19-digit and 24-character limits of the window tokenizer."""
     rnd = random.Random(74)
     lines = []
     for _ in range(40000):
@@ -204,6 +204,26 @@ def test_exact_ties_and_their_neighbours(hot_path, f32):
     check(hot_path, "\n".join(lines).encode(), f32, max_pending=0)
 
 
+def _top_of_tie_range_fields():
+    """Ties at q = 23, the top of the exact-tie range (Section 6): 2^k 10^23
+    has the 54-bit odd part 5^23, so it lies halfway between two doubles
+    (10^23 itself is the classic case).  Written plainly they reach the
+    window tokenizer with the exponent part as trailing zeros (q below 23);
+    with blanks around them they reach the general tokenizer with q = 23.
+    Their neighbours one unit away go to that side."""
+    out = []
+    for k in range(0, 14):
+        for w in (2 ** k, 2 ** k + 1, 2 ** k - 1 if k else 3):
+            for fmt in ("%de23", " %de23", "%de23 ", "\t%dE+23"):
+                out.append(fmt % w)
+    return out
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_ties_at_the_top_of_the_tie_range(hot_path, f32):
+    check(hot_path, "\n".join(_top_of_tie_range_fields()).encode(), f32, max_pending=0)
+
+
 def test_word_wide_byte_tests():
     """The tokenizers' word-wide byte tests (tests/native/swar_check.cpp)
     against byte-by-byte definitions, on four million words."""
@@ -251,8 +271,12 @@ def test_hot_path_under_sanitizers(tmp_path):
 HOT_MUTANTS = [
     ("tie range", "static constexpr int TIE_QMIN = -4, TIE_QMAX = 23;",
      "static constexpr int TIE_QMIN = -4, TIE_QMAX = 22;"),
-    ("point's exponent", "t.q = ex - (dpos >= 0 ? 23 - dpos : 0);",
-     "t.q = ex - (dpos >= 0 ? 22 - dpos : 0);"),
+    ("point's exponent", "t.q = ex + (hp ? dpos - 23 : em - 24);",
+     "t.q = ex + (hp ? dpos - 22 : em - 24);"),
+    ("exponent part as zeros", "t.q = ex + (hp ? dpos - 23 : em - 24);",
+     "t.q = ex + (hp ? dpos - 23 : em - 23);"),
+    ("exponent's sign", "      if (ch == '-') ex = -ex;\n", ""),
+    ("single point", "  if (Ms & (Ms - 1u)) return false;\n", ""),
     ("rounding step", "  m += (m & 1);\n  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))",
      "  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))"),
     ("19-digit truncation", "      exp_adj++;\n      sticky |= (d != 0);", "      sticky |= (d != 0);"),
@@ -268,7 +292,7 @@ HOT_MUTANTS = [
 def test_planted_slip_in_the_hot_path_is_caught(tmp_path, what, old, new):
     """Each slip planted in a host copy of the device header fails one of the
     checks above (bulk fields, range boundaries, digit-heavy and grammar
-    fuzz, exact ties, hard cases)."""
+    fuzz, exact ties, hard cases, ties at the top of the tie range)."""
     cxx = shutil.which("g++")
     if not cxx:
         pytest.skip("no g++")
@@ -286,7 +310,8 @@ def test_planted_slip_in_the_hot_path_is_caught(tmp_path, what, old, new):
               lambda: test_digit_heavy_fuzz(exe),
               lambda: test_exact_ties_and_their_neighbours(exe, False),
               lambda: test_grammar_fuzz(exe, 2),
-              lambda: test_hard_cases_decided_where_possible(exe)]
+              lambda: test_hard_cases_decided_where_possible(exe),
+              lambda: test_ties_at_the_top_of_the_tie_range(exe, False)]
     caught = 0
     for c in checks:
         try:

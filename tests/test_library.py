@@ -1,5 +1,5 @@
 """Host-side checks of the C-ABI library: it loads, exports every symbol
-include/fpparse.h declares, and rejects bad arguments before touching a GPU."""
+include/*.h declares, and rejects bad arguments before touching a GPU."""
 import ctypes
 import os
 import re
@@ -13,9 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    with open(os.path.join(ROOT, "include", "fpparse.h")) as f:
-        text = f.read()
-    return sorted(set(re.findall(r"FP_API [^;(]*?\b(fp_\w+)\s*\(", text)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            with open(os.path.join(inc, h)) as f:
+                names |= set(re.findall(r"FP_API [^;(]*?\b(fp_\w+)\s*\(", f.read()))
+    return sorted(names)
 
 
 def test_header_and_binding_agree():
@@ -60,6 +64,27 @@ def test_argument_errors_need_no_gpu():
     assert lib.fp_parse_f64_batch(ptrs, lens, 2, b"\n", ctypes.c_void_p(16), ctypes.c_void_p(16),
                                   offs, cnts, None) == _lib.FP_ERR_ARG
     assert lib.fp_get_stats(None, 0, None) == _lib.FP_ERR_ARG
+
+
+def test_noalloc_refuses_sizes_before_any_cuda_call():
+    # Only where no GPU is present: a refusal that regressed would reach the
+    # CUDA calls, which then fail cleanly here (tests/test_zz_no_alloc.py
+    # checks the same refusals on a GPU with real buffers behind the pointers).
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("covered with real device buffers by the GPU tests")
+    lib = _lib.load()
+    cnt = ctypes.c_uint64()
+    fake = ctypes.c_void_p(16)
+    for n in ((1 << 64) - 9, 1 << 40):  # wraps in a chunk count; beyond 2^40
+        assert lib.fp_parse_f64_noalloc(fake, n, b"\n", fake, fake, ctypes.addressof(cnt),
+                                        None) == _lib.FP_ERR_ARG
+    chunk = fp.get_config()["chunk_bytes"]
+    assert lib.fp_parse_f64_noalloc(fake, 65536 * chunk + 1, b"\n", fake, fake,
+                                    ctypes.addressof(cnt), None) == _lib.FP_ERR_CAPACITY
+    assert lib.fp_parse_f64_noalloc(None, 10, b"\n", fake, fake, ctypes.addressof(cnt),
+                                    None) == _lib.FP_ERR_ARG
+    assert lib.fp_parse_f64_noalloc(fake, 10, b"\n", fake, fake, None, None) == _lib.FP_ERR_ARG
 
 
 def test_config_validation():
