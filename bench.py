@@ -457,7 +457,7 @@ def run_ours(args, world, rank, dist) -> None:
         line["e2e"] = e2e
     if not args.skip_baseline:
         line["cpu_baseline"] = cpu_baseline(text, kind, f32=f32)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 EXT_WORKLOADS = {
@@ -602,7 +602,7 @@ def run_ext(args, world, rank, dist) -> None:
     }
     if not args.skip_baseline:
         line["cpu_baseline"] = cpu_baseline(text, kind, delim=delim, grammar=gid)
-    print(json.dumps(line), flush=True)
+    return line
 
 
 BATCH_WORKLOAD = ("batched: 4096 independent newline-separated buffers of uniform [0,1) %.17g "
@@ -802,7 +802,7 @@ def run_batch(args, world, rank, dist) -> None:
     }
     if e2e:
         line["e2e"] = e2e
-    print(json.dumps(line), flush=True)
+    return line
 
 
 SERVE_WORKLOAD = ("serving: Poisson arrivals of CSV requests (8 comma-separated columns of uniform "
@@ -1065,7 +1065,7 @@ def run_serve(args, world, rank, dist) -> None:
         "server_stats": s1,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def make_parser() -> argparse.ArgumentParser:
@@ -1084,6 +1084,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="bulk: leave out the hard-case, batched and served sections")
     ap.add_argument("--workload", choices=["bulk", "uniform", "hard", "batch", "serve", "json",
                                            "hex", "columns"],
                     default="bulk",
@@ -1105,6 +1107,66 @@ def make_parser() -> argparse.ArgumentParser:
     return ap
 
 
+def _condensed_levels(levels):
+    return [{"load": lv["load"], "offered_GBps": lv["offered_GBps"], "requests": lv["requests"],
+             "server": {k: lv["server"][k] for k in ("GBps", "p50_ms", "p99_ms", "mean_batch")},
+             "plain": lv["plain"]} for lv in levels]
+
+
+def run_extras(args, world, rank, dist) -> dict:
+    """The default line's other configurations, each in its own section: the
+    hard cases (fallback rate and throughput), the batched buffers (one
+    graph-replayed persistent launch against one launch per buffer) and the
+    served requests (the server against the plain per-request path, p50/p99
+    at 25/50/90% of the server's peak)."""
+    import copy
+
+    import torch
+
+    def sub(workload, **over):
+        a = copy.copy(args)
+        a.workload = workload
+        a.skip_baseline = True
+        for k, v in over.items():
+            setattr(a, k, v)
+        return a
+
+    out = {}
+    t = time.perf_counter()
+    h = run_ours(sub("hard", e2e_steps=min(args.e2e_steps, 10)), world, rank, dist)
+    torch.cuda.empty_cache()
+    if h:
+        out["hard"] = {k: h[k] for k in ("metric", "value", "unit", "ms_per_step", "roofline",
+                                         "fallback", "e2e", "path_counts_per_step", "clocks")
+                       if k in h}
+        out["hard"]["config"] = {k: h["config"][k] for k in ("workload", "numbers", "text_bytes",
+                                                              "mfloats_per_s", "checked_fields")}
+        out["hard"]["seconds"] = time.perf_counter() - t
+    t = time.perf_counter()
+    b = run_batch(sub("batch", e2e_steps=min(args.e2e_steps, 10)), world, rank, dist)
+    torch.cuda.empty_cache()
+    if b:
+        out["batch"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "forms",
+                                          "roofline", "e2e", "clocks") if k in b}
+        out["batch"]["config"] = {k: b["config"][k] for k in (
+            "workload", "buffers", "text_bytes", "numbers", "min_buffer", "max_buffer",
+            "mfloats_per_s", "autotuned", "checked_fields")}
+        out["batch"]["seconds"] = time.perf_counter() - t
+    t = time.perf_counter()
+    sv = run_serve(sub("serve", serve_seconds=min(args.serve_seconds, 1.5)), world, rank, dist)
+    torch.cuda.empty_cache()
+    if sv:
+        out["serve"] = {"metric": sv["metric"], "unit": sv["unit"], "p50_ms": sv["p50_ms"],
+                        "p99_ms": sv["p99_ms"], "peak": sv["peak"],
+                        "levels": _condensed_levels(sv["levels"]), "e2e": sv["e2e"],
+                        "clocks": sv.get("clocks"),
+                        "config": {k: sv["config"][k] for k in (
+                            "workload", "bodies", "mean_request_bytes", "max_request_bytes",
+                            "device_budget", "max_batch", "max_inflight", "checked_fields")}}
+        out["serve"]["seconds"] = time.perf_counter() - t
+    return out
+
+
 def main() -> None:
     ap = make_parser()
     args = ap.parse_args()
@@ -1118,16 +1180,28 @@ def main() -> None:
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist.init_process_group("nccl")
+    line = None
     if args.impl == "reference":
         run_reference(args, world, rank)
     elif args.workload == "batch":
-        run_batch(args, world, rank, dist)
+        line = run_batch(args, world, rank, dist)
     elif args.workload == "serve":
-        run_serve(args, world, rank, dist)
+        line = run_serve(args, world, rank, dist)
     elif args.workload in EXT_WORKLOADS:
-        run_ext(args, world, rank, dist)
+        line = run_ext(args, world, rank, dist)
     else:
-        run_ours(args, world, rank, dist)
+        line = run_ours(args, world, rank, dist)
+        # the default line also carries the hard-case, batched and served
+        # configurations (one GPU: replicas of those under torchrun would
+        # only repeat them)
+        if args.workload == "bulk" and not args.no_extras and world == 1:
+            import torch
+            torch.cuda.empty_cache()
+            extras = run_extras(args, world, rank, dist)
+            if line is not None:
+                line.update(extras)
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -72,7 +72,7 @@ constexpr uint32_t DERR_INTERNAL = 6;
 // Counters kept per CTA and added to the stream's totals.
 enum {
   CNT_FIELDS = 0,
-  CNT_EL,       // Algorithm 1 evaluations on the fast tokenizer's output
+  CNT_EL,       // fields settled by the window tokenizer and Algorithm 1 at once
   CNT_TWO_MUL,
   CNT_LONG,
   CNT_LONG_SETTLED,
@@ -80,6 +80,7 @@ enum {
   CNT_FALLBACK_BIGNUM,
   CNT_QUEUE_OVERFLOW,
   CNT_SLOW,     // fields that needed the general tokenizer
+  CNT_NOT_FAST, // fields the window tokenizer and Algorithm 1 did not settle at once
   CNT_NUM
 };
 
@@ -193,17 +194,14 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   if (lo <= 1 && q >= F::TIE_QMIN && q <= F::TIE_QMAX && (m & 3) == 1 &&
       (m << (u + F::SHIFT)) == hi)
     m &= ~1ull;
-  m += (m & 1);
-  m >>= 1;
-  if (m >= (1ull << (F::MBITS + 1))) {  // rounding carried into a new bit
-    m = 1ull << F::MBITS;
-    E += 1;
-  }
-  if (E >= F::EMAX_FIELD) {
-    r.bits = F::INF;
-    return r;
-  }
-  r.bits = ((uint64_t)E << F::MBITS) | (m & ((1ull << F::MBITS) - 1));
+  // round to nearest on the last bit: (m + (m & 1)) >> 1 is (m + 1) >> 1
+  m = (m + 1) >> 1;
+  // Pack with the significand's leading bit added into the exponent field:
+  // (E - 1) + 1 = E, and a rounding carry to 2^(MBITS+1) adds one more (the
+  // significand field then being zero), as Algorithm 1's carry step does.
+  // A field of EMAX_FIELD or more is infinity.
+  const uint64_t bits = ((uint64_t)(E - 1) << F::MBITS) + m;
+  r.bits = bits >= F::INF ? F::INF : bits;
   return r;
 }
 
@@ -540,6 +538,20 @@ FP_HD uint32_t flag_pair(uint32_t w0, uint32_t w1) {
 // 0x80 in every byte of t that is zero, exactly.
 FP_HD uint32_t zero_bytes(uint32_t t) {
   return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t) & 0x80808080u;
+}
+
+// 0x80 in every byte of w equal to the byte repeated in pat, exactly, for a
+// pattern byte below 0x80: zero_bytes(w ^ pat), where the final test can use
+// w's own bit 7 (pat's is clear), so the XOR costs nothing extra.
+FP_HD uint32_t sep_flags_one(uint32_t w, uint32_t pat) {
+  return ~((((w ^ pat) & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | w) & 0x80808080u;
+}
+
+// The same for bytes equal to either of two patterns (both below 0x80).
+FP_HD uint32_t sep_flags_two(uint32_t w, uint32_t p1, uint32_t p2) {
+  const uint32_t s1 = ((w ^ p1) & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+  const uint32_t s2 = ((w ^ p2) & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+  return ~((s1 & s2) | w) & 0x80808080u;
 }
 
 struct FastToken {

@@ -140,24 +140,26 @@ __device__ __forceinline__ void issue_stage(uint8_t* tile, uint64_t* bar, const 
 // are counted, one iteration before they are parsed, and their inclusive
 // prefixes once known; the warp reads PER entries per lane per round, newest
 // first, and stops at the nearest inclusive prefix.  Each wait is bounded.
-// One round: returns the sum of the entries up to and including the nearest
-// inclusive one (or of all PER*32 when there is none) to every lane, and
-// whether one was found.
+// One round of PER*32 entries: returns the sum of the entries up to and
+// including the nearest inclusive one (or of all of them when there is none)
+// to every lane, and whether one was found.
 template <int PER>
 __device__ __forceinline__ unsigned long long lookback_round(const LaunchParams& p, long long top,
                                                              long long first, int lane,
                                                              bool& found) {
+  // Entry at distance 32u + lane from top is this lane's u-th: the newest 32
+  // (the ones most likely not yet published) are on 32 lanes, waited for in
+  // parallel.
   unsigned long long wv[PER];
 #pragma unroll
   for (int u = 0; u < PER; u++) {
-    const long long idx = top - (PER * lane + u);
+    const long long idx = top - (lane + 32 * u);
     wv[u] = idx >= first ? ld_relaxed_u64(&p.chunk_status[idx]) : lb_word(p.epoch, LB_FLAG_AGG, 0);
   }
   unsigned int nearest = 0xFFFFFFFFu;  // distance of this lane's nearest inclusive entry
-  unsigned long long part = 0;
 #pragma unroll
   for (int u = 0; u < PER; u++) {
-    const long long idx = top - (PER * lane + u);
+    const long long idx = top - (lane + 32 * u);
     if ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0) {
       const uint64_t ts = globaltimer_ns();
       const uint64_t limit = p.wait_ns ? p.wait_ns : WAIT_NS_DEFAULT;
@@ -171,39 +173,35 @@ __device__ __forceinline__ unsigned long long lookback_round(const LaunchParams&
         }
       } while ((unsigned int)(wv[u] >> 40) != p.epoch || ((wv[u] >> LB_VALUE_BITS) & 3) == 0);
     }
-    const bool inc = ((wv[u] >> LB_VALUE_BITS) & 3) == LB_FLAG_INC;
-    if (nearest == 0xFFFFFFFFu) {
-      part += wv[u] & LB_VALUE_MASK;
-      if (inc) nearest = PER * lane + u;
-    }
+    if (nearest == 0xFFFFFFFFu && ((wv[u] >> LB_VALUE_BITS) & 3) == LB_FLAG_INC)
+      nearest = (unsigned int)(lane + 32 * u);
   }
+  // the sum of the entries up to and including the nearest inclusive one
   const unsigned int stop = __reduce_min_sync(0xFFFFFFFFu, nearest);
-  // lanes wholly beyond the nearest inclusive entry contribute nothing
-  if ((unsigned int)(PER * lane) > stop) part = 0;
+  unsigned long long part = 0;
+#pragma unroll
+  for (int u = 0; u < PER; u++)
+    if ((unsigned int)(lane + 32 * u) <= stop) part += wv[u] & LB_VALUE_MASK;
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, off);
   found = stop != 0xFFFFFFFFu;
   return part;
 }
 
-// The 32 nearest entries first (one load per lane: most look-backs stop
-// there), then the next 128, then rounds of 32*LB_PER_LANE.  Every lane
-// returns the prefix.
+// Rounds of 32*LB_PER_LANE entries, newest first, all of a round's loads
+// issued at once.  One block takes one ticket per iteration, so this block's
+// own previous chunk, whose inclusive prefix it knows, is about one grid of
+// chunks back: the first round reaches it whether or not the chunks in
+// between have published inclusive prefixes yet (a chain of those would make
+// the look-back as slow as its slowest link).  Every lane returns the prefix.
 constexpr int LB_PER_LANE = 16;
 __device__ __forceinline__ unsigned long long warp_lookback(const LaunchParams& p, long long g,
                                                             long long first,
                                                             unsigned long long known, int lane) {
   long long top = g - 1;
-  if (top < first) return known;
-  bool found = false;
-  unsigned long long prefix = lookback_round<1>(p, top, first, lane, found);
-  if (found) return prefix;
-  top -= 32;
-  if (top < first) return prefix + known;
-  prefix += lookback_round<4>(p, top, first, lane, found);
-  if (found) return prefix;
-  top -= 128;
+  unsigned long long prefix = 0;
   while (top >= first) {
+    bool found = false;
     prefix += lookback_round<LB_PER_LANE>(p, top, first, lane, found);
     if (found) return prefix;
     top -= 32 * LB_PER_LANE;
@@ -257,22 +255,21 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   const Pow5 pow5{table, 1, reinterpret_cast<const uint64_t*>(fp_pow5_table_dev) + 1};
   __syncthreads();
 
-  // path counters of this thread's fields (added up once, at the end)
-  uint32_t c_el = 0, c_two = 0, c_long = 0, c_long_ok = 0, c_slow = 0;
+  // Path counters: the second products of this thread's fields in a
+  // register (added up once, at the end); the rare paths count in shared
+  // memory; fields settled by the window tokenizer and Algorithm 1 at once
+  // are the block's fields less those that needed anything else.
+  uint32_t c_two = 0;
   auto flush_counters = [&]() {
-    uint32_t v[5] = {c_el, c_two, c_long, c_long_ok, c_slow};
-    const int idx[5] = {CNT_EL, CNT_TWO_MUL, CNT_LONG, CNT_LONG_SETTLED, CNT_SLOW};
-#pragma unroll
-    for (int i = 0; i < 5; i++) {
-      const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, v[i]);
-      if (lane == 0 && tot) atomicAdd(&ms->cnt[idx[i]], (unsigned long long)tot);
-    }
-    c_el = c_two = c_long = c_long_ok = c_slow = 0;
+    const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, c_two);
+    if (lane == 0 && tot) atomicAdd(&ms->cnt[CNT_TWO_MUL], (unsigned long long)tot);
+    c_two = 0;
   };
   uint32_t phases = 0;  // bit b: parity of buffer b's next phase
   const uint32_t NLW = 0x0A0A0A0Au;
   const uint32_t DLW = delim * 0x01010101u;
   const bool one_sep = (delim == '\n');
+  const bool dl_ascii = delim < 0x80u;  // the two-separator test's shortcut needs bit 7 clear
 
   // Wait until buffer b's bytes have landed (bounded).
   auto wait_buf = [&](int b) {
@@ -335,26 +332,35 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       uint32_t z[4];
 #pragma unroll
       for (int i = 0; i < 4; i++)
-        z[i] = one_sep ? zero_bytes(w4[i] ^ NLW) : (zero_bytes(w4[i] ^ NLW) | zero_bytes(w4[i] ^ DLW));
+        z[i] = one_sep ? sep_flags_one(w4[i], NLW)
+                       : (dl_ascii ? sep_flags_two(w4[i], NLW, DLW)
+                                   : (sep_flags_one(w4[i], NLW) | zero_bytes(w4[i] ^ DLW)));
       // one bit per byte position
-      uint32_t m16 = (flag_pair(z[0], z[1]) >> 7) | (flag_pair(z[2], z[3]) << 1);
-      const long long x0 = c0 + 16 * j;
-      // boundaries in this granule are field starts iff o <= b < endx-1,
-      // plus the virtual boundary o-1; the chunk's last byte c1-1 is not ours
-      if (x0 < o || x0 + 16 > endx - 1 || j == C / 16 - 1) {
-        uint32_t m = 0;
-        for (int q = 0; q < 16; q++) {
-          const long long bp = x0 + q;
-          bool isb = (m16 >> q) & 1;
-          if (bp < o || bp >= endx - 1) isb = false;
-          if (bp == o - 1) isb = true;
-          if (bp == c0 + C - 1) isb = false;
-          if (bp + 1 >= endx) isb = false;
-          m |= (uint32_t)isb << q;
-        }
-        m16 = m;
-      }
+      const uint32_t m16 = (flag_pair(z[0], z[1]) >> 7) | (flag_pair(z[2], z[3]) << 1);
       mask |= (MaskT)m16 << (16 * k);
+    }
+    {
+      // A boundary at byte b is a field start iff o <= b < endx - 1, plus
+      // the virtual boundary o - 1 (the buffer's first field, when it has
+      // one); the chunk's last byte is the next chunk's.  Interior threads
+      // (all but the chunk's last and those at a buffer's edges) keep every
+      // separator.
+      constexpr int NB = 16 * L::SEG_PER_THREAD;  // bytes (mask bits) per thread
+      const long long x0t = c0 + NB * tid;
+      if (x0t < o || x0t + NB > endx - 1 || tid == NT - 1) {
+        const long long lo = o - x0t, hi = endx - 1 - x0t;  // valid bit range [lo, hi)
+        const int lo_c = lo < 0 ? 0 : (lo > NB ? NB : (int)lo);
+        const int hi_c = hi < 0 ? 0 : (hi > NB ? NB : (int)hi);
+        MaskT valid = 0;
+        if (hi_c > lo_c) {
+          const MaskT ones = ~(MaskT)0;
+          valid = (ones << lo_c) & (hi_c >= (int)(8 * sizeof(MaskT)) ? ones : ~(ones << hi_c));
+        }
+        mask &= valid;
+        const long long vb = o - 1 - x0t;
+        if (vb >= 0 && vb < NB && o < endx) mask |= (MaskT)1 << vb;
+        if (tid == NT - 1) mask &= ~((MaskT)1 << (NB - 1));
+      }
     }
     cn.mask = mask;
     cnt += (sizeof(MaskT) == 8) ? __popcll((unsigned long long)mask) : __popc((uint32_t)mask);
@@ -367,13 +373,11 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     }
     if (lane == 31) ms->warp_sum[warp] = incl;
     __syncthreads();
-    uint32_t wpre = 0, n = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < NT / 32; w2++) {
-      uint32_t v = ms->warp_sum[w2];
-      wpre += (w2 < warp) ? v : 0;
-      n += v;
-    }
+    // the warps' totals: lane l holds warp l's (l < 8); the block's total and
+    // this warp's exclusive prefix are two warp reductions
+    const uint32_t wsum = lane < NT / 32 ? ms->warp_sum[lane] : 0u;
+    const uint32_t n = __reduce_add_sync(0xFFFFFFFFu, wsum);
+    const uint32_t wpre = __reduce_add_sync(0xFFFFFFFFu, lane < warp ? wsum : 0u);
     cn.n = n;
     cn.rank0 = wpre + incl - cnt;
     // publish at once so that later chunks can look past this one; the
@@ -394,11 +398,14 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       uint32_t rank = cn.rank0;
       if (cn.pad_bit) Sx[rank++] = PAD;
       const int base_off = PAD + 16 * tid * L::SEG_PER_THREAD + 1;
-      MaskT m = mask;
-      while (m) {
-        const int bpos = (sizeof(MaskT) == 8) ? __ffsll((long long)m) - 1 : __ffs((uint32_t)m) - 1;
-        Sx[rank++] = (uint16_t)(base_off + bpos);
-        m &= m - 1;
+      // the set bits in order, 32 at a time (32-bit bit scans)
+#pragma unroll
+      for (int h = 0; h < (int)sizeof(MaskT) / 4; h++) {
+        uint32_t m = (uint32_t)(mask >> (32 * h));
+        while (m) {
+          Sx[rank++] = (uint16_t)(base_off + 32 * h + __ffs(m) - 1);
+          m &= m - 1;
+        }
       }
       if (last >= 0) {
         // the last field ends at the first separator after its start, at the
@@ -487,7 +494,6 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       bool ok = parse_window(tile, *wtab, s, e, ft);
       if constexpr ((MODE & MODE_JSON) != 0) ok = ok && json_ok_fast(tile, s, ft);
       const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
-      c_el += ok;
       c_two += ok & (uint32_t)r.two_mul;
       uint64_t sgn = ft.sign;  // the binary64 sign bit
       if constexpr (F::MBITS != F64::MBITS) sgn = ft.sign ? F::SIGN : 0;
@@ -498,12 +504,13 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     // The rest: the general tokenizer on the field's exact extent, else the
     // fallback kernel (pending, with the field's location as the value).
     auto parse_general = [&](int s, int e, unsigned long long& bits, uint8_t& status) {
+      atomicAdd(&ms->cnt[CNT_NOT_FAST], 1ull);
       if (e - s <= LMAX) {
-        c_slow++;
+        atomicAdd(&ms->cnt[CNT_SLOW], 1ull);
         const FieldResult r = parse_short_field<F>(tile + s, e - s, pow5, p.grammar);
         c_two += r.two_mul;
-        c_long += r.is_long;
-        c_long_ok += r.long_settled;
+        if (r.is_long) atomicAdd(&ms->cnt[CNT_LONG], 1ull);
+        if (r.long_settled) atomicAdd(&ms->cnt[CNT_LONG_SETTLED], 1ull);
         if (r.status != ST_PENDING) {
           bits = r.bits;
           status = r.status;
@@ -706,6 +713,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   }
   __syncthreads();
   if (tid == 0) {
+    ms->cnt[CNT_EL] = ms->cnt[CNT_FIELDS] - ms->cnt[CNT_NOT_FAST];
     for (int i = 0; i < CNT_NUM; i++)
       if (ms->cnt[i]) atomicAdd(&ctl->stats[i], ms->cnt[i]);
     __threadfence();

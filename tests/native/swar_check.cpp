@@ -1,5 +1,5 @@
 // swar_check.cpp -- the word-wide byte tests of the device header, built for
-// the host, against byte-by-byte definitions: the zero-byte flags and the
+// the host, against byte-by-byte definitions: the zero-byte, separator and
 // non-digit flags are exact in every byte; two words of flags become the
 // right 8-bit mask; four ASCII digits give their value; the funnel shift
 // matches its definition; the window tokenizer's tables move and keep the
@@ -46,6 +46,18 @@ int main() {
     for (int i = 0; i < 4; i++)
       if ((byte_of(z, i) == 0x80) != (byte_of(w, i) == 0) || (byte_of(z, i) & 0x7F))
         return fail("zero_bytes", w, z);
+    // sep_flags_one / sep_flags_two: 0x80 exactly in the bytes equal to a
+    // separator ('\n', and a second one below 0x80)
+    const uint8_t sep2 = (uint8_t)(rng() % 0x80);
+    const uint32_t p1 = 0x0A0A0A0Au, p2 = sep2 * 0x01010101u;
+    const uint32_t s1 = sep_flags_one(w, p1), s2 = sep_flags_two(w, p1, p2);
+    for (int i = 0; i < 4; i++) {
+      const uint8_t c = byte_of(w, i);
+      if ((byte_of(s1, i) == 0x80) != (c == '\n') || (byte_of(s1, i) & 0x7F))
+        return fail("sep_flags_one", w, s1);
+      if ((byte_of(s2, i) == 0x80) != (c == '\n' || c == sep2) || (byte_of(s2, i) & 0x7F))
+        return fail("sep_flags_two", w, p2);
+    }
     // nondigit_exact: 0x80 exactly in the bytes that are not '0'..'9'
     const uint32_t nd = nondigit_exact(w);
     for (int i = 0; i < 4; i++)

@@ -277,8 +277,8 @@ HOT_MUTANTS = [
      "t.q = ex + (hp ? dpos - 23 : em - 23);"),
     ("exponent's sign", "      if (ch == '-') ex = -ex;\n", ""),
     ("single point", "  if (Ms & (Ms - 1u)) return false;\n", ""),
-    ("rounding step", "  m += (m & 1);\n  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))",
-     "  m >>= 1;\n  if (m >= (1ull << (F::MBITS + 1)))"),
+    ("rounding step", "  m = (m + 1) >> 1;\n", "  m = m >> 1;\n"),
+    ("overflow to infinity", "  r.bits = bits >= F::INF ? F::INF : bits;\n", "  r.bits = bits;\n"),
     ("19-digit truncation", "      exp_adj++;\n      sticky |= (d != 0);", "      sticky |= (d != 0);"),
     ("w+1 check", "    ElResult b = convert_wq<F>(w + 1, q, tab, true);",
      "    ElResult b = convert_wq<F>(w, q, tab, true);"),
