@@ -815,42 +815,6 @@ def _percentile_ms(lat_ns, q):
     return float(np.percentile(np.asarray(lat_ns, dtype=np.float64), q)) / 1e6
 
 
-SERVE_RING_BYTES = 1 << 32  # pinned result space of the serving bench's client
-
-
-class ResultRing:
-    """Byte regions of a ring of `cap` bytes, handed out in request order:
-    each starts where the newest held one ends, or at the ring's start when
-    it does not fit there, and the oldest held regions are given back (their
-    requests waited for, by `release(tag)`) only until the new one fits."""
-
-    def __init__(self, cap: int):
-        self.cap = cap
-        self.held = collections.deque()  # (start, end, tag), oldest first
-        self.head = 0                    # the end of the newest region
-
-    def reserve(self, need: int, tag, release) -> int:
-        if need > self.cap:
-            raise ValueError("region larger than the ring")
-        start = 0
-        while self.held:
-            tail = self.held[0][0]
-            if self.held[-1][0] >= tail:  # held: [tail, head)
-                if self.head + need <= self.cap:
-                    start = self.head
-                    break
-                if need <= tail:
-                    start = 0
-                    break
-            elif self.head + need <= tail:  # held: [tail, cap) and [0, head)
-                start = self.head
-                break
-            release(self.held.popleft()[2])
-        self.held.append((start, start + need, tag))
-        self.head = start + need
-        return start
-
-
 def run_serve(args, world, rank, dist) -> None:
     """The request server against the plain per-request path, both fed the
     same Poisson arrival traces of host-memory requests."""
@@ -898,83 +862,63 @@ def run_serve(args, world, rank, dist) -> None:
             raise SystemExit("bench: plain path failed (%d, %d fields of %d)" % (rc, cnt.value,
                                                                                 fields))
 
-    # Results of the timed requests go to one pinned ring, taken in arrival
-    # order: the client waits for an earlier request only when the ring comes
-    # round to space that request still holds (more than the ring's bytes of
-    # results in flight), never because a body is used again.
-    ring = torch.empty(SERVE_RING_BYTES, dtype=torch.uint8).pin_memory()
+    # The timed traces are replayed by native threads (fp_replay_server /
+    # fp_replay_plain), which submit every request at its arrival time; the
+    # results of a request go to its body's arrays (requests of the same body
+    # write the same values), checked against the body's results after
+    # every trace.
+    rbodies = (fp._lib.ReplayBody * R)(*[
+        fp._lib.ReplayBody(h.data_ptr(), h.numel(), v.data_ptr(), s_.data_ptr(), fields)
+        for h, v, s_, fields in bodies])
 
-    def ring_views(a, fields):
-        return (ring[a:a + 8 * fields].view(torch.float64), ring[a + 8 * fields:a + 9 * fields])
+    def check_bodies(what):
+        for j in range(R):
+            if not np.array_equal(bodies[j][1].numpy().view(np.uint64), ref_bits[j]):
+                raise SystemExit("bench: %s: body %d has wrong results" % (what, j))
 
-    def run_server(order, arr_ns, parts=None, check_last=64):
+    def run_server(order, arr_ns, parts=None):
         """Submit request i at t0 + arr_ns[i]; latency = done - that arrival.
         parts collects the latency's pieces: client lag (arrival -> submit),
-        queue (submit -> launch) and service (launch -> done).  The last
-        check_last requests' results, still in the ring at the end, are
-        compared with the body's reference results."""
+        queue (submit -> launch) and service (launch -> done)."""
         n = len(order)
-        t0 = time.monotonic_ns() + 2_000_000
-        infos = [None] * n
-        rids = [0] * n
-        where = [0] * n
-        results = ResultRing(SERVE_RING_BYTES)
-
-        def release(p):  # request p's region is reused: wait for it first
-            if infos[p] is None:
-                infos[p] = srv.wait(rids[p])
-
-        for i in range(n):
-            j = int(order[i])
-            fields = bodies[j][3]
-            need = (9 * fields + 63) // 64 * 64
-            a = results.reserve(need, i, release)
-            ta = t0 + int(arr_ns[i])
-            while time.monotonic_ns() < ta:
-                pass
-            v, s_ = ring_views(a, fields)
-            rids[i] = srv.submit(bodies[j][0], v, s_)
-            where[i] = a
-        for i in range(n):
-            if infos[i] is None:
-                infos[i] = srv.wait(rids[i])
-        for i, inf in enumerate(infos):
-            if inf["error"] or inf["count"] != bodies[int(order[i])][3]:
-                raise SystemExit("bench: server request %d failed: %r" % (i, inf))
-        for i in range(max(0, n - check_last), n):
-            j = int(order[i])
-            v, _ = ring_views(where[i], bodies[j][3])
-            if not np.array_equal(v.numpy().view(np.uint64), ref_bits[j]):
-                raise SystemExit("bench: server request %d (body %d) has wrong results" % (i, j))
-        arrival = [t0 + int(arr_ns[i]) for i in range(n)]
-        lat = [inf["done_ns"] - arrival[i] for i, inf in enumerate(infos)]
+        ordr = np.ascontiguousarray(order, dtype=np.uint32)
+        arr = np.ascontiguousarray(arr_ns, dtype=np.int64)
+        rec = np.zeros(4 * n, dtype=np.int64)
+        l0 = srv.stats()["launches"]
+        rc = lib.fp_replay_server(srv._h, rbodies, R, ordr.ctypes.data, arr.ctypes.data, n,
+                                  2_000_000, rec.ctypes.data)
+        if rc != 0:
+            raise SystemExit("bench: server trace failed: %s" % fp._lib.strerror(rc))
+        launches = max(srv.stats()["launches"] - l0, 1)
+        check_bodies("server trace")
+        arrival, submit, launch_t, done = rec.reshape(n, 4).T
+        lat = (done - arrival).tolist()
         if parts is not None:
-            for name, a, b in (("client_lag", None, "submit_ns"), ("queue", "submit_ns", "launch_ns"),
-                               ("service", "launch_ns", "done_ns")):
-                d = [inf[b] - (arrival[i] if a is None else inf[a]) for i, inf in enumerate(infos)]
+            for name, d in (("client_lag", submit - arrival), ("queue", launch_t - submit),
+                            ("service", done - launch_t)):
                 parts[name] = {"p50_ms": _percentile_ms(d, 50), "p99_ms": _percentile_ms(d, 99)}
             # latency by request size: below 1 MB and from 1 MB on
-            for name, pick in (("below_1MB", lambda j: lens[j] < (1 << 20)),
-                               ("from_1MB", lambda j: lens[j] >= (1 << 20))):
-                d = [lat_i for lat_i, j in zip((inf["done_ns"] - arrival[i]
-                                               for i, inf in enumerate(infos)), order) if pick(int(j))]
-                if d:
-                    parts[name] = {"requests": len(d), "p50_ms": _percentile_ms(d, 50),
+            small = lens[ordr] < (1 << 20)
+            for name, pick in (("below_1MB", small), ("from_1MB", ~small)):
+                d = (done - arrival)[pick]
+                if d.size:
+                    parts[name] = {"requests": int(d.size), "p50_ms": _percentile_ms(d, 50),
                                    "p99_ms": _percentile_ms(d, 99)}
-        span = max(inf["done_ns"] for inf in infos) - t0
-        return lat, span, [inf["batch_size"] for inf in infos]
+        span = int(done.max() - arrival.min())
+        return lat, span, n / launches
 
     def run_plain(order, arr_ns):
         n = len(order)
-        t0 = time.monotonic_ns() + 2_000_000
-        lat = [0] * n
-        for i in range(n):
-            ta = t0 + int(arr_ns[i])
-            while time.monotonic_ns() < ta:
-                pass
-            plain_one(int(order[i]))
-            lat[i] = time.monotonic_ns() - ta
-        return lat, time.monotonic_ns() - t0
+        ordr = np.ascontiguousarray(order, dtype=np.uint32)
+        arr = np.ascontiguousarray(arr_ns, dtype=np.int64)
+        rec = np.zeros(2 * n, dtype=np.int64)
+        rc = lib.fp_replay_plain(rbodies, R, ordr.ctypes.data, arr.ctypes.data, n, 2_000_000,
+                                 b",", stream.cuda_stream, rec.ctypes.data)
+        if rc != 0:
+            raise SystemExit("bench: plain trace failed: %s" % fp._lib.strerror(rc))
+        check_bodies("plain trace")
+        arrival, done = rec.reshape(n, 2).T
+        return (done - arrival).tolist(), int(done.max() - arrival.min())
 
     def perm_order(n, seed):
         r = np.random.default_rng(seed)
@@ -1024,13 +968,13 @@ def run_serve(args, world, rank, dist) -> None:
         order = perm_order(n, 200 + k)
         nbytes = float(lens[order].sum())
         parts = {}
-        lat_s, span_s, batch = run_server(order, arr, parts)
+        lat_s, span_s, mean_batch = run_server(order, arr, parts)
         lat_p, span_p = run_plain(order, arr)
         levels.append({
             "load": load, "offered_GBps": load * peak_server, "requests": n,
             "seconds": float(arr[-1]) / 1e9,
             "server": {"GBps": nbytes / (span_s / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_s, 50),
-                       "p99_ms": _percentile_ms(lat_s, 99), "mean_batch": float(np.mean(batch)),
+                       "p99_ms": _percentile_ms(lat_s, 99), "mean_batch": float(mean_batch),
                        "latency_parts": parts},
             "plain": {"GBps": nbytes / (span_p / 1e9) / 1e9, "p50_ms": _percentile_ms(lat_p, 50),
                       "p99_ms": _percentile_ms(lat_p, 99)},

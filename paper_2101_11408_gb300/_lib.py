@@ -17,14 +17,15 @@ STATUS_OK, STATUS_INVALID, STATUS_OVERFLOW, STATUS_UNDERFLOW, STATUS_BAD_SHAPE =
 FORMAT_F64, FORMAT_F32 = 0, 1
 GRAMMAR_DECIMAL, GRAMMAR_HEX, GRAMMAR_JSON = 0, 1, 2
 
-# every symbol include/*.h declares (fpparse_test.h: test hooks)
+# every symbol include/*.h declares (fpparse_test.h: test hooks; fpparse_bench.h:
+# trace replay for measurements)
 EXPORTS = ["fp_max_fields", "fp_parse_f64", "fp_parse_f32", "fp_parse_ex", "fp_parse_f64_batch", "fp_get_stats",
            "fp_get_error", "fp_set_config", "fp_get_config", "fp_autotune", "fp_timing_enable",
            "fp_timing_read", "fp_parse_f64_host", "fp_parse_f64_noalloc", "fp_batch_plan_create",
            "fp_batch_plan_launch", "fp_batch_plan_destroy", "fp_batch_plan_gather",
            "fp_server_create", "fp_server_submit",
            "fp_server_wait", "fp_server_get_stats", "fp_server_destroy", "fp_shutdown",
-           "fp_strerror", "fp_test_arm_stalled_lookback"]
+           "fp_strerror", "fp_test_arm_stalled_lookback", "fp_replay_server", "fp_replay_plain"]
 
 
 class Stats(ctypes.Structure):
@@ -70,6 +71,12 @@ class Options(ctypes.Structure):
     _fields_ = [("delim", ctypes.c_char), ("format", ctypes.c_uint8), ("grammar", ctypes.c_uint8),
                 ("reserved", ctypes.c_uint8), ("columns", ctypes.c_uint32),
                 ("rows_cap", ctypes.c_uint64)]
+
+
+class ReplayBody(ctypes.Structure):
+    _fields_ = [("host_text", ctypes.c_void_p), ("len", ctypes.c_size_t),
+                ("host_f64", ctypes.c_void_p), ("host_status", ctypes.c_void_p),
+                ("out_cap", ctypes.c_size_t)]
 
 
 class FpError(RuntimeError):
@@ -153,6 +160,12 @@ def load(build_if_missing: bool = True):
         lib.fp_server_destroy.restype = ctypes.c_int
         lib.fp_shutdown.argtypes = []
         lib.fp_shutdown.restype = ctypes.c_int
+        lib.fp_replay_server.argtypes = [vp, ctypes.POINTER(ReplayBody), ctypes.c_uint32, vp, vp,
+                                         sz, ctypes.c_int64, vp]
+        lib.fp_replay_server.restype = ctypes.c_int
+        lib.fp_replay_plain.argtypes = [ctypes.POINTER(ReplayBody), ctypes.c_uint32, vp, vp, sz,
+                                        ctypes.c_int64, ctypes.c_char, vp, vp]
+        lib.fp_replay_plain.restype = ctypes.c_int
         lib.fp_test_arm_stalled_lookback.argtypes = [vp, ctypes.c_uint64]
         lib.fp_test_arm_stalled_lookback.restype = ctypes.c_int
         lib.fp_strerror.argtypes = [ctypes.c_int]

@@ -3,7 +3,7 @@
 Every translation unit is compiled for sm_103a only (-gencode
 arch=compute_103a,code=sm_103a), in parallel, and linked with nvcc into one
 shared object exporting the C ABI of include/fpparse.h (and the test hooks of
-include/fpparse_test.h).
+include/fpparse_test.h and the trace replay of include/fpparse_bench.h).
 """
 from __future__ import annotations
 
@@ -19,10 +19,11 @@ LIB = os.path.join(BUILD, "libfpparse.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["fp_parse_kernel.cu", "fp_parse_kernel_ext.cu", "fp_fallback_kernel.cu", "fp_api.cu",
-           "fp_noalloc.cu", "fp_server.cu", "fp_copy_kernel.cu"]
+           "fp_noalloc.cu", "fp_server.cu", "fp_copy_kernel.cu", "fp_replay.cpp"]
 HEADERS = ["fp_device.cuh", "fp_sync.cuh", "fp_types.cuh", "fp_launch.h", "fp_internal.h",
            "fp_parse_kernel.cuh", "fp_copy.h", "fp_arena.h", "pow5_table.inc", "dec_tables.inc",
-           os.path.join(INCLUDE, "fpparse.h"), os.path.join(INCLUDE, "fpparse_test.h")]
+           os.path.join(INCLUDE, "fpparse.h"), os.path.join(INCLUDE, "fpparse_test.h"),
+           os.path.join(INCLUDE, "fpparse_bench.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",
@@ -51,7 +52,7 @@ def build_library(force: bool = False, verbose: bool = False, ptxas_info: bool =
     objs, procs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         objs.append(o)
         if force or _stale(o, [s, __file__] + headers):
             cmd = [nvcc()] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + \

@@ -129,6 +129,9 @@ FP_HD uint64_t load_lo(const uint64_t* p) {
 struct ElResult {
   uint64_t bits;  // positive pattern of the format, or EL_ABORT
   int two_mul;    // 1 if the second 64x64 product was needed
+  // ST_OK, ST_UNDERFLOW (a zero result) or ST_OVERFLOW (infinity), decided
+  // where the result is (ST_GENERAL when Algorithm 1 gave up)
+  uint8_t status;
 };
 
 // w in [1, 2^64), q in [FP_POW5_QMIN, FP_POW5_QMAX]; tab points at the table
@@ -140,6 +143,7 @@ template <class F = F64>
 FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort) {
   ElResult r;
   r.two_mul = 0;
+  r.status = ST_OK;
   // Normalise the decimal significand into [2^63, 2^64) (Algorithm 1).
   int l = clz64(w);
   w <<= l;
@@ -162,6 +166,7 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   // still carry into the top word, so give up (Algorithm 1).
   if (allow_abort && lo == ~0ull && (q < -27 || q > 55)) {
     r.bits = EL_ABORT;
+    r.status = ST_GENERAL;
     return r;
   }
   // MBITS + 2 significant bits (the significand plus one rounding bit)
@@ -178,12 +183,14 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
     // smallest normal number, whose bit pattern is that same integer.
     if (E <= -63) {
       r.bits = 0;
+      r.status = ST_UNDERFLOW;
       return r;
     }
     m >>= (1 - E);
     m += (m & 1);
     m >>= 1;
     r.bits = m;
+    r.status = m ? ST_OK : ST_UNDERFLOW;
     return r;
   }
   // Ties to even (Sections 8.1 and 9.1): only for q in [TIE_QMIN,
@@ -201,7 +208,9 @@ FP_HD ElResult eisel_lemire(uint64_t w, int q, const Pow5& tab, bool allow_abort
   // significand field then being zero), as Algorithm 1's carry step does.
   // A field of EMAX_FIELD or more is infinity.
   const uint64_t bits = ((uint64_t)(E - 1) << F::MBITS) + m;
-  r.bits = bits >= F::INF ? F::INF : bits;
+  const bool ovf = bits >= F::INF;
+  r.bits = ovf ? F::INF : bits;
+  r.status = ovf ? ST_OVERFLOW : ST_OK;
   return r;
 }
 
@@ -212,9 +221,40 @@ template <class F = F64>
 FP_HD ElResult convert_wq(uint64_t w, int64_t q, const Pow5& tab, bool allow_abort) {
   const int qc = q < FP_POW5_QMIN ? FP_POW5_QMIN : (q > FP_POW5_QMAX ? FP_POW5_QMAX : (int)q);
   ElResult r = eisel_lemire<F>(w, qc, tab, allow_abort);
-  if (q < FP_POW5_QMIN) r.bits = 0;
-  if (q > FP_POW5_QMAX) r.bits = F::INF;
+  if (q < FP_POW5_QMIN) {
+    r.bits = 0;
+    r.status = ST_UNDERFLOW;
+  }
+  if (q > FP_POW5_QMAX) {
+    r.bits = F::INF;
+    r.status = ST_OVERFLOW;
+  }
   return r;
+}
+
+// The nearest pattern of F to the integer w (ties to even): the conversion
+// instruction rounds correctly (the host build uses the host's conversion,
+// also round to nearest).  Integers never overflow either format.
+template <class F>
+FP_HD uint64_t int_to_bits(uint64_t w) {
+#ifdef __CUDA_ARCH__
+  if constexpr (F::MBITS == F64::MBITS)
+    return (uint64_t)__double_as_longlong(__ull2double_rn(w));
+  else
+    return (uint64_t)__float_as_uint(__ull2float_rn(w));
+#else
+  if constexpr (F::MBITS == F64::MBITS) {
+    const double d = (double)w;
+    uint64_t b;
+    __builtin_memcpy(&b, &d, 8);
+    return b;
+  } else {
+    const float f = (float)w;
+    uint32_t b;
+    __builtin_memcpy(&b, &f, 4);
+    return b;
+  }
+#endif
 }
 
 template <class F = F64>

@@ -699,6 +699,8 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   WarpSmem& sm = smem[wib];
   Ctl* ctl = p.ctl;
+  // the parse grid this launch depends on has completed, its writes visible
+  grid_dependency_wait();
   const unsigned long long nq_all = *(volatile unsigned long long*)&ctl->qcount;
   const unsigned long long nov_all = *(volatile unsigned long long*)&ctl->ovf_count;
   // Nothing pending (the usual case): nothing to decide and nothing to
@@ -763,10 +765,24 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
 
 }  // namespace
 
+// A programmatic dependent launch: the parse kernel releases it as it starts,
+// so this launch's set-up overlaps the parse; its blocks wait on the device
+// (griddepcontrol.wait) until the parse grid has completed and its writes
+// are visible.  On a workload with nothing pending they then return at once,
+// and the call pays little more than the parse.
 template <class F>
 static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream) {
-  fallback_kernel<F><<<grid, FB_NT, 0, stream>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(FB_NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fallback_kernel<F>, p);
 }
 
 cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32) {

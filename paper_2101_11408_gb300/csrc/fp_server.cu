@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
@@ -75,6 +76,7 @@ struct Request {
   uint64_t text_off = 0;        // where the text starts: off + (h_text mod 16)
   fp_request_info_t info{};
   bool done = false;
+  std::atomic<bool> done_flag{false};  // set with `done`, read by waiters without the lock
 };
 
 // The address the device uses for host memory p, or null when p is not
@@ -109,6 +111,8 @@ struct Slot {
   const fp::ScatterPiece* spieces_dv = nullptr;
   uint32_t cap_gpieces = 0, cap_spieces = 0;
   bool unmapped_out = false;     // some request's results go back by copy calls
+  bool direct = false;           // one request, results and count written to host memory by the parse
+  uint64_t* h_counts_dv = nullptr;  // device view of h_counts
   Phase phase = Phase::FREE;
   std::vector<Request*> reqs;
   std::vector<const char*> texts;
@@ -156,6 +160,7 @@ void finish(fp_server* S, Request* r, fp_err_t err) {
   {
     std::lock_guard<std::mutex> lk(S->mu);
     r->done = true;
+    r->done_flag.store(true, std::memory_order_release);
     S->outstanding--;
     S->st.completed++;
     if (err == FP_OK) S->st.fields += r->info.count;
@@ -192,7 +197,7 @@ bool retire(fp_server* S, Slot& sl) {
     }
     for (size_t i = 0; i < sl.reqs.size(); i++) {
       Request* r = sl.reqs[i];
-      const uint64_t count = sl.h_counts[i];
+      const uint64_t count = *(volatile uint64_t*)&sl.h_counts[i];
       r->info.count = count;
       if (count > r->len) {  // cannot happen: a text of len bytes has at most len fields
         r->info.error = FP_ERR_INTERNAL;
@@ -236,6 +241,30 @@ bool retire(fp_server* S, Slot& sl) {
   return false;
 }
 
+// A launch of one request whose host arrays the device can reach and whose
+// text is below DIRECT_BYTES: one copy in, then the parse writes the results
+// and the count straight into the caller's pinned arrays (no gather, scatter
+// or count copy), as fp_parse_f64_host does for such texts alone.
+constexpr uint64_t DIRECT_BYTES = 8u << 20;
+
+bool launch_direct(fp_server* S, Slot& sl, Request* r) {
+  uint8_t* dst = reinterpret_cast<uint8_t*>(S->d_text) + r->text_off;
+  if (r->len && cudaMemcpyAsync(dst, r->h_text, r->len, cudaMemcpyHostToDevice, sl.stream) !=
+                    cudaSuccess)
+    return false;
+  const char* text = reinterpret_cast<const char*>(dst);
+  const size_t len = r->len;
+  const uint64_t base = 0, cap = std::min<uint64_t>(r->out_cap, r->len);
+  *(volatile uint64_t*)&sl.h_counts[0] = ~0ull;
+  if (fp::parse_batch_ranges(&text, &len, 1, S->cfg.delim,
+                             reinterpret_cast<double*>(r->dv_f64), r->dv_status, &base, &cap,
+                             sl.h_counts_dv, sl.stream) != FP_OK)
+    return false;
+  return cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
+                         sl.stream) == cudaSuccess &&
+         cudaEventRecord(sl.ev_counts, sl.stream) == cudaSuccess;
+}
+
 // Launch step for one free slot.
 void launch(fp_server* S, Slot& sl) {
   const size_t kmax = std::min<size_t>(S->admitted.size(), S->cfg.max_batch);
@@ -245,6 +274,25 @@ void launch(fp_server* S, Slot& sl) {
   while (k < kmax && bytes + S->admitted[k]->len <= cap) bytes += S->admitted[k++]->len;
   sl.reqs.assign(S->admitted.begin(), S->admitted.begin() + k);
   S->admitted.erase(S->admitted.begin(), S->admitted.begin() + k);
+  sl.unmapped_out = false;
+  sl.direct = false;
+  if (k == 1) {
+    Request* r = sl.reqs[0];
+    if (r->len < DIRECT_BYTES && r->dv_f64 && r->dv_status && sl.h_counts_dv) {
+      sl.direct = true;
+      if (!launch_direct(S, sl, r)) {
+        fail_slot(S, sl, FP_ERR_CUDA);
+        return;
+      }
+      r->info.launch_ns = now_ns();
+      r->info.batch_size = 1;
+      sl.phase = Phase::PARSING;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->st.launches++;
+      S->st.max_batch_seen = std::max<uint64_t>(S->st.max_batch_seen, 1);
+      return;
+    }
+  }
   sl.texts.resize(k);
   sl.lens.resize(k);
   sl.base.resize(k);
@@ -328,8 +376,14 @@ void launch(fp_server* S, Slot& sl) {
   S->st.max_batch_seen = std::max<uint64_t>(S->st.max_batch_seen, k);
 }
 
+// After its last piece of work the scheduler keeps polling for this long
+// before it sleeps on the submission condition (a sleeping thread takes tens
+// of microseconds to wake, which a request arriving soon after would wait).
+constexpr int64_t SPIN_NS = 2000000;
+
 void scheduler(fp_server* S) {
   cudaSetDevice(S->device);
+  int64_t last_work = now_ns();
   for (;;) {
     bool progressed = false, busy = false;
     for (Slot& sl : S->slots) {
@@ -370,8 +424,11 @@ void scheduler(fp_server* S) {
       progressed = true;
       busy = true;
     }
-    if (progressed) continue;
-    if (busy || !S->admitted.empty()) {
+    if (progressed) {
+      last_work = now_ns();
+      continue;
+    }
+    if (busy || !S->admitted.empty() || now_ns() - last_work < SPIN_NS) {
       std::this_thread::yield();
     } else {
       std::unique_lock<std::mutex> lk(S->mu);
@@ -447,6 +504,7 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
     SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
     SRV_CUDA(cudaMalloc(&sl.d_counts, cfg->max_batch * sizeof(uint64_t)));
     SRV_CUDA(cudaMallocHost(&sl.h_counts, cfg->max_batch * sizeof(uint64_t)));
+    sl.h_counts_dv = device_view(sl.h_counts);
     SRV_CUDA(cudaMallocHost(&sl.h_err, sizeof(unsigned int)));
     *sl.h_err = 0;
     // piece tables: every unit of a batch once, plus one partial piece per request
@@ -524,6 +582,16 @@ extern "C" fp_err_t fp_server_wait(fp_server* S, uint64_t id, int64_t timeout_ns
   auto it = S->live.find(id);
   if (it == S->live.end()) return FP_ERR_ARG;
   Request* r = it->second;
+  if (!r->done && timeout_ns != 0) {
+    // most requests end within a few hundred microseconds: poll for that
+    // long (lock released) before sleeping on the completion condition
+    lk.unlock();
+    const int64_t t_end = now_ns() + SPIN_NS / 4;
+    while (!r->done_flag.load(std::memory_order_acquire) && now_ns() < t_end)
+      std::this_thread::yield();
+    lk.lock();
+    it = S->live.find(id);  // other submissions may have rehashed the map meanwhile
+  }
   if (!r->done) {
     if (timeout_ns == 0) return FP_ERR_TIMEOUT;
     auto pred = [&] { return r->done; };

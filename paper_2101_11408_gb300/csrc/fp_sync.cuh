@@ -80,4 +80,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Programmatic dependent launch (sm_90 and later): a grid launched after
+// this one with programmatic stream serialization may start once every block
+// of this grid has executed grid_launch_dependents (or exited);
+// grid_dependency_wait blocks until the grids the caller depends on have
+// completed and their memory operations are visible to it.
+__device__ __forceinline__ void grid_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 }  // namespace fp

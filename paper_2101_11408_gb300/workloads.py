@@ -362,3 +362,29 @@ def pack_buffers(texts: list[bytes], skew: bool = True) -> tuple[np.ndarray, lis
         if t:
             arr[s:s + len(t)] = np.frombuffer(t, dtype=np.uint8)
     return arr, starts
+
+
+def integer_lines(n: int, seed: int) -> list[str]:
+    """Plain integers, the shape of the paper's integer file (Section 12):
+    mostly uniform 32-bit values, plus signs, leading zeros, values around
+    2^53 (odd ones above it round to even) and up to 19 digits."""
+    r = _rng(seed)
+    kinds = r.integers(0, 10, size=n)
+    out = []
+    for k, a, b in zip(kinds.tolist(), r.integers(0, 1 << 32, size=n).tolist(),
+                       r.integers(0, 1 << 62, size=n).tolist()):
+        if k < 6:
+            out.append(str(a))
+        elif k == 6:
+            out.append("-" + str(a))
+        elif k == 7:
+            out.append("+" + "0" * (a % 5) + str(a % 100000))
+        elif k == 8:
+            out.append(str((1 << 53) + (a % 4096)))
+        else:
+            out.append(str(b * 2 + (a & 1)))  # up to 19 digits
+    return out
+
+
+def integer_text(n: int, seed: int) -> bytes:
+    return "\n".join(integer_lines(n, seed)).encode()

@@ -30,5 +30,7 @@ inline void fence_proxy_async_smem() {}
 inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t*) {
   std::memcpy(dst, src, bytes);
 }
+inline void grid_launch_dependents() {}
+inline void grid_dependency_wait() {}
 
 }  // namespace fp

@@ -45,8 +45,8 @@ void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& 
   uint64_t sgn = ft.sign;
   if (F::MBITS != F64::MBITS) sgn = ft.sign ? F::SIGN : 0;
   uint64_t bits = ft.w ? (r.bits | sgn) : sgn;
-  unsigned status = ft.w ? status_of<F>(r.bits) : ST_OK;
-  if (!ok || (ft.w && r.bits == EL_ABORT)) {
+  unsigned status = !ok ? (unsigned)ST_GENERAL : (ft.w ? (unsigned)r.status : (unsigned)ST_OK);
+  if (status == ST_GENERAL) {
     const FieldResult g = parse_short_field<F>(tile + s, n, tab, grammar);
     if (g.status == ST_PENDING) {
       std::printf("P\n");

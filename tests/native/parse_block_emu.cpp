@@ -71,7 +71,7 @@ inline emu_dim emu_bid() { return emu_dim{(unsigned)(emu::cur / emu::BT), 0, 0};
 #define blockIdx (emu_bid())
 #define gridDim (emu_dim{(unsigned)emu::nblocks, 1, 1})
 
-enum { K_BALLOT = 1, K_ANY, K_SHFL, K_UP, K_XOR, K_RADD, K_RMIN };
+enum { K_BALLOT = 1, K_ANY, K_ALL, K_SHFL, K_UP, K_XOR, K_RADD, K_RMIN };
 template <class T>
 uint64_t to_u(T v) {
   uint64_t u = 0;
@@ -89,6 +89,12 @@ unsigned int __ballot_sync(unsigned int, int pred) {
   unsigned int m = 0;
   for (int i = 0; i < 32; i++) m |= (unsigned int)(s[i] & 1) << i;
   return m;
+}
+int __all_sync(unsigned int, int pred) {
+  const uint64_t* s = emu::post(pred ? 1 : 0, K_ALL);
+  for (int i = 0; i < 32; i++)
+    if (!s[i]) return 0;
+  return 1;
 }
 int __any_sync(unsigned int, int pred) {
   const uint64_t* s = emu::post(pred ? 1 : 0, K_ANY);

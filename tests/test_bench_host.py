@@ -125,40 +125,6 @@ def test_cpu_baseline_fields():
     assert c["value"] > 0 and "context" not in c
 
 
-@pytest.mark.parametrize("seed", [1, 2, 3])
-def test_result_ring_never_overlaps_a_held_region(seed):
-    """The serving bench's result ring: every region lies in the ring and
-    overlaps no region still held; regions are given back oldest first, and
-    none while the new one fits after the newest."""
-    import random
-    rnd = random.Random(seed)
-    cap = 1000
-    ring = bench.ResultRing(cap)
-    live = {}          # tag -> (start, end)
-    released = []
-
-    def release(tag):
-        released.append(tag)
-        del live[tag]
-
-    for tag in range(20000):
-        need = rnd.choice([1, 7, 64, 100, 333, 500, 999, 1000]) if rnd.random() < 0.3 \
-            else rnd.randrange(1, 120)
-        before = len(released)
-        fits_after_head = bool(ring.held) and ring.head + need <= cap and (
-            ring.held[-1][0] >= ring.held[0][0] or ring.head + need <= ring.held[0][0])
-        a = ring.reserve(need, tag, release)
-        assert 0 <= a and a + need <= cap
-        for s, e in live.values():
-            assert a + need <= s or e <= a, (tag, a, need, s, e)
-        live[tag] = (a, a + need)
-        if fits_after_head:
-            assert len(released) == before and a == ring.held[-2][1]
-    assert released == sorted(released)
-    with pytest.raises(ValueError):
-        ring.reserve(cap + 1, -1, release)
-
-
 def test_profile_commands_run_committed_files():
     """Every profile summary gives the command that made it; each bench
     invocation there still parses with the bench's current arguments, and

@@ -137,3 +137,10 @@ def test_f32_and_f64_calls_interleave_on_one_stream():
         rb, rs = oracle.parse_buffer(a)
         assert np.array_equal(v.cpu().numpy().view(np.uint64), rb)
         assert_parity32(b)
+
+
+def test_integer_file_to_binary32():
+    """Integer files to binary32: the conversion instruction rounds 32- to
+    64-bit integers to 24 bits, to nearest with ties to even."""
+    lines = workloads.integer_lines(1_000_000, 141) + [str((1 << 24) + k) for k in range(64)]
+    assert_parity32("\n".join(lines).encode(), lines=lines)

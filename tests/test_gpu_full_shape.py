@@ -95,17 +95,21 @@ def test_served_workload_at_full_shape_alone_equals_mix_and_oracle():
     # arrive while others are on the GPU
     rnd = random.Random(77)
     bufs = []
+    for t in texts:  # pinned before the arrivals start
+        n = max(len(t), 1)
+        bufs.append((torch.frombuffer(bytearray(t), dtype=torch.uint8).pin_memory(),
+                     torch.full((n,), -5.0, dtype=torch.float64).pin_memory(),
+                     torch.full((n,), 0xEE, dtype=torch.uint8).pin_memory()))
+    gaps = [rnd.expovariate(1.0 / 0.0002) for _ in texts]  # mean 0.2 ms between arrivals
     with fp.Server(device_budget=40_000_000_000, max_batch=1024, max_inflight=4,
                    delim=b",") as srv:
         rids = []
-        for t in texts:
-            n = max(len(t), 1)
-            h = (torch.frombuffer(bytearray(t), dtype=torch.uint8).pin_memory(),
-                 torch.full((n,), -5.0, dtype=torch.float64).pin_memory(),
-                 torch.full((n,), 0xEE, dtype=torch.uint8).pin_memory())
-            bufs.append(h)
+        t_next = time.perf_counter()
+        for h, gap in zip(bufs, gaps):
+            while time.perf_counter() < t_next:
+                pass
             rids.append(srv.submit(*h))
-            time.sleep(rnd.expovariate(1.0 / 0.002))  # mean 2 ms between arrivals
+            t_next += gap
         infos = [srv.wait(r, timeout_s=300) for r in rids]
         stats = srv.stats()
     assert stats["completed"] == len(texts)

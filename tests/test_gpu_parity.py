@@ -473,3 +473,13 @@ def test_host_entry_point_pipelined(delim):
         assert np.array_equal(h_st[:k].numpy(), rs)
         assert (h_st[k:k + 1000].numpy() == 0xEE).all()  # nothing written past the count
     assert fp.get_error() == 0
+
+
+def test_integer_file():
+    """The integer file's shape (Section 12): whole groups of plain integers
+    take the conversion instruction; mixed groups keep Algorithm 1."""
+    lines = workloads.integer_lines(2_000_000, 131)
+    assert_parity("\n".join(lines).encode(), lines=lines)
+    mixed = workloads.integer_lines(300_000, 132) + workloads.bulk_mixed_lines(100_000, 133)
+    random.Random(134).shuffle(mixed)
+    assert_parity("\n".join(mixed).encode(), lines=mixed)

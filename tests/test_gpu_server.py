@@ -58,9 +58,9 @@ def alone(texts):
 
 def serve(texts, server, stagger_s=0.0, seed=0):
     rnd = random.Random(seed)
+    arrays = [host_arrays(t) for t in texts]  # pinned before the submissions start
     reqs = []
-    for t in texts:
-        h = host_arrays(t)
+    for h in arrays:
         reqs.append((server.submit(*h), h))
         if stagger_s:
             time.sleep(rnd.random() * stagger_s)

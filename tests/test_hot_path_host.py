@@ -278,7 +278,9 @@ HOT_MUTANTS = [
     ("exponent's sign", "      if (ch == '-') ex = -ex;\n", ""),
     ("single point", "  if (Ms & (Ms - 1u)) return false;\n", ""),
     ("rounding step", "  m = (m + 1) >> 1;\n", "  m = m >> 1;\n"),
-    ("overflow to infinity", "  r.bits = bits >= F::INF ? F::INF : bits;\n", "  r.bits = bits;\n"),
+    ("overflow to infinity", "  r.bits = ovf ? F::INF : bits;\n", "  r.bits = bits;\n"),
+    ("overflow status", "  r.status = ovf ? ST_OVERFLOW : ST_OK;\n", "  r.status = ST_OK;\n"),
+    ("underflow status", "    r.status = m ? ST_OK : ST_UNDERFLOW;\n", "    r.status = ST_OK;\n"),
     ("19-digit truncation", "      exp_adj++;\n      sticky |= (d != 0);", "      sticky |= (d != 0);"),
     ("w+1 check", "    ElResult b = convert_wq<F>(w + 1, q, tab, true);",
      "    ElResult b = convert_wq<F>(w, q, tab, true);"),
