@@ -232,31 +232,6 @@ FP_HD ElResult convert_wq(uint64_t w, int64_t q, const Pow5& tab, bool allow_abo
   return r;
 }
 
-// The nearest pattern of F to the integer w (ties to even): the conversion
-// instruction rounds correctly (the host build uses the host's conversion,
-// also round to nearest).  Integers never overflow either format.
-template <class F>
-FP_HD uint64_t int_to_bits(uint64_t w) {
-#ifdef __CUDA_ARCH__
-  if constexpr (F::MBITS == F64::MBITS)
-    return (uint64_t)__double_as_longlong(__ull2double_rn(w));
-  else
-    return (uint64_t)__float_as_uint(__ull2float_rn(w));
-#else
-  if constexpr (F::MBITS == F64::MBITS) {
-    const double d = (double)w;
-    uint64_t b;
-    __builtin_memcpy(&b, &d, 8);
-    return b;
-  } else {
-    const float f = (float)w;
-    uint32_t b;
-    __builtin_memcpy(&b, &f, 4);
-    return b;
-  }
-#endif
-}
-
 template <class F = F64>
 FP_HD uint8_t status_of(uint64_t pos_bits) {
   if (pos_bits == 0) return ST_UNDERFLOW;  // nonzero text, zero result

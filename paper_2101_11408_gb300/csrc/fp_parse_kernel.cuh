@@ -490,30 +490,14 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     // Algorithm 1.  Fields it cannot settle are marked for the general
     // tokenizer, which runs in a separate pass so that this loop stays free
     // of rare branches.
-    auto tokenize = [&](int s, int e, FastToken& ft) -> bool {
+    auto parse_hot = [&](int s, int e, unsigned long long& bits, uint8_t& status) {
+      FastToken ft;
       ft.w = 0;
       ft.q = 0;
       ft.sign = 0;
       bool ok = parse_window(tile, *wtab, s, e, ft);
       if constexpr ((MODE & MODE_JSON) != 0) ok = ok && json_ok_fast(tile, s, ft);
-      return ok;
-    };
-    // A group whose fields are all plain integers (q = 0; integer files, as
-    // Section 12's) takes the conversion instruction, which rounds w to
-    // nearest, ties to even, exactly as Algorithm 1 would, for any w < 2^64
-    // (the q = 0 case of Clinger's fast path, Section 3, without its
-    // multiply); all_int is decided per group, so that mixed groups keep one
-    // straight path.
-    auto convert = [&](const FastToken& ft, bool ok, bool all_int, unsigned long long& bits,
-                       uint8_t& status) {
-      ElResult r;
-      if (all_int) {
-        r.bits = int_to_bits<F>(ft.w);
-        r.two_mul = 0;
-        r.status = ST_OK;
-      } else {
-        r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
-      }
+      const ElResult r = convert_wq<F>(ft.w ? ft.w : 1ull, ok ? ft.q : 0, pow5, true);
       c_two += ok & (uint32_t)r.two_mul;
       uint64_t sgn = ft.sign;  // the binary64 sign bit
       if constexpr (F::MBITS != F64::MBITS) sgn = ft.sign ? F::SIGN : 0;
@@ -670,15 +654,10 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         gi = __shfl_sync(0xFFFFFFFFu, gi, 0);
         if (gi >= ngroups) break;
         const uint32_t k = 32 * gi + lane;
-        const bool act = k < cntw;
         uint8_t status = ST_OK;
-        FastToken ft;
-        bool ok = false;
-        if (act) ok = tokenize(Sw[k], Sw[k + 1] - 1, ft);
-        const bool all_int = __all_sync(0xFFFFFFFFu, !act || !ok || ft.q == 0);
-        if (act) {
+        if (k < cntw) {
           unsigned long long bits;
-          convert(ft, ok, all_int, bits, status);
+          parse_hot(Sw[k], Sw[k + 1] - 1, bits, status);
           stage_bits[k] = bits;
           stage_st[k] = status;
         }

@@ -140,7 +140,7 @@ def test_f32_and_f64_calls_interleave_on_one_stream():
 
 
 def test_integer_file_to_binary32():
-    """Integer files to binary32: the conversion instruction rounds 32- to
-    64-bit integers to 24 bits, to nearest with ties to even."""
+    """Integer files to binary32: 32- to 64-bit integers rounded to 24 bits,
+    to nearest with ties to even (and the ties just above 2^24)."""
     lines = workloads.integer_lines(1_000_000, 141) + [str((1 << 24) + k) for k in range(64)]
     assert_parity32("\n".join(lines).encode(), lines=lines)

@@ -476,8 +476,8 @@ def test_host_entry_point_pipelined(delim):
 
 
 def test_integer_file():
-    """The integer file's shape (Section 12): whole groups of plain integers
-    take the conversion instruction; mixed groups keep Algorithm 1."""
+    """The integer file's shape (Section 12), alone and mixed with the bulk
+    shapes: signs, leading zeros, values around 2^53 and up to 19 digits."""
     lines = workloads.integer_lines(2_000_000, 131)
     assert_parity("\n".join(lines).encode(), lines=lines)
     mixed = workloads.integer_lines(300_000, 132) + workloads.bulk_mixed_lines(100_000, 133)

@@ -180,9 +180,8 @@ def test_whole_path_on_the_hard_mix(emu, tmp_path):
 
 @pytest.mark.parametrize("f32", [False, True])
 def test_integer_groups(emu, f32):
-    """Integer files (Section 12's integer set): whole groups of plain
-    integers take the conversion instruction instead of Algorithm 1; mixed
-    groups keep Algorithm 1.  Both must give the oracle's results."""
+    """Integer files (Section 12's integer set), alone and mixed with the
+    bulk shapes: the oracle's results."""
     text = workloads.integer_text(6000, 123)
     _check(emu, text, f32=f32, max_pending=0)
     mixed = "\n".join(workloads.integer_lines(2000, 124) + workloads.bulk_mixed_lines(500, 125))
