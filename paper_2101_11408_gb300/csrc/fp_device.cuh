@@ -718,11 +718,8 @@ FP_HD bool parse_window(const uint8_t* tile, const WindowTables& wt, int s, int 
   }
   // the five high positions zero, so that the value is below 10^19
   if (x[0] != 0x30303030u || (x[1] & 0xFFu) != 0x30u) return false;
-  uint64_t w = dig4(x[1]) * 10000u + dig4(x[2]);
-  w = w * 10000u + dig4(x[3]);
-  w = w * 10000u + dig4(x[4]);
-  w = w * 10000u + dig4(x[5]);
-  t.w = w;
+  // two 8-digit halves in 32-bit arithmetic, then two 64-bit steps
+  t.w = ((uint64_t)dig4(x[1]) * 100000000u + dig8(x[2], x[3])) * 100000000ull + dig8(x[4], x[5]);
   // the last digit sits at window position 23 once the exponent part is
   // zeros: with a point, 23 - dpos of the digits follow it
   t.q = ex + (hp ? dpos - 23 : em - 24);

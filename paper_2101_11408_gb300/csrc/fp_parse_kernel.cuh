@@ -648,11 +648,14 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       const uint32_t cntw = hi - lo;
       const uint32_t ngroups = (cntw + 31) / 32;  // at most S_CAP / 32 = 32
       uint32_t general = 0;  // this warp's groups with a field for the general tokenizer
+      // each group's ticket is taken before the group ahead of it is parsed,
+      // so the atomic's round trip overlaps that parse
+      uint32_t gnext = 0;
+      if (lane == 0) gnext = atomicAdd(&ms->group[sset], 1u);
       for (;;) {
-        uint32_t gi = 0;
-        if (lane == 0) gi = atomicAdd(&ms->group[sset], 1u);
-        gi = __shfl_sync(0xFFFFFFFFu, gi, 0);
+        const uint32_t gi = __shfl_sync(0xFFFFFFFFu, gnext, 0);
         if (gi >= ngroups) break;
+        if (lane == 0) gnext = atomicAdd(&ms->group[sset], 1u);
         const uint32_t k = 32 * gi + lane;
         uint8_t status = ST_OK;
         if (k < cntw) {
