@@ -439,10 +439,11 @@ FP_API fp_err_t fp_timing_read(struct CUstream_st *stream, double *parse_ms,
  * through their device addresses; otherwise the library reads the field
  * count and copies back exactly that many results.  When all three host
  * arrays are pinned and len >= 32 MB, the text is cut at separators into
- * segments (at least four, of at most about 32 MB) whose copies in, parses
- * and copies out overlap,
- * each segment's count written by its parse kernel into pinned host memory
- * (results identical).  Synchronous: returns after the
+ * segments (at least four, of at most about 32 MB; on texts of 64 MB and
+ * more the last three shrink to 16, 8 and 4 MB, so that little is left to
+ * do after the last bytes arrive) whose copies in, parses and copies out
+ * overlap, each segment's count written by its parse kernel into pinned
+ * host memory (results identical).  Synchronous: returns after the
  * results are in host memory.  The staging buffers are allocated with
  * cudaMalloc on first use and grown as needed.
  */

@@ -328,21 +328,25 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
       cnt = cn.pad_bit;
     }
     MaskT mask = 0;
+    // one loop per separator test (the choice is block-uniform), so that no
+    // word pays for the tests it does not use
+    auto scan_granules = [&](auto flags) {
 #pragma unroll
-    for (int k = 0; k < L::SEG_PER_THREAD; k++) {
-      const int j = tid * L::SEG_PER_THREAD + k;  // granule within the chunk
-      const uint4 v = *reinterpret_cast<const uint4*>(tile + PAD + 16 * j);
-      const uint32_t w4[4] = {v.x, v.y, v.z, v.w};
-      uint32_t z[4];
-#pragma unroll
-      for (int i = 0; i < 4; i++)
-        z[i] = one_sep ? sep_flags_one(w4[i], NLW)
-                       : (dl_ascii ? sep_flags_two(w4[i], NLW, DLW)
-                                   : (sep_flags_one(w4[i], NLW) | zero_bytes(w4[i] ^ DLW)));
-      // one bit per byte position
-      const uint32_t m16 = (flag_pair(z[0], z[1]) >> 7) | (flag_pair(z[2], z[3]) << 1);
-      mask |= (MaskT)m16 << (16 * k);
-    }
+      for (int k = 0; k < L::SEG_PER_THREAD; k++) {
+        const int j = tid * L::SEG_PER_THREAD + k;  // granule within the chunk
+        const uint4 v = *reinterpret_cast<const uint4*>(tile + PAD + 16 * j);
+        // one bit per byte position
+        const uint32_t m16 = (flag_pair(flags(v.x), flags(v.y)) >> 7) |
+                             (flag_pair(flags(v.z), flags(v.w)) << 1);
+        mask |= (MaskT)m16 << (16 * k);
+      }
+    };
+    if (one_sep)
+      scan_granules([&](uint32_t w) { return sep_flags_one(w, NLW); });
+    else if (dl_ascii)
+      scan_granules([&](uint32_t w) { return sep_flags_two(w, NLW, DLW); });
+    else
+      scan_granules([&](uint32_t w) { return sep_flags_one(w, NLW) | zero_bytes(w ^ DLW); });
     {
       // A boundary at byte b is a field start iff o <= b < endx - 1, plus
       // the virtual boundary o - 1 (the buffer's first field, when it has

@@ -450,9 +450,9 @@ def test_autotune_picks_a_valid_config(tmp_path):
 @pytest.mark.parametrize("delim", [b"\n", b","])
 def test_host_entry_point_pipelined(delim):
     """Texts of 32 MB and more in pinned memory take the pipelined path
-    (segments cut at separators, results written to the host arrays on the
-    device); they must equal the oracle, and pageable copies of the same
-    arrays (the one-copy path)."""
+    (segments cut at separators, parsed as they arrive, their results
+    copied back at the running field total); they must equal the oracle,
+    and pageable copies of the same arrays (the one-copy path)."""
     parts = [workloads.bulk_mixed_text(1_500_000, 91), workloads.hard_case_text(20_000, 92),
              b"7" * (3 << 20),  # a field of 3 MB: no separator near some cuts
              workloads.bulk_mixed_text(800_000, 93)]
@@ -472,6 +472,29 @@ def test_host_entry_point_pipelined(delim):
         assert np.array_equal(h_out[:k].numpy().view(np.uint64), rb)
         assert np.array_equal(h_st[:k].numpy(), rs)
         assert (h_st[k:k + 1000].numpy() == 0xEE).all()  # nothing written past the count
+    assert fp.get_error() == 0
+
+
+def test_host_entry_point_pipelined_tapered_segments():
+    """A text of about 80 MB in pinned memory: full segments, then three
+    shrinking ones, each segment's results copied back at the running field
+    total; hard cases (fields for the fallback kernel) sit in the first and
+    in the last, smallest segments."""
+    parts = [workloads.hard_case_text(5_000, 135), workloads.bulk_mixed_text(4_000_000, 136),
+             workloads.hard_case_text(5_000, 137)]
+    text = b"\n".join(parts)
+    assert len(text) > (72 << 20)
+    n = len(text)
+    rb, rs = oracle.parse_buffer(text)
+    h_text = torch.frombuffer(bytearray(text), dtype=torch.uint8).pin_memory()
+    h_out = torch.full((n,), -1.0, dtype=torch.float64).pin_memory()
+    h_st = torch.full((n,), 0xEE, dtype=torch.uint8).pin_memory()
+    for rep in range(2):
+        k = fp.parse_f64_host_into(h_text, h_out, h_st)
+        assert k == rb.size, rep
+        assert np.array_equal(h_out[:k].numpy().view(np.uint64), rb), rep
+        assert np.array_equal(h_st[:k].numpy(), rs), rep
+        assert (h_st[k:k + 1000].numpy() == 0xEE).all()
     assert fp.get_error() == 0
 
 
