@@ -372,7 +372,7 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
 template <class Range>
 fp_err_t batch_impl(const char* const* texts, const size_t* lens, uint32_t nbuf, char delim,
                     double* out_f64, uint8_t* out_status, uint64_t* out_counts,
-                    cudaStream_t stream, Range range) {
+                    cudaStream_t stream, Range range, unsigned int* err_out = nullptr) {
   if (!texts || !lens || !out_counts) return FP_ERR_ARG;
   if (nbuf == 0 || nbuf > MAX_BUFS) return FP_ERR_ARG;
   bool any = false;
@@ -403,6 +403,7 @@ fp_err_t batch_impl(const char* const* texts, const size_t* lens, uint32_t nbuf,
   p.delim = (unsigned char)delim;
   p.out_bits = reinterpret_cast<unsigned long long*>(out_f64);
   p.out_status = out_status;
+  p.err_out = err_out;
   if (nbuf == 1) {
     const auto r = range(0);
     fill_desc(p.one, texts[0], lens[0], 0, total, r.first, r.second, out_counts);
@@ -434,10 +435,11 @@ namespace fp {
 fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32_t nbuf,
                             char delim, double* out_f64, uint8_t* out_status,
                             const uint64_t* out_base, const uint64_t* out_cap,
-                            uint64_t* out_counts, cudaStream_t stream) {
+                            uint64_t* out_counts, cudaStream_t stream, unsigned int* err_out) {
   if (!out_base || !out_cap) return FP_ERR_ARG;
   return batch_impl(texts, lens, nbuf, delim, out_f64, out_status, out_counts, stream,
-                    [&](uint32_t b) { return std::make_pair(out_base[b], out_cap[b]); });
+                    [&](uint32_t b) { return std::make_pair(out_base[b], out_cap[b]); },
+                    err_out);
 }
 
 fp_err_t reserve_stream_scratch(cudaStream_t stream, unsigned long long chunks, uint32_t nbuf) {

@@ -759,6 +759,8 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
       ctl->ovf_count = 0;
       ctl->done_fallback = 0;
       __threadfence();
+      // every block's errors were made visible before its count above
+      if (p.err_out) *p.err_out = *(volatile unsigned int*)&ctl->error;
     }
   }
 }

@@ -13,11 +13,13 @@ namespace fp {
 // fp_parse_f64_batch with explicit output ranges: buffer b writes entries
 // [out_base[b], out_base[b] + out_cap[b]) of out_f64 / out_status (ranges
 // of different buffers must not overlap) and its field count to
-// out_counts[b].
+// out_counts[b].  err_out (optional, a device address, e.g. of pinned host
+// memory) receives the stream's error word at the end of the call.
 fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32_t nbuf,
                             char delim, double* out_f64, uint8_t* out_status,
                             const uint64_t* out_base, const uint64_t* out_cap,
-                            uint64_t* out_counts, cudaStream_t stream);
+                            uint64_t* out_counts, cudaStream_t stream,
+                            unsigned int* err_out = nullptr);
 
 // Grow the scratch of (current device, stream) now, so that later calls of
 // up to `chunks` chunks and `nbuf` buffers allocate nothing.

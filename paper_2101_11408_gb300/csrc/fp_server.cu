@@ -101,7 +101,8 @@ struct Slot {
   uint64_t* d_counts = nullptr;  // max_batch field counts
   uint64_t* h_counts = nullptr;  // pinned copy
   unsigned int* d_err = nullptr; // the parse scratch's error word of this stream
-  unsigned int* h_err = nullptr; // pinned copy
+  unsigned int* h_err = nullptr; // pinned copy, written by the fallback kernel at the end of each launch
+  unsigned int* h_err_dv = nullptr;  // device view of h_err
   // piece tables in pinned host memory, read by the copy kernels
   fp::CopyPiece* gpieces = nullptr;   // written here ...
   fp::ScatterItem* sitems = nullptr;
@@ -188,8 +189,9 @@ bool retire(fp_server* S, Slot& sl) {
       fail_slot(S, sl, FP_ERR_CUDA);
       return true;
     }
-    if (*sl.h_err) {  // a bounded device wait ran out: the batch's results are void
-      const fp_err_t e = (fp_err_t)*sl.h_err;
+    const unsigned int derr = *(volatile unsigned int*)sl.h_err;
+    if (derr) {  // a bounded device wait ran out: the batch's results are void
+      const fp_err_t e = (fp_err_t)derr;
       *sl.h_err = 0;
       cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned int), sl.stream);
       fail_slot(S, sl, e);
@@ -258,11 +260,9 @@ bool launch_direct(fp_server* S, Slot& sl, Request* r) {
   *(volatile uint64_t*)&sl.h_counts[0] = ~0ull;
   if (fp::parse_batch_ranges(&text, &len, 1, S->cfg.delim,
                              reinterpret_cast<double*>(r->dv_f64), r->dv_status, &base, &cap,
-                             sl.h_counts_dv, sl.stream) != FP_OK)
+                             sl.h_counts_dv, sl.stream, sl.h_err_dv) != FP_OK)
     return false;
-  return cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
-                         sl.stream) == cudaSuccess &&
-         cudaEventRecord(sl.ev_counts, sl.stream) == cudaSuccess;
+  return cudaEventRecord(sl.ev_counts, sl.stream) == cudaSuccess;
 }
 
 // Launch step for one free slot.
@@ -349,15 +349,13 @@ void launch(fp_server* S, Slot& sl) {
   if (e == FP_OK)
     e = fp::parse_batch_ranges(sl.texts.data(), sl.lens.data(), (uint32_t)k, S->cfg.delim,
                                S->d_f64, S->d_status, sl.base.data(), sl.cap.data(), sl.d_counts,
-                               sl.stream);
+                               sl.stream, sl.h_err_dv);
   if (e == FP_OK &&
       fp::launch_scatter(sl.sitems_dv, sl.spieces_dv, ns, (int)std::min<uint32_t>(ns ? ns : 1, grid),
                          sl.stream) != cudaSuccess)
     e = FP_ERR_CUDA;
   if (e == FP_OK &&
       (cudaMemcpyAsync(sl.h_counts, sl.d_counts, k * sizeof(uint64_t), cudaMemcpyDeviceToHost,
-                       sl.stream) != cudaSuccess ||
-       cudaMemcpyAsync(sl.h_err, sl.d_err, sizeof(unsigned int), cudaMemcpyDeviceToHost,
                        sl.stream) != cudaSuccess ||
        cudaEventRecord(sl.ev_counts, sl.stream) != cudaSuccess))
     e = FP_ERR_CUDA;
@@ -507,6 +505,7 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
     sl.h_counts_dv = device_view(sl.h_counts);
     SRV_CUDA(cudaMallocHost(&sl.h_err, sizeof(unsigned int)));
     *sl.h_err = 0;
+    sl.h_err_dv = device_view(sl.h_err);
     // piece tables: every unit of a batch once, plus one partial piece per request
     sl.cap_gpieces = (uint32_t)(S->units / fp::GATHER_PIECE + cfg->max_batch + 1);
     sl.cap_spieces = (uint32_t)(S->units / fp::SCATTER_PIECE + cfg->max_batch + 1);
@@ -516,7 +515,7 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
     sl.gpieces_dv = device_view(sl.gpieces);
     sl.sitems_dv = device_view(sl.sitems);
     sl.spieces_dv = device_view(sl.spieces);
-    if (!sl.gpieces_dv || !sl.sitems_dv || !sl.spieces_dv) {
+    if (!sl.gpieces_dv || !sl.sitems_dv || !sl.spieces_dv || !sl.h_err_dv) {
       free_server(S);
       return FP_ERR_CUDA;
     }

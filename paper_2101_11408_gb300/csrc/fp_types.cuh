@@ -59,6 +59,11 @@ struct LaunchParams {
   // How long a device wait (look-back word, staging barrier) may spin before
   // it gives up with DERR_TIMEOUT; 0 means the default, WAIT_NS_DEFAULT.
   unsigned long long wait_ns;
+  // Optional (null: unused), e.g. pinned host memory through its device
+  // address: at the end of the call the fallback kernel's last block stores
+  // the stream's error word (Ctl::error) here, so that the host learns the
+  // call's outcome without a copy of its own.
+  unsigned int* err_out;
 };
 
 constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;  // 2 s
