@@ -292,7 +292,12 @@ FP_API fp_err_t fp_batch_plan_gather(fp_batch_plan *plan, double *dst_f64, uint8
  * host arrays; then the request's units are released.  The kernels reach
  * host memory directly when it is pinned (page-locked); requests of 1 MB
  * or more, and texts and arrays in pageable memory, are moved by copy
- * calls instead (results after their counts are back).  Different
+ * calls instead (results after their counts are back).  A request below
+ * 8 MB launched alone with pinned arrays is copied in and parsed straight
+ * into its host arrays (no gather or scatter).  A request of 32 MB or more
+ * launched alone with pinned text and arrays is cut at separators into
+ * segments (as fp_parse_f64_host cuts such a text) whose copies in, parses
+ * and copies out overlap, each segment one parse launch.  Different
  * slots' sequences overlap on the device.  Results equal those of
  * fp_parse_f64 on the same text, alone or in any mix.
  * Besides the arena, each slot's stream holds the parse scratch of up to
@@ -340,6 +345,7 @@ typedef struct {
   int64_t submit_ns, admit_ns, launch_ns, done_ns;
 } fp_request_info_t;
 typedef struct {
+  /* launches: parse launches (a segmented request counts one per segment) */
   uint64_t submitted, completed, launches, bytes, fields;
   uint64_t peak_units;     /* most arena units held at once */
   uint64_t peak_requests;  /* most requests admitted at once */

@@ -103,7 +103,7 @@ struct Scratch {
   unsigned long long cap_loc = 0;
   // the pipelined host parse: copy-in and copy-out streams, per-segment
   // events, segment counts
-  static constexpr int PIPE_SEGS = 64;
+  static constexpr int PIPE_SEGS = fp::PIPE_MAX_SEGS;
   cudaStream_t pipe_in = nullptr, pipe_out = nullptr;
   cudaEvent_t pipe_ev_in[PIPE_SEGS] = {}, pipe_ev_parsed[PIPE_SEGS] = {};
   cudaEvent_t pipe_ev_start = nullptr, pipe_ev_done = nullptr;
@@ -432,6 +432,55 @@ fp_err_t batch_impl(const char* const* texts, const size_t* lens, uint32_t nbuf,
 // Entry points for the library's own host runtime (fp_internal.h).
 namespace fp {
 
+// Segments of the pipelined path: at most this many bytes (each copy in and
+// each parse call has a fixed cost; 32 MB measured fastest on a 188 MB text,
+// 3% above 16 MB), and at least PIPE_MIN_SEGS of them so that copies in,
+// parses and copies out still overlap on texts near PIPE_MIN_BYTES.
+constexpr size_t PIPE_SEG_BYTES = 32u << 20;
+constexpr size_t PIPE_MIN_SEGS = 4;
+
+// Segment starts of the pipelined host parse, cuts[0] = 0 < cuts[1] < ... <
+// cuts[K] = len (returns K): each cut follows a separator near a target
+// position, so a segment's fields are exactly the text's fields in that
+// range.  Segments hold at most about PIPE_SEG_BYTES, there are at least
+// PIPE_MIN_SEGS of them, and on long texts the last three shrink to 1/2, 1/4
+// and 1/8 of a full one, so that little parse and copy work is left once the
+// last bytes have arrived.
+int plan_host_segments(const char* host_text, size_t len, char delim, size_t* cuts) {
+  const size_t S = PIPE_SEG_BYTES;
+  const size_t tail[3] = {S / 2, S / 4, S / 8};
+  size_t front = len;
+  int ntail = 0;
+  for (int j = 0; j < 3 && front >= 2 * S; j++) {
+    front -= tail[j];
+    ntail++;
+  }
+  size_t nf = (front + S - 1) / S;
+  if (nf + ntail < PIPE_MIN_SEGS) nf = PIPE_MIN_SEGS - ntail;
+  if (nf + ntail > (size_t)PIPE_MAX_SEGS) nf = PIPE_MAX_SEGS - ntail;
+  size_t targets[PIPE_MAX_SEGS];
+  size_t nt = 0;
+  for (size_t i = 1; i < nf; i++) targets[nt++] = i * (front / nf);
+  size_t at = front;
+  for (int j = 0; j < ntail; j++) {
+    targets[nt++] = at;
+    at += tail[j];
+  }
+  const unsigned char d = (unsigned char)delim;
+  int K = 0;
+  cuts[K++] = 0;
+  for (size_t t = 0; t < nt; t++) {
+    size_t c = targets[t];
+    if (c <= cuts[K - 1]) continue;
+    const size_t stop = c + (1u << 20) < len ? c + (1u << 20) : len;
+    while (c < stop && host_text[c - 1] != '\n' && (unsigned char)host_text[c - 1] != d) c++;
+    if (c < stop && c < len) cuts[K++] = c;  // else: no separator near, no cut here
+  }
+  cuts[K] = len;
+  return K;
+}
+
+
 fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32_t nbuf,
                             char delim, double* out_f64, uint8_t* out_status,
                             const uint64_t* out_base, const uint64_t* out_cap,
@@ -478,17 +527,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // host-buffer parse
 // ---------------------------------------------------------------------------
-constexpr size_t PIPE_MIN_BYTES = 32u << 20;  // smaller texts take the simple path
 // Below this many bytes the simple path lets the parse kernel write the
 // results into pinned host arrays directly (no count round trip, no copy
 // calls); larger result sets move faster by copy engine.
 constexpr size_t DIRECT_MAX_BYTES = 8u << 20;
-// Segments of the pipelined path: at most this many bytes (each copy in and
-// each parse call has a fixed cost; 32 MB measured fastest on a 188 MB text,
-// 3% above 16 MB), and at least PIPE_MIN_SEGS of them so that copies in,
-// parses and copies out still overlap on texts near PIPE_MIN_BYTES.
-constexpr size_t PIPE_SEG_BYTES = 32u << 20;
-constexpr size_t PIPE_MIN_SEGS = 4;
 
 // The address the device uses for host memory p, or null when p is not
 // pinned (page-locked) memory.
@@ -624,49 +666,8 @@ fp_err_t host_simple(const char* host_text, size_t len, char delim, double* host
   return FP_OK;
 }
 
-// Segment starts of the pipelined host parse, cuts[0] = 0 < cuts[1] < ... <
-// cuts[K] = len (returns K): each cut follows a separator near a target
-// position, so a segment's fields are exactly the text's fields in that
-// range.  Segments hold at most about PIPE_SEG_BYTES, there are at least
-// PIPE_MIN_SEGS of them, and on long texts the last three shrink to 1/2, 1/4
-// and 1/8 of a full one, so that little parse and copy work is left once the
-// last bytes have arrived.
-int plan_segments(const char* host_text, size_t len, char delim, size_t* cuts) {
-  const size_t S = PIPE_SEG_BYTES;
-  const size_t tail[3] = {S / 2, S / 4, S / 8};
-  size_t front = len;
-  int ntail = 0;
-  for (int j = 0; j < 3 && front >= 2 * S; j++) {
-    front -= tail[j];
-    ntail++;
-  }
-  size_t nf = (front + S - 1) / S;
-  if (nf + ntail < PIPE_MIN_SEGS) nf = PIPE_MIN_SEGS - ntail;
-  if (nf + ntail > (size_t)Scratch::PIPE_SEGS) nf = Scratch::PIPE_SEGS - ntail;
-  size_t targets[Scratch::PIPE_SEGS];
-  size_t nt = 0;
-  for (size_t i = 1; i < nf; i++) targets[nt++] = i * (front / nf);
-  size_t at = front;
-  for (int j = 0; j < ntail; j++) {
-    targets[nt++] = at;
-    at += tail[j];
-  }
-  const unsigned char d = (unsigned char)delim;
-  int K = 0;
-  cuts[K++] = 0;
-  for (size_t t = 0; t < nt; t++) {
-    size_t c = targets[t];
-    if (c <= cuts[K - 1]) continue;
-    const size_t stop = c + (1u << 20) < len ? c + (1u << 20) : len;
-    while (c < stop && host_text[c - 1] != '\n' && (unsigned char)host_text[c - 1] != d) c++;
-    if (c < stop && c < len) cuts[K++] = c;  // else: no separator near, no cut here
-  }
-  cuts[K] = len;
-  return K;
-}
-
 // Pinned host memory: the text is cut at separators into segments
-// (plan_segments).  All segments are copied in on
+// (fp::plan_host_segments).  All segments are copied in on
 // pipe_in, back to back; segment i is parsed on the caller's stream once it
 // has landed, and the parse kernel writes its field count straight into
 // pinned host memory (no copy call queues behind the result copies); this
@@ -681,7 +682,7 @@ int plan_segments(const char* host_text, size_t len, char delim, size_t* cuts) {
 fp_err_t host_pipelined(const char* host_text, size_t len, char delim, double* host_f64,
                         uint8_t* host_status, uint64_t* host_count, cudaStream_t stream) {
   size_t cuts[Scratch::PIPE_SEGS + 1];
-  const int K = plan_segments(host_text, len, delim, cuts);
+  const int K = fp::plan_host_segments(host_text, len, delim, cuts);
   Scratch* s = nullptr;
   Config cfg;
   {
@@ -1007,7 +1008,7 @@ fp_err_t fp_parse_f64_host(const char* host_text, size_t len, char delim, double
   if (len >= MAX_LEN || !host_count) return FP_ERR_ARG;
   if (len > 0 && (!host_text || !host_f64 || !host_status)) return FP_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  if (len >= PIPE_MIN_BYTES) {
+  if (len >= fp::PIPE_MIN_BYTES) {
     const void* dv_text = device_view(host_text);
     void* dv_f64 = device_view(host_f64);
     void* dv_st = device_view(host_status);

@@ -21,6 +21,18 @@ fp_err_t parse_batch_ranges(const char* const* texts, const size_t* lens, uint32
                             uint64_t* out_counts, cudaStream_t stream,
                             unsigned int* err_out = nullptr);
 
+// The pipelined host parse's segments: at most this many per text.
+constexpr int PIPE_MAX_SEGS = 64;
+// Texts of at least this many bytes in pinned memory are parsed in segments
+// whose copies in, parses and copies out overlap.
+constexpr size_t PIPE_MIN_BYTES = 32u << 20;
+
+// Segment starts of a host text, cuts[0] = 0 < cuts[1] < ... < cuts[K] = len
+// (returns K <= PIPE_MAX_SEGS; cuts has room for PIPE_MAX_SEGS + 1): each
+// cut follows a separator ('\n' or delim), so a segment's fields are
+// exactly the text's fields in that range.
+int plan_host_segments(const char* host_text, size_t len, char delim, size_t* cuts);
+
 // Grow the scratch of (current device, stream) now, so that later calls of
 // up to `chunks` chunks and `nbuf` buffers allocate nothing.
 fp_err_t reserve_stream_scratch(cudaStream_t stream, unsigned long long chunks, uint32_t nbuf);

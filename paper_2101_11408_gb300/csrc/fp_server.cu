@@ -93,7 +93,7 @@ T* device_view(T* p) {
   return static_cast<T*>(a.devicePointer);
 }
 
-enum class Phase { FREE, PARSING, COPYING };
+enum class Phase { FREE, PARSING, PIPELINED, COPYING };
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -114,6 +114,13 @@ struct Slot {
   bool unmapped_out = false;     // some request's results go back by copy calls
   bool direct = false;           // one request, results and count written to host memory by the parse
   uint64_t* h_counts_dv = nullptr;  // device view of h_counts
+  // one large request in segments (Phase::PIPELINED): copies in on s_in,
+  // parses on `stream`, copies out on s_out, segment i's count in h_counts[i]
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[fp::PIPE_MAX_SEGS] = {}, ev_parsed[fp::PIPE_MAX_SEGS] = {};
+  size_t cuts[fp::PIPE_MAX_SEGS + 1] = {};
+  int nseg = 0, next_seg = 0;  // segments, and the first whose results are not yet queued
+  uint64_t seg_total = 0;      // fields of the segments before next_seg
   Phase phase = Phase::FREE;
   std::vector<Request*> reqs;
   std::vector<const char*> texts;
@@ -174,6 +181,8 @@ void fail_slot(fp_server* S, Slot& sl, fp_err_t err) {
   // callers' host arrays, kernels writing arena units) ends before the
   // requests complete and their units return to the arena.
   cudaStreamSynchronize(sl.stream);
+  cudaStreamSynchronize(sl.s_in);
+  cudaStreamSynchronize(sl.s_out);
   cudaGetLastError();  // the failure is reported through the requests
   for (Request* r : sl.reqs) finish(S, r, err);
   sl.reqs.clear();
@@ -228,6 +237,53 @@ bool retire(fp_server* S, Slot& sl) {
     sl.phase = Phase::COPYING;
     return true;
   }
+  if (sl.phase == Phase::PIPELINED) {
+    // segments in order: once one is parsed, its results go to the caller's
+    // arrays at the running field total
+    Request* r = sl.reqs[0];
+    bool moved = false;
+    while (sl.next_seg < sl.nseg) {
+      const int i = sl.next_seg;
+      const cudaError_t q = cudaEventQuery(sl.ev_parsed[i]);
+      if (q == cudaErrorNotReady) return moved;
+      if (q != cudaSuccess) {
+        fail_slot(S, sl, FP_ERR_CUDA);
+        return true;
+      }
+      const unsigned int derr = *(volatile unsigned int*)sl.h_err;
+      if (derr) {  // a bounded device wait ran out: the request's results are void
+        *sl.h_err = 0;
+        cudaMemsetAsync(sl.d_err, 0, sizeof(unsigned int), sl.stream);
+        fail_slot(S, sl, (fp_err_t)derr);
+        return true;
+      }
+      const uint64_t count = *(volatile uint64_t*)&sl.h_counts[i];
+      if (count > sl.cuts[i + 1] - sl.cuts[i]) {  // at most one field per byte
+        fail_slot(S, sl, FP_ERR_INTERNAL);
+        return true;
+      }
+      const uint64_t room = r->out_cap > sl.seg_total ? r->out_cap - sl.seg_total : 0;
+      const uint64_t n = std::min<uint64_t>(count, room);
+      const uint64_t src = r->off + sl.cuts[i];
+      if (n && (cudaMemcpyAsync(r->h_f64 + sl.seg_total, S->d_f64 + src, n * sizeof(double),
+                                cudaMemcpyDeviceToHost, sl.s_out) != cudaSuccess ||
+                cudaMemcpyAsync(r->h_status + sl.seg_total, S->d_status + src, n,
+                                cudaMemcpyDeviceToHost, sl.s_out) != cudaSuccess)) {
+        fail_slot(S, sl, FP_ERR_CUDA);
+        return true;
+      }
+      sl.seg_total += count;
+      sl.next_seg++;
+      moved = true;
+    }
+    r->info.count = sl.seg_total;
+    if (cudaEventRecord(sl.ev_done, sl.s_out) != cudaSuccess) {
+      fail_slot(S, sl, FP_ERR_CUDA);
+      return true;
+    }
+    sl.phase = Phase::COPYING;
+    return true;
+  }
   if (sl.phase == Phase::COPYING) {
     const cudaError_t q = cudaEventQuery(sl.ev_done);
     if (q == cudaErrorNotReady) return false;
@@ -265,6 +321,38 @@ bool launch_direct(fp_server* S, Slot& sl, Request* r) {
   return cudaEventRecord(sl.ev_counts, sl.stream) == cudaSuccess;
 }
 
+// One large request alone, with pinned host arrays: its text is cut at
+// separators into segments (as fp_parse_f64_host cuts a large pinned text),
+// copied into its arena range on s_in back to back; segment i is parsed on
+// the slot's stream once it has landed, into the request's arena slots from
+// its own byte offset on, its count going to pinned memory; the retire step
+// then queues each segment's results on s_out at the running total.  Copies
+// in, parses and copies out of different segments overlap.
+bool launch_pipelined(fp_server* S, Slot& sl, Request* r) {
+  sl.nseg = fp::plan_host_segments(r->h_text, r->len, S->cfg.delim, sl.cuts);
+  sl.next_seg = 0;
+  sl.seg_total = 0;
+  uint8_t* dst = reinterpret_cast<uint8_t*>(S->d_text) + r->text_off;
+  for (int i = 0; i < sl.nseg; i++) {
+    if (cudaMemcpyAsync(dst + sl.cuts[i], r->h_text + sl.cuts[i], sl.cuts[i + 1] - sl.cuts[i],
+                        cudaMemcpyHostToDevice, sl.s_in) != cudaSuccess ||
+        cudaEventRecord(sl.ev_in[i], sl.s_in) != cudaSuccess)
+      return false;
+  }
+  for (int i = 0; i < sl.nseg; i++) {
+    const char* text = reinterpret_cast<const char*>(dst + sl.cuts[i]);
+    const size_t len = sl.cuts[i + 1] - sl.cuts[i];
+    const uint64_t base = r->off + sl.cuts[i], cap = len;  // at most one field per byte
+    *(volatile uint64_t*)&sl.h_counts[i] = ~0ull;
+    if (cudaStreamWaitEvent(sl.stream, sl.ev_in[i], 0) != cudaSuccess ||
+        fp::parse_batch_ranges(&text, &len, 1, S->cfg.delim, S->d_f64, S->d_status, &base, &cap,
+                               sl.h_counts_dv + i, sl.stream, sl.h_err_dv) != FP_OK ||
+        cudaEventRecord(sl.ev_parsed[i], sl.stream) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+
 // Launch step for one free slot.
 void launch(fp_server* S, Slot& sl) {
   const size_t kmax = std::min<size_t>(S->admitted.size(), S->cfg.max_batch);
@@ -289,6 +377,19 @@ void launch(fp_server* S, Slot& sl) {
       sl.phase = Phase::PARSING;
       std::lock_guard<std::mutex> lk(S->mu);
       S->st.launches++;
+      S->st.max_batch_seen = std::max<uint64_t>(S->st.max_batch_seen, 1);
+      return;
+    }
+    if (r->len >= fp::PIPE_MIN_BYTES && r->dv_text && r->dv_f64 && r->dv_status) {
+      if (!launch_pipelined(S, sl, r)) {
+        fail_slot(S, sl, FP_ERR_CUDA);
+        return;
+      }
+      r->info.launch_ns = now_ns();
+      r->info.batch_size = 1;
+      sl.phase = Phase::PIPELINED;
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->st.launches += (uint64_t)sl.nseg;
       S->st.max_batch_seen = std::max<uint64_t>(S->st.max_batch_seen, 1);
       return;
     }
@@ -444,6 +545,16 @@ void free_server(fp_server* S) {
       fp::release_stream_scratch(sl.stream);
       cudaStreamDestroy(sl.stream);
     }
+    for (cudaStream_t x : {sl.s_in, sl.s_out}) {
+      if (x) {
+        cudaStreamSynchronize(x);
+        cudaStreamDestroy(x);
+      }
+    }
+    for (int i = 0; i < fp::PIPE_MAX_SEGS; i++) {
+      if (sl.ev_in[i]) cudaEventDestroy(sl.ev_in[i]);
+      if (sl.ev_parsed[i]) cudaEventDestroy(sl.ev_parsed[i]);
+    }
     if (sl.ev_counts) cudaEventDestroy(sl.ev_counts);
     if (sl.ev_done) cudaEventDestroy(sl.ev_done);
     cudaFree(sl.d_counts);
@@ -501,7 +612,14 @@ extern "C" fp_err_t fp_server_create(const fp_server_config_t* cfg, fp_server** 
     SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_counts, cudaEventDisableTiming));
     SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_done, cudaEventDisableTiming));
     SRV_CUDA(cudaMalloc(&sl.d_counts, cfg->max_batch * sizeof(uint64_t)));
-    SRV_CUDA(cudaMallocHost(&sl.h_counts, cfg->max_batch * sizeof(uint64_t)));
+    SRV_CUDA(cudaMallocHost(&sl.h_counts, std::max<uint32_t>(cfg->max_batch, fp::PIPE_MAX_SEGS) *
+                                              sizeof(uint64_t)));
+    SRV_CUDA(cudaStreamCreateWithFlags(&sl.s_in, cudaStreamNonBlocking));
+    SRV_CUDA(cudaStreamCreateWithFlags(&sl.s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < fp::PIPE_MAX_SEGS; i++) {
+      SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_in[i], cudaEventDisableTiming));
+      SRV_CUDA(cudaEventCreateWithFlags(&sl.ev_parsed[i], cudaEventDisableTiming));
+    }
     sl.h_counts_dv = device_view(sl.h_counts);
     SRV_CUDA(cudaMallocHost(&sl.h_err, sizeof(unsigned int)));
     *sl.h_err = 0;

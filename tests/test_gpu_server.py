@@ -203,3 +203,38 @@ def test_pageable_host_memory_takes_the_copy_path(texts, ref):
             k = info["count"]
             got.append((hv[:k].numpy().view(np.uint64).copy(), hs[:k].numpy().copy(), info))
     assert_same(ref[:60], got)
+
+
+def test_large_requests_in_overlapping_segments():
+    """Requests of 32 MB and more with pinned host arrays launch alone and
+    are parsed in segments cut at separators, whose copies in, parses and
+    copies out overlap: results equal the oracle's (hard cases at both ends
+    of a segmented request included) while small requests are served beside
+    them; a segmented request whose result array is shorter than its field
+    count gets the full count and exactly the first out_cap results."""
+    pool = workloads.csv_pool()
+    hard_a = workloads.hard_case_text(2000, 143).replace(b"\n", b",")
+    hard_b = workloads.hard_case_text(2000, 145).replace(b"\n", b",")
+    big = [hard_a + b"\n" + workloads.csv_request(90 << 20, 144, pool) + b"\n" + hard_b,
+           workloads.csv_request(40 << 20, 146, pool)]
+    small = [workloads.csv_request(200_000, 147 + i, pool) for i in range(6)]
+    texts = [big[0], small[0], small[1], big[1]] + small[2:]
+    with fp.Server(device_budget=8_000_000_000, max_batch=64, max_inflight=4, delim=b",") as srv:
+        got = serve(texts, srv)
+        st = srv.stats()
+    for i, (t, (gv, gs, info)) in enumerate(zip(texts, got)):
+        rb, rs = oracle.parse_buffer(t, b",")
+        assert gv.size == rb.size, i
+        assert np.array_equal(gv, rb) and np.array_equal(gs, rs), i
+    # 5 + 4 segment launches for the two large requests, at least one for the rest
+    assert st["launches"] >= 10, st
+    t = big[1]
+    rb, rs = oracle.parse_buffer(t, b",")
+    cap = rb.size // 2 + 3
+    ht, hv, hs = host_arrays(t)
+    with fp.Server(device_budget=2_000_000_000, max_batch=4, max_inflight=2, delim=b",") as srv:
+        info = srv.wait(srv.submit(ht, hv[:cap], hs[:cap]), timeout_s=120)
+    assert info["error"] == 0 and info["count"] == rb.size
+    assert np.array_equal(hv[:cap].numpy().view(np.uint64), rb[:cap])
+    assert np.array_equal(hs[:cap].numpy(), rs[:cap])
+    assert (hv[cap:] == -5.0).all() and (hs[cap:].numpy() == 0xEE).all()
