@@ -587,42 +587,45 @@ FP_HD uint32_t nondigit_exact(uint32_t x) {
   return ((t + 0x76767676u) | x) & 0x80808080u;
 }
 
-// Shared-memory tables of the window tokenizer (1,672 bytes), so that the
+// Shared-memory tables of the window tokenizer (1,664 bytes), so that the
 // per-field byte moves are table lookups instead of computed masks:
-//   sel[d][j]        byte-permute selector of window word j that moves the
+//   sel[j][d]        byte-permute selector of window word j that moves the
 //                    bytes at or before window position d (a point) one place
 //                    toward the end, over the point (d = 24: no point, the
 //                    identity);
-//   keep_from[l][j]  mask of the bytes of word j at window positions >= l;
-//   keep_below[m-16] masks of words 4 and 5 for the positions below m (an
-//                    exponent marker at m >= 16).
+//   keep_from[j][l]  mask of the bytes of word j at window positions >= l;
+//   keep_below[j-4][m-16]  masks of words 4 and 5 for the positions below m
+//                    (an exponent marker at m >= 16).
+// The position is the inner index and rows are 32 words, so the lanes of a
+// warp, each looking up its own field's position in the same row, read 32
+// different banks (no shared-memory bank conflicts).
 struct WindowTables {
-  uint32_t sel[25][8];
-  uint32_t keep_from[25][8];
-  uint32_t keep_below[9][2];
+  uint32_t sel[6][32];
+  uint32_t keep_from[6][32];
+  uint32_t keep_below[2][16];
 };
 constexpr int WINDOW_TABLE_WORDS = (int)(sizeof(WindowTables) / 4);
 
 // Word i of the tables (in the struct's order).
 FP_HD uint32_t window_table_word(int i) {
-  if (i < 25 * 8) {  // sel
-    const int d = i >> 3, j = i & 7;
-    if (j >= 6 || d == 24) return 0x7654u;
+  if (i < 6 * 32) {  // sel[j][d]
+    const int j = i >> 5, d = i & 31;
+    if (d >= 24) return 0x7654u;
     int c = d + 1 - 4 * j;  // bytes of word j at or before the point
     c = c < 0 ? 0 : (c > 4 ? 4 : c);
     const uint32_t m = 0xFFFFu >> (16 - 4 * c);
     return (0x6543u & m) | (0x7654u & ~m & 0xFFFFu);
   }
-  i -= 25 * 8;
-  if (i < 25 * 8) {  // keep_from
-    const int l = i >> 3, j = i & 7;
+  i -= 6 * 32;
+  if (i < 6 * 32) {  // keep_from[j][l]
+    const int j = i >> 5, l = i & 31;
     uint32_t m = 0;
     for (int b = 0; b < 4; b++)
       if (4 * j + b >= l) m |= 0xFFu << (8 * b);
-    return j < 6 ? m : 0;
+    return m;
   }
-  i -= 25 * 8;
-  const int mk = 16 + (i >> 1), j = 4 + (i & 1);  // keep_below
+  i -= 6 * 32;
+  const int j = 4 + (i >> 4), mk = 16 + (i & 15);  // keep_below[j-4][mk-16]
   uint32_t m = 0;
   for (int b = 0; b < 4; b++)
     if (4 * j + b < mk) m |= 0xFFu << (8 * b);
@@ -698,21 +701,18 @@ FP_HD bool parse_window(const uint8_t* tile, const WindowTables& wt, int s, int 
   const int lo = tsig + hp;  // the first digit's position once the point is gone
   if (em - lo < 1) return false;  // no digit at all
   {
-    const uint32_t* sel = wt.sel[dpos];
     uint32_t prev = 0x30303030u;
 #pragma unroll
     for (int j = 0; j < 6; j++) {
       const uint32_t xj = x[j];
-      x[j] = byte_perm(prev, xj, sel[j]);
+      x[j] = byte_perm(prev, xj, wt.sel[j][dpos]);
       prev = xj;
     }
-    const uint32_t* kf = wt.keep_from[lo];
-    const uint32_t* kb = wt.keep_below[em - 16];
     uint32_t k[6];
 #pragma unroll
-    for (int j = 0; j < 6; j++) k[j] = kf[j];
-    k[4] &= kb[0];
-    k[5] &= kb[1];
+    for (int j = 0; j < 6; j++) k[j] = wt.keep_from[j][lo];
+    k[4] &= wt.keep_below[0][em - 16];
+    k[5] &= wt.keep_below[1][em - 16];
 #pragma unroll
     for (int j = 0; j < 6; j++) x[j] = (x[j] & k[j]) | (0x30303030u & ~k[j]);
   }

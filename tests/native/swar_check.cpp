@@ -82,7 +82,7 @@ int main() {
       for (int j = 0; j < 6; j++) {
         uint32_t xj = 0;
         for (int b = 0; b < 4; b++) xj |= (uint32_t)win[4 * j + b] << (8 * b);
-        const uint32_t r = byte_perm(prev, xj, wt.sel[d][j]);
+        const uint32_t r = byte_perm(prev, xj, wt.sel[j][d]);
         prev = xj;
         for (int b = 0; b < 4; b++) {
           const int p = 4 * j + b;
@@ -93,12 +93,12 @@ int main() {
     }
     for (int l = 0; l <= 24; l++)
       for (int p = 0; p < 24; p++)
-        if ((byte_of(wt.keep_from[l][p / 4], p % 4) == 0xFF) != (p >= l) ||
-            (byte_of(wt.keep_from[l][p / 4], p % 4) != 0 && byte_of(wt.keep_from[l][p / 4], p % 4) != 0xFF))
+        if ((byte_of(wt.keep_from[p / 4][l], p % 4) == 0xFF) != (p >= l) ||
+            (byte_of(wt.keep_from[p / 4][l], p % 4) != 0 && byte_of(wt.keep_from[p / 4][l], p % 4) != 0xFF))
           return fail("window keep_from", (uint32_t)l, (uint32_t)p);
     for (int m = 16; m <= 24; m++)
       for (int p = 16; p < 24; p++) {
-        const uint8_t k = byte_of(wt.keep_below[m - 16][(p - 16) / 4], p % 4);
+        const uint8_t k = byte_of(wt.keep_below[(p - 16) / 4][m - 16], p % 4);
         if ((k == 0xFF) != (p < m) || (k != 0 && k != 0xFF))
           return fail("window keep_below", (uint32_t)m, (uint32_t)p);
       }
