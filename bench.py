@@ -312,14 +312,15 @@ def run_ours(args, world, rank, dist) -> None:
     cnt = torch.zeros(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # one untimed parse, checked against the oracle on a prefix
+    # one untimed parse, checked against the oracle (the whole text, up to
+    # --check-mb MB of whole lines)
     parse_into(d_text, out, st, cnt, stream=stream)
     torch.cuda.synchronize()
     N = int(cnt.item())
     check_fields = 0
     if rank == 0 and not args.skip_check:
         import oracle
-        prefix = cut_at_line(text, 4 << 20)
+        prefix = cut_at_line(text, args.check_mb << 20)
         rb, rs = oracle.parse_buffer(prefix, f32=f32)
         got = out[:rb.size].cpu().numpy().view(np.uint32 if f32 else np.uint64)
         gst = st[:rb.size].cpu().numpy()
@@ -510,14 +511,15 @@ def run_ext(args, world, rank, dist) -> None:
     def call():
         fp.parse_ex_into(d_text, out, st, cnt, delim, grammar, columns, rows_cap, stream)
 
-    # one untimed call, checked against the oracle on a prefix of whole lines
+    # one untimed call, checked against the oracle (whole lines, up to
+    # --check-mb MB)
     call()
     torch.cuda.synchronize()
     N = int(cnt.item())
     check_fields = 0
     if rank == 0 and not args.skip_check:
         import oracle
-        prefix = cut_at_line(text, 4 << 20)
+        prefix = cut_at_line(text, args.check_mb << 20)
         rb, rs = oracle.parse_buffer(prefix, delim, grammar=gid)
         k = rb.size
         if columns:
@@ -1028,6 +1030,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--skip-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--check-mb", type=int, default=512,
+                    help="text checked against the oracle before timing (MB of whole lines)")
     ap.add_argument("--no-extras", action="store_true",
                     help="bulk: leave out the hard-case, batched and served sections")
     ap.add_argument("--workload", choices=["bulk", "uniform", "hard", "batch", "serve", "json",
