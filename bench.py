@@ -730,28 +730,66 @@ def run_batch(args, world, rank, dist) -> None:
     ms_per = _time_steps(torch, stream, per_buffer, few, 3)
     wall_per = (time.perf_counter() - t0) / (few + 3) * 1e3
 
-    # end to end: packed host text -> device, graph replay, the results
-    # packed in buffer order on the device (fp_batch_plan_gather), their
-    # total and then exactly that many results -> host, every step
+    # end to end, host to host, every step: the buffers in G groups of about
+    # equal bytes, one graph-replayed plan per group.  Group g's packed text
+    # goes to the device on a copy stream; its plan runs once those bytes
+    # have landed and packs its results in buffer order on the device
+    # (fp_batch_plan_gather); its total comes back, and exactly that many
+    # results go to the host arrays at the running total on a third stream.
+    # Copies in, parses and copies out of different groups overlap.
     e2e = None
     if not args.skip_e2e:
+        G = max(1, min(args.e2e_groups, len(texts)))
+        bounds, acc, target = [0], 0, B / G
+        for b in range(len(texts)):
+            acc += lens[b]
+            if acc >= target * len(bounds) and len(bounds) < G and b + 1 < len(texts):
+                bounds.append(b + 1)
+        bounds.append(len(texts))
+        G = len(bounds) - 1
+        plans_e = [fp.BatchPlan(views[a:z], out, st, offs[a:z + 1], cnt[a:z], graph=True)
+                   for a, z in zip(bounds, bounds[1:])]
+        text_rng = [(starts[a], starts[z - 1] + lens[z - 1]) for a, z in zip(bounds, bounds[1:])]
         h_out = torch.empty(N, dtype=torch.float64).pin_memory()
         h_st = torch.empty(N, dtype=torch.uint8).pin_memory()
-        d_pv = torch.empty(max(N, 1), dtype=torch.float64, device=dev)
-        d_ps = torch.empty(max(N, 1), dtype=torch.uint8, device=dev)
-        d_tot = torch.empty(1, dtype=torch.int64, device=dev)
-        h_tot = torch.empty(1, dtype=torch.int64).pin_memory()
+        d_pv = torch.empty(cap, dtype=torch.float64, device=dev)
+        d_ps = torch.empty(cap, dtype=torch.uint8, device=dev)
+        d_tot = torch.empty(G, dtype=torch.int64, device=dev)
+        h_tot = torch.empty(G, dtype=torch.int64).pin_memory()
+        s_in = torch.cuda.Stream(dev)
+        s_out = torch.cuda.Stream(dev)
 
         def e2e_step():
-            d_packed.copy_(h_packed, non_blocking=True)
-            plan_g.launch(stream)
-            plan_g.gather(d_pv, d_ps, d_tot, stream)
-            h_tot.copy_(d_tot, non_blocking=True)
-            stream.synchronize()
-            n = int(h_tot[0])
-            h_out[:n].copy_(d_pv[:n], non_blocking=True)
-            h_st[:n].copy_(d_ps[:n], non_blocking=True)
-            stream.synchronize()
+            start = torch.cuda.Event()
+            start.record(stream)
+            s_in.wait_event(start)
+            s_out.wait_event(start)
+            landed, packed_ev = [], []
+            with torch.cuda.stream(s_in):  # all groups' text in, back to back
+                for x0, x1 in text_rng:
+                    d_packed[x0:x1].copy_(h_packed[x0:x1], non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(s_in)
+                    landed.append(ev)
+            for g, (a, z) in enumerate(zip(bounds, bounds[1:])):
+                stream.wait_event(landed[g])
+                plans_e[g].launch(stream)
+                plans_e[g].gather(d_pv[offs[a]:], d_ps[offs[a]:], d_tot[g:g + 1], stream)
+                with torch.cuda.stream(stream):
+                    h_tot[g:g + 1].copy_(d_tot[g:g + 1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                packed_ev.append(ev)
+            n = 0
+            for g, (a, z) in enumerate(zip(bounds, bounds[1:])):
+                packed_ev[g].synchronize()
+                k = int(h_tot[g])
+                s_out.wait_event(packed_ev[g])
+                with torch.cuda.stream(s_out):
+                    h_out[n:n + k].copy_(d_pv[offs[a]:offs[a] + k], non_blocking=True)
+                    h_st[n:n + k].copy_(d_ps[offs[a]:offs[a] + k], non_blocking=True)
+                n += k
+            s_out.synchronize()
             return n
 
         for _ in range(3):
@@ -761,15 +799,22 @@ def run_batch(args, world, rank, dist) -> None:
         for _ in range(steps):
             n_e2e = e2e_step()
         dt = (time.perf_counter() - t0) / steps
-        # the packed results are the buffers' results one after the other
-        packed_ref = torch.cat([out[offs[b]:offs[b] + counts[b]] for b in range(len(texts))])
-        if n_e2e != N or not torch.equal(d_pv[:N].view(torch.int64), packed_ref.view(torch.int64)):
-            raise SystemExit("bench: packed batch results differ from the per-buffer ones")
-        e2e = {"value": world * B / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(packed.size),
-               "d2h_bytes_per_step": 9 * N + 8, "steps": steps,
-               "api": "one host->device copy of the packed buffers, fp_batch_plan_launch (graph), "
-                      "fp_batch_plan_gather (results packed in buffer order on the device), then "
-                      "one copy of the total and two of exactly that many results"}
+        # the host results are the buffers' results one after the other
+        packed_ref = torch.cat([out1[offs[b]:offs[b] + counts[b]] for b in range(len(texts))])
+        packed_st = torch.cat([st1[offs[b]:offs[b] + counts[b]] for b in range(len(texts))])
+        if n_e2e != N or not (torch.equal(h_out.view(torch.int64), packed_ref.view(torch.int64).cpu())
+                              and torch.equal(h_st, packed_st.cpu())):
+            raise SystemExit("bench: host batch results differ from the per-buffer ones")
+        for pl in plans_e:
+            pl.close()
+        e2e = {"value": world * B / dt / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(x1 - x0 for x0, x1 in text_rng)),
+               "d2h_bytes_per_step": 9 * N + 8 * G, "steps": steps, "groups": G,
+               "api": "per group of buffers (about equal bytes): one host->device copy of its "
+                      "packed text, fp_batch_plan_launch (graph) and fp_batch_plan_gather once "
+                      "it has landed, a copy of its total, then two copies of exactly that many "
+                      "results to the host at the running total; copies in, parses and copies "
+                      "out of different groups overlap"}
     if rank != 0:
         return
     peak, peak_kind = measured_hbm_peak()
@@ -1051,6 +1096,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--format", choices=["f64", "f32"], default="f64",
                     help="bulk/uniform/hard: binary64 (fp_parse_f64) or binary32 (fp_parse_f32)")
     ap.add_argument("--nbuf", type=int, default=4096, help="batch: buffers")
+    ap.add_argument("--e2e-groups", type=int, default=8,
+                    help="batch: buffer groups of the end-to-end pipeline")
     ap.add_argument("--batch-bytes", type=int, default=2 << 30, help="batch: total text bytes")
     return ap
 
