@@ -42,7 +42,9 @@ struct uint4 {
 namespace emu {
 constexpr int BT = 256, MAXB = 4, NT = BT * MAXB, NW = NT / 32;
 int nthreads = BT, nblocks = 1;
-enum State { RUN, WAIT_WARP, WAIT_BLOCK, DONE };
+// SPIN: a lane in a bounded wait (it slept); it runs again once no other
+// thread can, so that the other blocks publish what it waits for
+enum State { RUN, WAIT_WARP, WAIT_BLOCK, DONE, SPIN };
 ucontext_t sched, th[NT];
 int cur = 0;
 State st[NT];
@@ -71,7 +73,7 @@ inline emu_dim emu_bid() { return emu_dim{(unsigned)(emu::cur / emu::BT), 0, 0};
 #define blockIdx (emu_bid())
 #define gridDim (emu_dim{(unsigned)emu::nblocks, 1, 1})
 
-enum { K_BALLOT = 1, K_ANY, K_ALL, K_SHFL, K_UP, K_XOR, K_RADD, K_RMIN };
+enum { K_BALLOT = 1, K_ANY, K_ALL, K_SHFL, K_UP, K_XOR, K_RADD, K_RMIN, K_SYNC };
 template <class T>
 uint64_t to_u(T v) {
   uint64_t u = 0;
@@ -128,11 +130,15 @@ unsigned int __reduce_min_sync(unsigned int, unsigned int v) {
   for (int i = 0; i < 32; i++) t = (unsigned int)s[i] < t ? (unsigned int)s[i] : t;
   return t;
 }
+void __syncwarp(unsigned int = 0xFFFFFFFFu) { emu::post(0, K_SYNC); }
 void __syncthreads() {
   emu::st[emu::cur] = emu::WAIT_BLOCK;
   emu::yield();
 }
-void __nanosleep(unsigned int) { emu::yield(); }  // let the others run
+void __nanosleep(unsigned int) {  // let the others run first
+  emu::st[emu::cur] = emu::SPIN;
+  emu::yield();
+}
 void __threadfence() {}
 int __popc(unsigned int x) { return __builtin_popcount(x); }
 int __popcll(unsigned long long x) { return __builtin_popcountll(x); }
@@ -227,10 +233,10 @@ bool run_block() {
       ran = true;
     }
     if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(EMU_LIMIT_S)) {
-      int n[4] = {0, 0, 0, 0};
+      int n[5] = {0, 0, 0, 0, 0};
       for (int t = 0; t < NTH; t++) n[emu::st[t]]++;
-      std::fprintf(stderr, "states: run %d warp %d block %d done %d; running warps:", n[0], n[1],
-                   n[2], n[3]);
+      std::fprintf(stderr, "states: run %d warp %d block %d done %d spin %d; running warps:", n[0],
+                   n[1], n[2], n[3], n[4]);
       for (int t = 0; t < NTH; t += 32)
         if (emu::st[t] == emu::RUN) std::fprintf(stderr, " %d", t / 32);
       std::fprintf(stderr, "\n");
@@ -275,6 +281,13 @@ bool run_block() {
     }
     if (released) continue;
     if (nd_all == NTH) return true;
+    bool spinning = false;
+    for (int t = 0; t < NTH; t++)
+      if (emu::st[t] == emu::SPIN) {
+        emu::st[t] = emu::RUN;
+        spinning = true;
+      }
+    if (spinning) continue;  // (a wait that nothing ends runs out on the timer)
     emu::why = "deadlock";
     return false;
   }
