@@ -45,6 +45,9 @@ HARD_WORKLOAD = ("hard cases, 1M strings: 50% with 20-800 significant digits, 30
                  "subnormal and near-DBL_MAX values with 17-25 digits")
 FALLBACK_HBM_GBS = 6800.0
 L2_BYTES = 129 * 1000 * 1000
+# how kernel_ms is measured (the value is the sample interval)
+KERNEL_TIMING = ("CUDA events recorded by the library on the call's stream around the kernels of "
+                 "every %d-th call of the timed region; the mean over those calls")
 
 
 def log(*a):
@@ -341,7 +344,10 @@ def run_ours(args, world, rank, dist) -> None:
             parse_into(d_text, out, st, cnt, stream=stream)
         torch.cuda.synchronize()
 
-    fp.timing_enable(True)
+    # the library's CUDA events around the kernels of every --kernel-sample-th
+    # timed call (an event between two kernels ends their programmatic
+    # overlap, so timing every call would slow every step a little)
+    fp.timing_enable(True, every=args.kernel_sample)
     fp.timing_read(stream)  # reset the sums
     s_before = fp.stats(reset=True, stream=stream)
     if dist is not None:
@@ -436,6 +442,8 @@ def run_ours(args, world, rank, dist) -> None:
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "parse_kernel (fused index+parse+Algorithm 1)",
                      "kernel_ms": parse_ms, "fallback_kernel_ms": fb_ms,
+                     "kernel_calls_timed": kt["calls"],
+                     "kernel_timing": KERNEL_TIMING % args.kernel_sample,
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"},
         "gpu_launches": 2 * args.steps,
@@ -544,7 +552,7 @@ def run_ext(args, world, rank, dist) -> None:
         for _ in range(20):
             call()
         torch.cuda.synchronize()
-    fp.timing_enable(True)
+    fp.timing_enable(True, every=args.kernel_sample)
     fp.timing_read(stream)
     fp.stats(reset=True, stream=stream)
     if dist is not None:
@@ -591,7 +599,9 @@ def run_ext(args, world, rank, dist) -> None:
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "parse_kernel (%s)" % mode, "kernel_ms": parse_ms,
-                     "fallback_kernel_ms": fb_ms, "algorithmic_bytes_per_launch": alg_bytes,
+                     "fallback_kernel_ms": fb_ms, "kernel_calls_timed": kt["calls"],
+                     "kernel_timing": KERNEL_TIMING % args.kernel_sample,
+                     "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_kind": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
@@ -1068,6 +1078,8 @@ def make_parser() -> argparse.ArgumentParser:
     ap.add_argument("--n", type=int, default=0,
                     help="numbers per shard (0: the workload's own size)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--kernel-sample", type=int, default=8,
+                    help="time the kernels of every k-th timed call with CUDA events (k >= 1)")
     ap.add_argument("--clock-settle", type=float, default=1.0,
                     help="seconds of untimed steps before the timed region")
     ap.add_argument("--reference-seconds", type=float, default=60.0,

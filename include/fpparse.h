@@ -417,10 +417,14 @@ FP_API fp_err_t fp_autotune(const char *text, size_t len, char delim, const char
                      fp_config_t *chosen);
 
 /*
- * fp_timing_enable -- when on != 0, later parse calls record CUDA events on
- * their stream around each kernel they launch, and the library adds up the
+ * fp_timing_enable -- when on > 0, every on-th later parse call on a stream
+ * (counting that stream's calls; on = 1: every call) records CUDA events on
+ * the stream around each kernel it launches, and the library adds up those
  * kernels' device time per stream without synchronising (events are
- * harvested as they complete).  Off by default.
+ * harvested as they complete).  on <= 0 turns it off (the default).  An
+ * event between two kernels ends their programmatic overlap, so a timed
+ * call takes a few microseconds longer than an untimed one; timing a sample
+ * of the calls (on > 1) keeps that cost off the others.
  */
 FP_API fp_err_t fp_timing_enable(int on);
 

@@ -461,9 +461,12 @@ def autotune(text: torch.Tensor, delim=b"\n", cache_path: str | None = None) -> 
             "fallback_queue": c.fallback_queue}
 
 
-def timing_enable(on: bool = True) -> None:
-    """Record CUDA events around each kernel of later calls (see timing_read)."""
-    _lib.check(_lib.load().fp_timing_enable(int(on)), "fp_timing_enable")
+def timing_enable(on: bool = True, every: int = 1) -> None:
+    """Record CUDA events around each kernel of every `every`-th later call on
+    a stream (see timing_read); on=False turns it off."""
+    if on and every < 1:
+        raise ValueError("every must be at least 1")
+    _lib.check(_lib.load().fp_timing_enable(int(every) if on else 0), "fp_timing_enable")
 
 
 def timing_read(stream=None) -> dict:

@@ -116,7 +116,8 @@ struct Scratch {
   bool test_stall = false;
   unsigned long long test_wait_ns = 0;
 };
-bool g_timing = false;
+// fp_timing_enable: 0 off, else every g_timing-th call on a stream is timed
+int g_timing = 0;
 
 std::map<std::pair<int, cudaStream_t>, Scratch*> g_scratch;
 
@@ -336,7 +337,7 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   const int per_sm = cfg.ctas_per_sm ? std::min<int>((int)cfg.ctas_per_sm, occ) : occ;
   unsigned long long grid = (unsigned long long)di.sms * per_sm;
   if (grid > total_chunks) grid = total_chunks;
-  const bool timing = g_timing;
+  const bool timing = g_timing > 0 && s->calls % (unsigned long long)g_timing == 0;
   int slot = -1;
   if (timing) {
     slot = s->ev_head;
@@ -974,7 +975,7 @@ fp_err_t fp_get_config(fp_config_t* cfg) {
 
 fp_err_t fp_timing_enable(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
-  g_timing = on != 0;
+  g_timing = on > 0 ? on : 0;
   return FP_OK;
 }
 

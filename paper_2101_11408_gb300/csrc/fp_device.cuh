@@ -543,11 +543,11 @@ FP_HD uint32_t dp4a_u(uint32_t a, uint32_t b, uint32_t c) {
 #endif
 }
 
-// Two words of flag bytes (each 0x80 or 0) to 128 times an 8-bit mask: bit
-// b for byte b of w0, bit 4 + b for byte b of w1 (a byte dot product weighs
-// each flag by 2^b or 2^(4+b)).
-FP_HD uint32_t flag_pair(uint32_t w0, uint32_t w1) {
-  return dp4a_u(w1, 0x80402010u, dp4a_u(w0, 0x08040201u, 0u));
+// Two words of flag bytes (each 0x80 or 0) to 128 times an 8-bit mask, plus
+// c: bit b for byte b of w0, bit 4 + b for byte b of w1 (a byte dot product
+// weighs each flag by 2^b or 2^(4+b)).
+FP_HD uint32_t flag_pair(uint32_t w0, uint32_t w1, uint32_t c = 0u) {
+  return dp4a_u(w1, 0x80402010u, dp4a_u(w0, 0x08040201u, c));
 }
 
 // 0x80 in every byte of t that is zero, exactly.
@@ -674,7 +674,11 @@ FP_HD bool parse_window(const uint8_t* tile, const WindowTables& wt, int s, int 
     uint32_t f[6];
 #pragma unroll
     for (int j = 0; j < 6; j++) f[j] = nondigit_exact(x[j]);
-    M = (flag_pair(f[0], f[1]) >> 7) | (flag_pair(f[2], f[3]) << 1) | (flag_pair(f[4], f[5]) << 9);
+    // 128 M, the higher pairs carried in the dot products' accumulator (128 M
+    // < 2^31)
+    uint32_t t = flag_pair(f[4], f[5]);
+    t = flag_pair(f[2], f[3], t << 8);
+    M = flag_pair(f[0], f[1], t << 8) >> 7;
     M &= 0xFFFFFFFFu << tsig;
   }
   // An exponent: the last non-digit is an 'e' or 'E', or a sign right after

@@ -699,6 +699,9 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   WarpSmem& sm = smem[wib];
   Ctl* ctl = p.ctl;
+  // The next call's parse kernel (a programmatic dependent launch) may be
+  // set up now; it waits on the device until this grid has completed.
+  grid_launch_dependents();
   // the parse grid this launch depends on has completed, its writes visible
   grid_dependency_wait();
   const unsigned long long nq_all = *(volatile unsigned long long*)&ctl->qcount;
@@ -771,7 +774,8 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
 // so this launch's set-up overlaps the parse; its blocks wait on the device
 // (griddepcontrol.wait) until the parse grid has completed and its writes
 // are visible.  On a workload with nothing pending they then return at once,
-// and the call pays little more than the parse.
+// and the call pays little more than the parse.  It releases the next call's
+// parse kernel in turn, so that launch's set-up overlaps this one.
 template <class F>
 static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream) {
   cudaLaunchConfig_t cfg = {};

@@ -16,8 +16,19 @@ static cudaError_t launch_parse_c(const LaunchParams& p, int grid, cudaStream_t 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  parse_kernel<C, F, 0><<<grid, NT, Layout<C>::TOTAL, stream>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = Layout<C>::TOTAL;
+  cfg.stream = stream;
+  // a programmatic dependent launch (the kernel waits on the device for the
+  // kernel before it; see parse_kernel)
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, parse_kernel<C, F, 0>, p);
 }
 
 template <class F>

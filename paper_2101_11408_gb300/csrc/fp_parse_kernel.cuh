@@ -233,6 +233,12 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
   // on the device for this grid to finish); every block of this persistent
   // grid is resident by the time all of them have executed this
   grid_launch_dependents();
+  // This launch is itself a programmatic dependent of the kernel before it
+  // on the stream (usually the previous call's fallback kernel, which
+  // releases it as it starts): its blocks are set up while that kernel
+  // runs and wait here until it has completed and its writes are visible.
+  // Nothing is read or written before this point.
+  grid_dependency_wait();
   if (tid == 0) {
     for (int b = 0; b < NSTAGE; b++) mbar_init(&ms->bar[b], 1);
     fence_mbar_init();
@@ -336,8 +342,7 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
         const int j = tid * L::SEG_PER_THREAD + k;  // granule within the chunk
         const uint4 v = *reinterpret_cast<const uint4*>(tile + PAD + 16 * j);
         // one bit per byte position
-        const uint32_t m16 = (flag_pair(flags(v.x), flags(v.y)) >> 7) |
-                             (flag_pair(flags(v.z), flags(v.w)) << 1);
+        const uint32_t m16 = flag_pair(flags(v.x), flags(v.y), flag_pair(flags(v.z), flags(v.w)) << 8) >> 7;
         mask |= (MaskT)m16 << (16 * k);
       }
     };
