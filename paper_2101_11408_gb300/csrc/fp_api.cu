@@ -832,7 +832,9 @@ fp_err_t fp_parse_ex(const char* text, size_t len, const fp_options_t* opt, void
   }
   if (len > 0 && (!text || !out_values || !out_status)) return FP_ERR_ARG;
   const bool f32 = opt->format == FP_FORMAT_F32;
-  const int mode = (opt->grammar == FP_GRAMMAR_JSON ? 1 : 0) | (K ? 2 : 0);  // MODE_* bits
+  // MODE_* bits of the parse kernel: JSON 1, column-major 2, hexadecimal 4
+  const int mode = (opt->grammar == FP_GRAMMAR_JSON ? 1 : 0) | (K ? 2 : 0) |
+                   (opt->grammar == FP_GRAMMAR_HEX ? 4 : 0);
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   std::lock_guard<std::mutex> lk(g_mu);
   Config cfg = g_cfg;

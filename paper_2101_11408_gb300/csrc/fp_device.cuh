@@ -745,4 +745,129 @@ FP_HD bool json_ok_fast(const uint8_t* tile, int s, const FastToken& t) {
   return !bad;
 }
 
+
+// Value of four hexadecimal digit values (bytes 0-15), the first byte most
+// significant: 4096 v0 + 256 v1 + 16 v2 + v3.
+FP_HD uint32_t hex4(uint32_t v) {
+#ifdef __CUDA_ARCH__
+  return __dp2a_hi(0x00010010u, v, __dp2a_lo(0x01001000u, v, 0u));
+#else
+  return 4096u * (v & 0xFF) + 256u * ((v >> 8) & 0xFF) + 16u * ((v >> 16) & 0xFF) + (v >> 24);
+#endif
+}
+
+// Straight-line tokenizer for the common shape of a hexadecimal float
+// (Appendix C's %a form, Python's float.hex()):
+//     [+-] 0 (x|X) hexdigits-with-at-most-one-'.' (p|P) [+-] d{1,4}
+// with at most 24 bytes after the sign and a significand below 2^64 (at
+// most 16 hexadecimal digits from the first nonzero one).  The same window
+// as parse_window: the 24 bytes ending at the terminator e.  Exact per-byte
+// flags mark the bytes that are not hexadecimal digits (and, in the last
+// two words, not decimal digits: the exponent's); the point is moved out
+// and the bytes outside the significand set to '0' with parse_window's
+// tables; four digit values per byte-dot-product pair give the 96-bit
+// window, which is shifted right by the exponent part's length.  The value
+// is exactly significand x 2^(exponent - 4 x fraction digits), rounded
+// once (hex_to_bits).  Returns false for any other shape; the general
+// tokenizer then decides (with identical results for the shapes accepted
+// here).  Reads as parse_window does.
+template <class F>
+FP_HD bool parse_hex_window(const uint8_t* tile, const WindowTables& wt, int s, int e,
+                            uint64_t& bits, uint8_t& status) {
+  const int L = e - s;
+  if (L < 5 || L > 25) return false;
+  const uint32_t c0 = tile[s];
+  const int sg = (c0 == '-') | (c0 == '+');
+  const int s1 = s + sg;
+  const int tsig = 24 - (e - s1);  // window position of the "0x"
+  if (tsig < 0 || tile[s1] != '0' || (tile[s1 + 1] | 0x20u) != 'x') return false;
+  const int w0 = e - 24;
+  const uint32_t* t32 = reinterpret_cast<const uint32_t*>(tile);
+  const int i0 = w0 >> 2;
+  const uint32_t sh = (uint32_t)(w0 & 3) * 8;
+  uint32_t x[6];
+  {
+    uint32_t W[7];
+#pragma unroll
+    for (int j = 0; j < 7; j++) W[j] = t32[i0 + j];
+#pragma unroll
+    for (int j = 0; j < 6; j++) x[j] = fshr(W[j], W[j + 1], sh);
+  }
+  // per byte (bit 7 of a flag byte): nd = not a decimal digit (exact, as
+  // nondigit_exact); nl = not a letter a-f or A-F: with the case bit set,
+  // (byte ^ 0x60) & 0x7F lies in [1, 6] exactly for those letters
+  uint32_t fh[6];  // not a hexadecimal digit
+  uint32_t fd4 = 0, fd5 = 0;
+#pragma unroll
+  for (int j = 0; j < 6; j++) {
+    const uint32_t t1 = (x[j] ^ 0x30303030u) & 0x7F7F7F7Fu;
+    const uint32_t nd = (t1 + 0x76767676u) | x[j];
+    const uint32_t t2 = ((x[j] | 0x20202020u) ^ 0x60606060u) & 0x7F7F7F7Fu;
+    const uint32_t nl = (t2 + 0x79797979u) | ~(t2 + 0x7F7F7F7Fu) | x[j];
+    fh[j] = nd & nl & 0x80808080u;
+    if (j == 4) fd4 = nd & 0x80808080u;
+    if (j == 5) fd5 = nd & 0x80808080u;
+  }
+  const int m0 = tsig + 2;  // first byte after the "0x"
+  uint32_t MH;              // bit i: window byte i is not a hexadecimal digit
+  {
+    uint32_t t = flag_pair(fh[4], fh[5]);
+    t = flag_pair(fh[2], fh[3], t << 8);
+    MH = (flag_pair(fh[0], fh[1], t << 8) >> 7) & (0xFFFFFFFFu << m0);
+  }
+  // The exponent: the last byte that is not a hexadecimal digit is a 'p'
+  // or a sign right after one, and 1 to 4 decimal digits follow it.
+  const int hb = 31 - clz32(MH);
+  if (hb < 19 || hb > 22) return false;
+  const uint32_t MD = ((flag_pair(fd4, fd5) >> 7) << 16) & (0xFFFFFFFFu << (hb + 1));
+  if (MD != 0) return false;  // a letter among the exponent digits
+  const uint32_t ch = tile[w0 + hb];
+  const int hs = (ch == '+') | (ch == '-');
+  const int pp = hb - hs;  // the marker's position
+  if ((tile[w0 + pp] | 0x20u) != 'p' || pp <= m0) return false;
+  const uint32_t keep_e = 0xFFFFFFFFu << (8 * (hb - 19));  // the 23 - hb exponent digits
+  int ex = (int)dig4((x[5] & keep_e) | (0x30303030u & ~keep_e));
+  if (ch == '-') ex = -ex;
+  // the significand [m0, pp): hexadecimal digits and at most one point
+  const uint32_t Mp = MH & ((1u << pp) - 1u);
+  if (Mp & (Mp - 1u)) return false;
+  const int hp = Mp != 0;
+  const int dpos = hp ? ctz32(Mp) : 24;
+  if (hp && tile[w0 + dpos] != '.') return false;
+  const int lo = m0 + hp;  // the first digit's position once the point is gone
+  if (pp - lo < 1) return false;  // no digit at all
+  {
+    uint32_t prev = 0x30303030u;
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+      const uint32_t xj = x[j];
+      x[j] = byte_perm(prev, xj, wt.sel[j][dpos]);
+      prev = xj;
+    }
+    uint32_t k[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) k[j] = wt.keep_from[j][lo];
+    k[4] &= wt.keep_below[0][pp - 16];
+    k[5] &= wt.keep_below[1][pp - 16];
+#pragma unroll
+    for (int j = 0; j < 6; j++) x[j] = (x[j] & k[j]) | (0x30303030u & ~k[j]);
+  }
+  // digit values (letters have bit 6 set: their low nibble + 9), four per
+  // 16-bit group, the window as three 32-bit words
+  uint32_t N[6];
+#pragma unroll
+  for (int j = 0; j < 6; j++)
+    N[j] = hex4((x[j] & 0x0F0F0F0Fu) + 9u * ((x[j] >> 6) & 0x01010101u));
+  const uint32_t v_hi = (N[0] << 16) | N[1], v_mid = (N[2] << 16) | N[3], v_lo = (N[4] << 16) | N[5];
+  // the 24 - pp zero digits from the exponent part shifted out
+  const uint32_t zs = 4u * (uint32_t)(24 - pp);  // 8..24
+  if (v_hi >> zs) return false;  // more than 64 bits of significand
+  const uint64_t m = ((uint64_t)fshr(v_mid, v_hi, zs) << 32) | fshr(v_lo, v_mid, zs);
+  const int64_t e2 = (int64_t)ex - 4 * (hp ? pp - 1 - dpos : 0);
+  const uint64_t b = m ? hex_to_bits<F>(m, e2, false) : 0;
+  bits = b | (c0 == '-' ? F::SIGN : 0);
+  status = m ? status_of<F>(b) : (uint8_t)ST_OK;
+  return true;
+}
+
 }  // namespace fp

@@ -42,9 +42,11 @@ namespace fp {
 // carries none of their instructions): MODE_JSON checks the JSON number
 // grammar on the fast path's fields; MODE_COLUMNS stores field i at column
 // i mod K, row i div K, and flags fields whose terminator disagrees with
-// their column.
+// their column; MODE_HEX (the decimal-or-hexadecimal grammar) sends fields
+// with an "0x" to the hexadecimal window tokenizer.
 constexpr int MODE_JSON = 1;
 constexpr int MODE_COLUMNS = 2;
+constexpr int MODE_HEX = 4;
 
 constexpr int NT = 256;       // threads per block
 constexpr int PAD = 16;       // bytes staged before the chunk (holds the byte at c0-1)
@@ -500,6 +502,20 @@ __global__ void __launch_bounds__(NT, (C >= 16384 ? 3 : 4)) parse_kernel(const L
     // tokenizer, which runs in a separate pass so that this loop stays free
     // of rare branches.
     auto parse_hot = [&](int s, int e, unsigned long long& bits, uint8_t& status) {
+      if constexpr ((MODE & MODE_HEX) != 0) {
+        // a hexadecimal float (Appendix C): its own window tokenizer, whose
+        // value needs no Algorithm 1 (the digits give the bits)
+        const uint32_t c0 = tile[s];
+        const int s1 = s + ((c0 == '-') | (c0 == '+'));
+        if ((tile[s1 + 1] | 0x20u) == 'x') {
+          uint64_t hbits = 0;
+          uint8_t hst = ST_GENERAL;
+          if (!parse_hex_window<F>(tile, *wtab, s, e, hbits, hst)) hst = ST_GENERAL;
+          bits = hbits;
+          status = hst;
+          return;
+        }
+      }
       FastToken ft;
       ft.w = 0;
       ft.q = 0;

@@ -2,11 +2,14 @@
 // host from the device header (its functions are host-callable) and run on
 // every '\n'-separated field of standard input: the window tokenizer of
 // Section 4 on a padded tile (with its lookup tables as the kernel builds
-// them), Algorithm 1 (Section 5) on its (w, q), and
+// them), Algorithm 1 (Section 5) on its (w, q), in the hexadecimal grammar
+// the hexadecimal window tokenizer for fields with an "0x" (as the kernel's
+// hexadecimal mode does), and
 // the general tokenizer with the 19-digit check of Section 11 for the fields
 // the first one declines; fields both leave undecided are printed as "P"
 // (the fallback kernel's).  One line per field: "<bits hex> <status>" or
-// "P".  The test compares the decided ones with the oracle.
+// "P".  The test compares the decided ones with the oracle.  The number of
+// fields the hexadecimal window decided goes to standard error.
 //
 // usage: hot_path_check <64|32> <grammar 0|1|2> < text
 #include <cstdio>
@@ -22,6 +25,7 @@ namespace {
 constexpr int LEAD = 32;  // tile bytes before the field (parse_window reads up to 28)
 
 fp::WindowTables g_wt;
+long g_hex_window = 0;
 
 template <class F>
 void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& tab) {
@@ -35,6 +39,23 @@ void check_field(const uint8_t* field, int n, uint32_t grammar, const fp::Pow5& 
   std::memcpy(tile + LEAD, field, (size_t)n);
   tile[LEAD + n] = '\n';
   const int s = LEAD, e = LEAD + n;
+  if (grammar == GRAMMAR_HEX) {
+    const uint32_t c0 = tile[s];
+    const int s1 = s + ((c0 == '-') | (c0 == '+'));
+    if ((tile[s1 + 1] | 0x20u) == 'x') {
+      uint64_t hbits = 0;
+      uint8_t hst = ST_GENERAL;
+      if (parse_hex_window<F>(tile, g_wt, s, e, hbits, hst)) {
+        g_hex_window++;
+        std::printf("%016llx %u\n", (unsigned long long)hbits, (unsigned)hst);
+        return;
+      }
+      const FieldResult g = parse_short_field<F>(tile + s, n, tab, grammar);
+      if (g.status == ST_PENDING) std::printf("P\n");
+      else std::printf("%016llx %u\n", (unsigned long long)g.bits, (unsigned)g.status);
+      return;
+    }
+  }
   FastToken ft;
   ft.w = 0;
   ft.q = 0;
@@ -90,5 +111,6 @@ int main(int argc, char** argv) {
     else check_field<fp::F64>(f, n, grammar, tab);
     p = q + 1;
   }
+  std::fprintf(stderr, "hex_window %ld\n", g_hex_window);
   return 0;
 }

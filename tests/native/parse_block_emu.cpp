@@ -9,8 +9,9 @@
 // other blocks' words.  The text is placed at a chosen offset modulo 16.
 //
 // usage: parse_block_emu <64|32> <grammar 0|1|2> <chunk bytes> <offset 0..15> [blocks
-//        [columns rows_cap]] < text   (grammar 2 runs the JSON mode; columns K >= 2
-//        the column-major mode, '\n' rows of K ','-separated fields)
+//        [columns rows_cap]] < text   (grammar 1 runs the hexadecimal mode, 2 the
+//        JSON mode; columns K >= 2 the column-major mode, '\n' rows of K
+//        ','-separated fields)
 // One line per field: "<bits hex> <status>" as stored (pending fields keep
 // their location word and a pending status), then "count <n>".
 #include <ucontext.h>
@@ -190,6 +191,8 @@ void body() {
   switch (g_mode) {
     case fp::MODE_JSON: fp::parse_kernel<C, F, fp::MODE_JSON>(g_p); break;
     case fp::MODE_COLUMNS: fp::parse_kernel<C, F, fp::MODE_COLUMNS>(g_p); break;
+    case fp::MODE_HEX: fp::parse_kernel<C, F, fp::MODE_HEX>(g_p); break;
+    case fp::MODE_HEX | fp::MODE_COLUMNS: fp::parse_kernel<C, F, fp::MODE_HEX | fp::MODE_COLUMNS>(g_p); break;
     default: fp::parse_kernel<C, F, 0>(g_p); break;
   }
 }
@@ -314,6 +317,7 @@ int main(int argc, char** argv) {
   while ((got = std::fread(buf, 1, sizeof(buf), stdin)) > 0) text.append(buf, got);
   const size_t len = text.size();
   g_mode = columns ? fp::MODE_COLUMNS : (grammar == fp::GRAMMAR_JSON ? fp::MODE_JSON : 0);
+  if (grammar == fp::GRAMMAR_HEX) g_mode |= fp::MODE_HEX;
   const size_t cap = columns ? columns * rows_cap : len;
   // the text at `offset` modulo 16, with digits around it (never used)
   std::vector<uint8_t> mem(len + 256, '7');

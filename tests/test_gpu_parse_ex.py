@@ -74,6 +74,36 @@ def test_hex_grammar(f32):
     check(workloads.bulk_mixed_text(200000, 5), "hex", f32)     # decimal fields still parse
 
 
+@pytest.mark.parametrize("f32", [False, True])
+def test_hex_workload_takes_the_hex_window(f32):
+    """float.hex() values (the hexadecimal-float workload's recipe): every
+    field decided in the parse kernel's hexadecimal mode by the hexadecimal
+    window tokenizer (none reaches the general tokenizer), bit-exact with the
+    oracle; then the same values as 4-column CSV rows (the hexadecimal and
+    column-major modes together)."""
+    n = 300000
+    text = workloads.hex_float_text(n, workloads.SEED_BASE + 84)
+    torch.cuda.synchronize()
+    fp.stats(reset=True)
+    check(text, "hex", f32)
+    s = fp.stats(reset=True)
+    assert s["fields"] == n and s["general_tokenizer"] == 0, s
+    K = 4
+    lines = text.split(b"\n")[:40000]
+    csv = b"\n".join(b",".join(lines[r * K:(r + 1) * K]) for r in range(len(lines) // K))
+    rows_cap = len(lines) // K + 2
+    vals, st, cnt = fp.parse_ex(to_device(csv, 5), b",", f32=f32, grammar="hex", columns=K,
+                                rows_cap=rows_cap)
+    torch.cuda.synchronize()
+    assert fp.get_error() == 0 and cnt == len(lines) // K * K
+    rb, rs = oracle.parse_buffer(csv, b",", f32=f32, grammar=oracle.GRAMMAR_HEX)
+    ov, ost = oracle.columnar(csv, rb, rs, K, rows_cap, b",")
+    got = vals.cpu().numpy().reshape(-1).view(np.uint32 if f32 else np.uint64)
+    gst = st.cpu().numpy().reshape(-1)
+    filled = ost != 0xEE
+    assert np.array_equal(gst, ost) and np.array_equal(got[filled], ov[filled])
+
+
 def test_hex_and_json_are_off_by_default():
     lines = ["0x1p3", "+1", "01", ".5"]
     check(join(lines), "decimal", lines=lines)

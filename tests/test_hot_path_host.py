@@ -35,10 +35,13 @@ def hot_path(tmp_path_factory):
     return exe
 
 
-def run_hot_path(exe, text: bytes, f32=False, grammar=0):
-    """Decided fields as (index, bits, status) arrays, and the pending count."""
+def run_hot_path(exe, text: bytes, f32=False, grammar=0, stderr=None):
+    """Decided fields as (index, bits, status) arrays, and the pending count
+    (the harness's report, "hex_window <fields>", goes into stderr if given)."""
     r = subprocess.run([exe, "32" if f32 else "64", str(grammar)], input=text,
                        capture_output=True, timeout=600, check=True)
+    if stderr is not None:
+        stderr.append(r.stderr.decode())
     lines = r.stdout.split(b"\n")[:-1]
     idx, bits, st = [], [], []
     pending = 0
@@ -54,8 +57,8 @@ def run_hot_path(exe, text: bytes, f32=False, grammar=0):
         np.array(st, dtype=np.uint8), pending
 
 
-def check(exe, text: bytes, f32=False, grammar=0, max_pending=None):
-    n, idx, bits, st, pending = run_hot_path(exe, text, f32, grammar)
+def check(exe, text: bytes, f32=False, grammar=0, max_pending=None, stderr=None):
+    n, idx, bits, st, pending = run_hot_path(exe, text, f32, grammar, stderr)
     rb, rs = oracle.parse_buffer(text, f32=f32, grammar=grammar)
     assert n == rb.size, "field counts differ"
     want_b = rb.astype(np.uint64)[idx]
@@ -154,6 +157,28 @@ def test_hex_floats(hot_path, f32):
     lines += ["1.5", "-0.25e-3", "0x", "0x.p1", "0x1p", "0x1g", "0X1P-1074", "0x1p-1075",
               "0x1.fffffffffffff8p1023", "0x1.fffffffffffff7p1023"]
     check(hot_path, "\n".join(lines).encode(), f32, grammar=1)
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_hex_window_decides_the_hex_workload(hot_path, f32):
+    """The hexadecimal-float workload (float.hex() of uniform values and of
+    random finite bit patterns: subnormals, zeros, both signs, exponents to
+    +-1023) plus hand-made shapes at the window's edges: every field of the
+    workload is decided by the hexadecimal window tokenizer, bit-exact with
+    the oracle (the value is dyadic: one rounding of the exact significand x
+    2^exponent, Appendix C)."""
+    text = workloads.hex_float_text(20000, workloads.SEED_BASE + 83)
+    err = []
+    n, _ = check(hot_path, text, f32, grammar=1, max_pending=0, stderr=err)
+    assert err[-1].split() == ["hex_window", str(n)]
+    edges = ["0x1p0", "0x.8p1", "0x1.p0", "0X1.8P3", "+0x1p-1", "-0x0p+0", "0x0.0p-9999",
+             "0x1p+9999", "0x1p-1074", "0x1p-1075", "0x1.8p-1075", "0x1.fffffffffffffp+1023",
+             "0x1.fffffffffffff8p+1023", "0xffffffffffffffffp0", "0x1ffffffffffffffffp0",
+             "0x0000000000000001.0p0", "0x1.0000000000000000p0", "0xabcdefABCDEFp-20",
+             "0x1.99999999999999999p-4", "0x1pp1", "0x1.8.p1", "0x1p1a", "0x1p+", "0xp1",
+             "0x1.gp1", "0x1p12345", "-0x1.0000000000001p-1022", "0x123456789abcdefp-2",
+             "0x1.8p1 ", " 0x1.8p1", "0x1.8", "0x1_8p1"]
+    check(hot_path, "\n".join(edges).encode(), f32, grammar=1)
 
 
 def test_hard_cases_decided_where_possible(hot_path):
@@ -284,6 +309,14 @@ HOT_MUTANTS = [
     ("19-digit truncation", "      exp_adj++;\n      sticky |= (d != 0);", "      sticky |= (d != 0);"),
     ("w+1 check", "    ElResult b = convert_wq<F>(w + 1, q, tab, true);",
      "    ElResult b = convert_wq<F>(w, q, tab, true);"),
+    ("hex letter value", "hex4((x[j] & 0x0F0F0F0Fu) + 9u * ((x[j] >> 6) & 0x01010101u))",
+     "hex4((x[j] & 0x0F0F0F0Fu) + 10u * ((x[j] >> 6) & 0x01010101u))"),
+    ("hex fraction digits", "(int64_t)ex - 4 * (hp ? pp - 1 - dpos : 0)",
+     "(int64_t)ex - 4 * (hp ? pp - dpos : 0)"),
+    ("hex exponent part", "const uint32_t zs = 4u * (uint32_t)(24 - pp);",
+     "const uint32_t zs = 4u * (uint32_t)(23 - pp);"),
+    ("hex significand limit", "  if (v_hi >> zs) return false;", ""),
+    ("hex single point", "  if (Mp & (Mp - 1u)) return false;\n", ""),
     ("JSON leading zero",
      "    ok = ok && nint > 0 && !(nint > 1 && s[int_start] == '0') && !(point && ndig == nint);",
      "    ok = ok && nint > 0 && !(point && ndig == nint);"),
@@ -313,7 +346,9 @@ def test_planted_slip_in_the_hot_path_is_caught(tmp_path, what, old, new):
               lambda: test_exact_ties_and_their_neighbours(exe, False),
               lambda: test_grammar_fuzz(exe, 2),
               lambda: test_hard_cases_decided_where_possible(exe),
-              lambda: test_ties_at_the_top_of_the_tie_range(exe, False)]
+              lambda: test_ties_at_the_top_of_the_tie_range(exe, False),
+              lambda: test_hex_floats(exe, False),
+              lambda: test_hex_window_decides_the_hex_workload(exe, False)]
     caught = 0
     for c in checks:
         try:

@@ -105,8 +105,23 @@ def test_grammar_edges_blanks_and_empty_fields(emu):
 
 
 def test_hex_grammar_and_a_long_field(emu):
+    """The hexadecimal mode: float.hex() values (the hexadecimal window
+    tokenizer), decimal fields among them (the decimal one), and random
+    hexadecimal shapes, some beyond the window (the general tokenizer)."""
     lines = workloads.hex_float_lines(3000, 99) + ["1.5", "2e-3", "0x1p-1075"]
     _check(emu, "\n".join(lines).encode(), grammar=1, offset=6, max_pending=0)
+    rnd = random.Random(98)
+    mixed = []
+    for _ in range(4000):
+        m = "".join(rnd.choice("0123456789abcdefABCDEF") for _ in range(rnd.randrange(1, 20)))
+        if rnd.random() < 0.5:
+            p = rnd.randrange(0, len(m) + 1)
+            m = m[:p] + "." + m[p:]
+        f = rnd.choice(["", "-", "+"]) + rnd.choice(["0x", "0X"]) + m
+        if rnd.random() < 0.8:
+            f += rnd.choice("pP") + rnd.choice(["", "+", "-"]) + str(rnd.randrange(0, 1100))
+        mixed.append(f if rnd.random() < 0.9 else "%.17g" % rnd.random())
+    _check(emu, "\n".join(mixed).encode(), grammar=1, offset=3, max_pending=0, blocks=2)
     big = b"1." + b"0" * 40000 + b"1"  # one field over several chunks: the fallback's
     n, pending = _check(emu, b"2.5\n" + big + b"\n-7", offset=0)
     assert n == 3 and pending == 1
