@@ -21,6 +21,12 @@
  * outputs, counts and device-side errors are valid after the stream has
  * reached that point.  Calls on the same stream are ordered.  Calls on
  * different streams may run concurrently; each stream gets its own scratch.
+ * A parse call's kernels are programmatic dependent launches and release
+ * the kernel queued after them early: a caller's kernel launched with
+ * programmatic stream serialization right after a call may start before
+ * the call has finished, so it must wait (cudaGridDependencySynchronize)
+ * before it reads the call's results, as that launch mode requires; any
+ * other operation queued after a call starts once the call is complete.
  *
  * Host threads.  Every entry point may be called from any host thread; the
  * library's shared state (the per-stream scratch table, the configuration,
