@@ -109,6 +109,10 @@ struct Scratch {
   cudaEvent_t pipe_ev_start = nullptr, pipe_ev_done = nullptr;
   unsigned long long* pipe_counts = nullptr;     // segment counts (pinned) ...
   unsigned long long* pipe_counts_dv = nullptr;  // ... and the address the parse kernel writes them at
+  // how many fields the stream's last finished call queued for the fallback
+  // kernel (pinned; written by that kernel), and its device address
+  unsigned long long* pend_host = nullptr;
+  unsigned long long* pend_dv = nullptr;
   unsigned long long* pipe_host = nullptr;       // one count (pinned) ...
   unsigned long long* pipe_host_dv = nullptr;    // ... and the address the parse kernel writes it at
   // fp_test_arm_stalled_lookback: the next call skips chunk 0 and waits at
@@ -212,6 +216,7 @@ void free_scratch(Scratch* s) {
   if (s->pipe_ev_done) cudaEventDestroy(s->pipe_ev_done);
   cudaFreeHost(s->pipe_counts);
   cudaFreeHost(s->pipe_host);
+  cudaFreeHost(s->pend_host);
   if (prev >= 0) cudaSetDevice(prev);
   delete s;
 }
@@ -316,6 +321,17 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   }
   p.ctl = s->ctl;
   p.chunk_status = s->chunk_status;
+  if (!s->pend_host) {
+    FP_CUDA(cudaMallocHost(&s->pend_host, sizeof(unsigned long long)));
+    *s->pend_host = 0;
+    FP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->pend_dv), s->pend_host, 0));
+  }
+  p.pending_out = s->pend_dv;
+  // When the stream's last finished call had fallback work, a one-block
+  // launch separates this call's parse and fallback kernels, so that the
+  // fallback kernel's blocks start in their own division of the SMs' on-chip
+  // memory (large L1) instead of the parse kernel's (fp_fallback_kernel.cu).
+  const bool separate = *reinterpret_cast<volatile unsigned long long*>(s->pend_host) != 0;
   p.epoch = s->epoch++;
   p.queue = s->queue;
   p.qcap = s->qcap;
@@ -351,6 +367,7 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   if (mode) FP_CUDA(fp::launch_parse_ext(p, (int)cfg.chunk_bytes, (int)grid, stream, f32, mode));
   else FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
   if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
+  if (separate) FP_CUDA(fp::launch_fallback_separator(stream));
   const int fb_grid =
       total_bytes < SMALL_TEXT_BYTES ? di.sms : di.sms * (f32 ? di.fb_occ32 : di.fb_occ);
   FP_CUDA(fp::launch_fallback(p, fb_grid, stream, f32));

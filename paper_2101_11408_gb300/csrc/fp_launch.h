@@ -10,15 +10,18 @@ namespace fp {
 // else binary64 (8-byte values; p.loc == p.out_bits).
 cudaError_t launch_parse(const LaunchParams& p, int chunk_bytes, int grid, cudaStream_t stream,
                          bool f32 = false);
-// The JSON / column-major modes (mode: MODE_* bits of fp_parse_kernel.cuh,
-// nonzero), for 8 KiB and 16 KiB chunks; the occupancy of the most
-// demanding of those instances.
+// The JSON / hexadecimal / column-major modes (mode: MODE_* bits of
+// fp_parse_kernel.cuh, nonzero), for 8 KiB and 16 KiB chunks; the blocks
+// per SM that every one of those instances reaches.
 cudaError_t launch_parse_ext(const LaunchParams& p, int chunk_bytes, int grid,
                              cudaStream_t stream, bool f32, int mode);
 cudaError_t parse_occupancy_ext(int chunk_bytes, int* blocks_per_sm);
 cudaError_t parse_occupancy(int chunk_bytes, int* blocks_per_sm, bool f32 = false);
 
 cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32 = false);
+// a one-block launch that separates the parse and fallback kernels (see
+// fp_fallback_kernel.cu)
+cudaError_t launch_fallback_separator(cudaStream_t stream);
 cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32 = false);
 
 }  // namespace fp

@@ -64,6 +64,11 @@ struct LaunchParams {
   // the stream's error word (Ctl::error) here, so that the host learns the
   // call's outcome without a copy of its own.
   unsigned int* err_out;
+  // Optional (null: unused), pinned host memory through its device address:
+  // the fallback kernel stores how many fields the call queued for it (queue
+  // appends plus overflow chunks; 0 when none), so that the host can tell
+  // whether the stream's calls have fallback work.
+  unsigned long long* pending_out;
 };
 
 constexpr unsigned long long WAIT_NS_DEFAULT = 2000000000ull;  // 2 s
