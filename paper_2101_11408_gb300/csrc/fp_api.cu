@@ -62,7 +62,8 @@ struct DeviceInfo {
   std::map<int, int> parse_occ;    // chunk bytes -> resident blocks per SM (binary64)
   std::map<int, int> parse_occ32;  // the same for the binary32 kernels
   std::map<int, int> parse_occ_ext;  // JSON / column-major kernels (8 and 16 KiB chunks)
-  int fb_occ = 0, fb_occ32 = 0;
+  int fb_occ = 0, fb_occ32 = 0;          // the fallback kernel's idle build
+  int fb_busy = 0, fb_busy32 = 0;        // and its busy build (fp_launch.h)
   char name[256] = {0};
 };
 std::map<int, DeviceInfo> g_dev;
@@ -175,6 +176,10 @@ fp_err_t device_info(int dev, DeviceInfo** out) {
     di.fb_occ = std::max(di.fb_occ, 1);
     FP_CUDA(fp::fallback_occupancy(&di.fb_occ32, true));
     di.fb_occ32 = std::max(di.fb_occ32, 1);
+    FP_CUDA(fp::fallback_occupancy(&di.fb_busy, false, true));
+    di.fb_busy = std::max(di.fb_busy, 1);
+    FP_CUDA(fp::fallback_occupancy(&di.fb_busy32, true, true));
+    di.fb_busy32 = std::max(di.fb_busy32, 1);
     it = g_dev.emplace(dev, di).first;
   }
   *out = &it->second;
@@ -368,9 +373,11 @@ fp_err_t run(Scratch* s, const Config& cfg, const DeviceInfo& di, LaunchParams& 
   else FP_CUDA(fp::launch_parse(p, (int)cfg.chunk_bytes, (int)grid, stream, f32));
   if (timing) FP_CUDA(cudaEventRecord(s->ev[slot][1], stream));
   if (separate) FP_CUDA(fp::launch_fallback_separator(stream));
-  const int fb_grid =
-      total_bytes < SMALL_TEXT_BYTES ? di.sms : di.sms * (f32 ? di.fb_occ32 : di.fb_occ);
-  FP_CUDA(fp::launch_fallback(p, fb_grid, stream, f32));
+  // the fallback kernel's busy build on a stream with fallback work, else its
+  // idle build (fp_launch.h); either decides whatever is queued
+  const int fb_occ = separate ? (f32 ? di.fb_busy32 : di.fb_busy) : (f32 ? di.fb_occ32 : di.fb_occ);
+  const int fb_grid = total_bytes < SMALL_TEXT_BYTES ? di.sms : di.sms * fb_occ;
+  FP_CUDA(fp::launch_fallback(p, fb_grid, stream, f32, separate));
   if (timing) {
     FP_CUDA(cudaEventRecord(s->ev[slot][2], stream));
     s->ev_used[slot] = true;

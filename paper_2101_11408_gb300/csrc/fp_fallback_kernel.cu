@@ -39,6 +39,7 @@
 
 #include "dec_tables.inc"
 #include "fp_device.cuh"
+#include "fp_launch.h"
 #include "fp_sync.cuh"
 #include "fp_types.cuh"
 
@@ -693,8 +694,13 @@ __device__ void resolve(const LaunchParams& p, unsigned long long oi, WarpSmem& 
   __syncwarp();
 }
 
-template <class F>
-__global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p) {
+// Two builds (MINB, the blocks per SM the registers must allow): 5 (96
+// registers) for a launch that is expected to find nothing queued, 8 (64
+// registers, a few spilled) for a stream with fallback work.  The wider one
+// decided the hard-case mix 3% faster (2.53 against 2.61 ms), but used for
+// every call it made the bulk step 3.7 us longer.
+template <class F, int MINB>
+__global__ void __launch_bounds__(FB_NT, MINB) fallback_kernel(const LaunchParams p) {
   __shared__ WarpSmem smem[FB_WARPS];
   const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
   WarpSmem& sm = smem[wib];
@@ -781,7 +787,8 @@ __global__ void __launch_bounds__(FB_NT, 5) fallback_kernel(const LaunchParams p
 // and the call pays little more than the parse.  It releases the next call's
 // parse kernel in turn, so that launch's set-up overlaps this one.
 template <class F>
-static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream) {
+static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream_t stream,
+                                     bool busy) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(FB_NT);
@@ -792,7 +799,8 @@ static cudaError_t launch_fallback_f(const LaunchParams& p, int grid, cudaStream
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, fallback_kernel<F>, p);
+  return busy ? cudaLaunchKernelEx(&cfg, fallback_kernel<F, FB_BUSY_BLOCKS>, p)
+              : cudaLaunchKernelEx(&cfg, fallback_kernel<F, FB_IDLE_BLOCKS>, p);
 }
 
 // One block that does nothing, queued between a parse kernel and the
@@ -809,17 +817,23 @@ cudaError_t launch_fallback_separator(cudaStream_t stream) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32) {
-  return f32 ? launch_fallback_f<F32>(p, grid, stream) : launch_fallback_f<F64>(p, grid, stream);
+cudaError_t launch_fallback(const LaunchParams& p, int grid, cudaStream_t stream, bool f32,
+                            bool busy) {
+  return f32 ? launch_fallback_f<F32>(p, grid, stream, busy)
+             : launch_fallback_f<F64>(p, grid, stream, busy);
 }
 
 template <class F>
-static cudaError_t fallback_occupancy_f(int* blocks_per_sm) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fallback_kernel<F>, FB_NT, 0);
+static cudaError_t fallback_occupancy_f(int* blocks_per_sm, bool busy) {
+  return busy ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    blocks_per_sm, fallback_kernel<F, FB_BUSY_BLOCKS>, FB_NT, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    blocks_per_sm, fallback_kernel<F, FB_IDLE_BLOCKS>, FB_NT, 0);
 }
 
-cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32) {
-  return f32 ? fallback_occupancy_f<F32>(blocks_per_sm) : fallback_occupancy_f<F64>(blocks_per_sm);
+cudaError_t fallback_occupancy(int* blocks_per_sm, bool f32, bool busy) {
+  return f32 ? fallback_occupancy_f<F32>(blocks_per_sm, busy)
+             : fallback_occupancy_f<F64>(blocks_per_sm, busy);
 }
 
 }  // namespace fp

@@ -8,6 +8,7 @@
 // use; this entry point instead keeps the scratch of the same two kernels
 // in one fixed device array below, which every GPU that loads the library
 // holds until the process exits.
+#include <algorithm>
 #include <cuda_runtime.h>
 
 #include <cstring>
